@@ -1,0 +1,128 @@
+"""The oracle's pins must catch plausible mistakes (no GPU).
+
+Each case plants one mistake in a temporary copy of ``oracle/cliffs_oracle.cpp`` (a dropped
+term, a wrong sign, a wrong index or factor), builds it with the host compiler, points the
+oracle module at it, and requires at least one pin of ``test_oracle_pins`` to fail. The
+committed oracle is never modified.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "cliffs_oracle.cpp")
+
+# (name, exact text in the oracle source, replacement, pins expected to notice)
+MUTATIONS = [
+    ("depth term of eq. (eqQ) dropped",
+     "return 0.5 * (lam_a + lam_b) * (r_a - r_b) / ds - GRAV * (d_a - d_b) / ds;",
+     "return 0.5 * (lam_a + lam_b) * (r_a - r_b) / ds;",
+     ["test_lake_at_rest", "test_pulse_closed_form"]),
+    ("sign of the averaged flux in eq. (solver2)",
+     "pn = pC - Fp + lpC", "pn = pC + Fp + lpC",
+     ["test_pulse_closed_form", "test_dalembert_speed_and_second_order"]),
+    ("second-order term of eq. (solver2) dropped",
+     "pn = pC - Fp + lpC * k2 * (QpR - QpL) - adt + sdt;", "pn = pC - Fp - adt + sdt;",
+     ["test_pulse_closed_form"]),
+    ("mirror ghost keeps the velocity sign",
+     "Node<T> Gh{S.e1[j], -S.w1[j], S.t1[j], d[j]};", "Node<T> Gh{S.e1[j], S.w1[j], S.t1[j], d[j]};",
+     ["test_standing_wave_wall_at_half_node", "test_mass_linear_limit"]),
+    ("wall on the node instead of half a node out",
+     "const double dsR = (j < n - 1) ? ds[j] : ds[n - 2];",
+     "const double dsR = (j < n - 1) ? ds[j] : 0.5 * ds[n - 2];",
+     ["test_standing_wave_wall_at_half_node"]),
+    ("eq. (stateh) with 8g",
+     "T hn = (pn - qn) * (pn - qn) / (16.0 * g);", "T hn = (pn - qn) * (pn - qn) / (8.0 * g);",
+     ["test_lake_at_rest", "test_pulse_closed_form"]),
+    ("friction exponent 3/2 instead of 4/3",
+     "inline double pow43(double a) { return a * std::cbrt(a); }",
+     "inline double pow43(double a) { return a * std::sqrt(a); }",
+     ["test_friction_uniform_flow"]),
+    ("flooding test with -d_i",
+     "if (!(val(eta[j]) + d[i] > hmin)) continue;", "if (!(val(eta[j]) - d[i] > hmin)) continue;",
+     ["test_step_b_flooding_by_hand", "test_step_b_threshold_and_dry_velocity"]),
+    ("tie-break picks the smaller eta",
+     "if (best < 0 || val(eta[j]) > val(eta[best])) best = j;",
+     "if (best < 0 || val(eta[j]) < val(eta[best])) best = j;",
+     ["test_step_b_tie_break"]),
+    ("cushion sets h_j instead of h_j/2",
+     "if (val(hi) > 0.5 * val(hj)) S.e2[i] = 0.5 * hj - d[i];",
+     "if (val(hi) > 0.5 * val(hj)) S.e2[i] = hj - d[i];",
+     ["test_step_e_cushion_limiter"]),
+    ("transverse advection sign",
+     "tn = C.t - Ft + C.w * k2 * (QtR - QtL);", "tn = C.t + Ft + C.w * k2 * (QtR - QtL);",
+     ["test_transverse_velocity_advected_by_u"]),
+    ("cos(phi) missing from the row metric",
+     "const double f = sph() ? R_SPHERE * std::cos(y[jy] * DEG) * DEG : 1.0;",
+     "const double f = sph() ? R_SPHERE * DEG : 1.0;",
+     ["test_spherical_zonal_speed_scales_with_cos_lat"]),
+    ("spherical continuity term with the wrong sign",
+     "if (src) sdt = dt * cC * C.w * src[j];", "if (src) sdt = -dt * cC * C.w * src[j];",
+     ["test_spherical_area_weighted_mass"]),
+    ("friction reverses the flow",
+     "if (std::fabs(val(adt)) > std::fabs(val(C.w))) adt = C.w;", "",
+     ["test_friction_clamp_never_reverses"]),
+    ("max-wave counts dry cells",
+     "if (!(fl && val(eta[c]) + Gd.d[c] >= Gd.P.h_min)) continue;", "(void)fl;",
+     ["test_maxwave_ignores_dry_cells"]),
+    ("bilinear weights transposed",
+     "w01 = a * (1 - b), w10 = (1 - a) * b", "w01 = (1 - a) * b, w10 = a * (1 - b)",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("eq. (newdw) over 2 instead of 4",
+     "nd = s * s / 4.0;", "nd = s * s / 2.0;",
+     ["test_depth_filter_by_hand"]),
+    ("tangent of a quotient with the wrong sign",
+     "return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));",
+     "return Dual(a.v / b.v, (a.d * b.v + a.v * b.d) / (b.v * b.v));",
+     ["test_tlm_matches_central_differences"]),
+]
+
+
+def _pin_functions(names):
+    out = []
+    for name in names:
+        fn = getattr(pins, name)
+        params = getattr(fn, "pytestmark", [])
+        combos = [{}]
+        for m in params:
+            if m.name == "parametrize":
+                keys = [k.strip() for k in m.args[0].split(",")]
+                vals = m.args[1]
+                new = []
+                for c in combos:
+                    for v in vals:
+                        v = v if isinstance(v, tuple) else (v,)
+                        cc = dict(c)
+                        cc.update(zip(keys, v))
+                        new.append(cc)
+                combos = new
+        for c in combos:
+            out.append((name, fn, c))
+    return out
+
+
+@pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(case, tmp_path):
+    name, old, new, targets = case
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor must occur exactly once: %r" % old
+    path = tmp_path / "mut.cpp"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                    "-ffp-contract=off", "-o", str(so), str(path)], check=True)
+    oracle.swap_library(str(so))
+    caught = []
+    try:
+        for pname, fn, kw in _pin_functions(targets):
+            try:
+                fn(**kw)
+            except (AssertionError, ValueError, FloatingPointError):
+                caught.append((pname, kw))
+    finally:
+        oracle.swap_library(None)
+    assert caught, "no pin caught: %s" % name

@@ -1,0 +1,555 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test names the passage of the Cliffs manual (arXiv 1410.0753) it checks. None of them
+compares the oracle with itself: the expected values come from the paper's closed forms,
+from exact solutions of the linear equations, from conservation and symmetry, or from the
+algorithm's rules applied by hand to tiny inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+G = 9.81
+
+
+def line_params(n, dt, **kw):
+    return oracle.params(n, 1, dt, **kw)
+
+
+# ----------------------------------------------------------------------------------------
+# Section "Numerical stability", eqs. (eq:uet2), (eq:f), (eq:uet): one-step response of a
+# single-node pulse (eta_j, u_j) in a still basin on an uneven bottom, uniform spacing.
+
+def pulse_residual(eps, solver, form):
+    dx, dt = 100.0, 1.0
+    d = np.array([40.0, 40.0, 30.0, 20.0, 35.0, 60.0, 60.0, 60.0, 60.0])
+    j = 4
+    n = len(d)
+    eta = np.zeros(n)
+    u = np.zeros(n)
+    eta[j] = eps
+    u[j] = 0.3 * eps
+    p = line_params(n, dt, manning_n2=0.0, solver=solver, form=form, h_min=0.01)
+    r = oracle.sweep_line(p, np.full(n - 1, dx), d, eta, u, np.zeros(n))
+    beta = dt * math.sqrt(G * d[j]) / dx                                        # Courant number
+    f = (6 * math.sqrt(d[j]) - math.sqrt(d[j - 1]) - math.sqrt(d[j + 1])) / (4 * math.sqrt(d[j]))
+    u_exp = (1 - beta ** 2 * f) * u[j]                                          # eq. (eq:u2)
+    eta_exp = (1 - beta ** 2) * eta[j]                                          # eq. (eq:et)
+    if solver == 2:                                                             # eq. (eq:et2)
+        eta_exp -= beta / (4 * math.sqrt(G)) * (math.sqrt(d[j + 1]) - math.sqrt(d[j - 1])) * u[j]
+    return abs(r["w"][j] - u_exp), abs(r["eta"][j] - eta_exp), abs(eta_exp - eta[j])
+
+
+@pytest.mark.parametrize("solver", [2, 1])
+@pytest.mark.parametrize("form", [0, 1])
+def test_pulse_closed_form(solver, form):
+    """The residual against the closed form is second order in the pulse size: halving
+    the pulse quarters it (a wrong first-order term would only halve it)."""
+    ru1, re1, shift = pulse_residual(1e-4, solver, form)
+    ru2, re2, _ = pulse_residual(5e-5, solver, form)
+    for a, b in ((ru1, ru2), (re1, re2)):
+        assert a < 1e-7
+        assert 3.3 < a / b < 4.7, (a, b)
+    assert shift > 50 * re1          # the one-step change itself is far above the residual
+
+
+def test_pulse_solvers_differ_by_the_printed_term():
+    """eq. (eq:et2) minus eq. (eq:et): solver2 adds -beta/(4 sqrt g)(sqrt d_{j+1} - sqrt d_{j-1}) u."""
+    _, re2, _ = pulse_residual(1e-4, 2, 0)
+    # evaluating solver1 against the solver2 closed form leaves the printed term as residual
+    dx, dt, j = 100.0, 1.0, 4
+    d = np.array([40.0, 40.0, 30.0, 20.0, 35.0, 60.0, 60.0, 60.0, 60.0])
+    eta = np.zeros(9); u = np.zeros(9); eta[j] = 1e-4; u[j] = 3e-5
+    r1 = oracle.sweep_line(line_params(9, dt, solver=1), np.full(8, dx), d, eta, u, np.zeros(9))
+    r2 = oracle.sweep_line(line_params(9, dt, solver=2), np.full(8, dx), d, eta, u, np.zeros(9))
+    beta = dt * math.sqrt(G * d[j]) / dx
+    term = beta / (4 * math.sqrt(G)) * (math.sqrt(d[j + 1]) - math.sqrt(d[j - 1])) * u[j]
+    assert abs((r1["eta"][j] - r2["eta"][j]) - term) < 1e-3 * abs(term)
+
+
+# ----------------------------------------------------------------------------------------
+# eq. (eqQ): "In the steady state, Q = 0". Lake at rest over wet/dry steps, with land,
+# a shoreline, an island, friction and both shoreline modes (itopo).
+
+def lake_bathy(nx=40, ny=30):
+    x = np.arange(nx) * 100.0
+    y = np.arange(ny) * 100.0
+    X, Y = np.meshgrid(x, y)
+    d = 20.0 - 25.0 * X / x[-1] + 3.0 * np.sin(Y / 300.0)
+    d -= 30.0 * np.exp(-((X - 1500) ** 2 + (Y - 1500) ** 2) / (2 * 250.0 ** 2))   # island
+    d, _ = oracle.depth_filter(d)
+    return x, y, d
+
+
+@pytest.mark.parametrize("itopo", [1, 0])
+def test_lake_at_rest(itopo):
+    x, y, d = lake_bathy()
+    assert (d < 0).any() and (d > 0).any()
+    for form, tol in ((0, 1e-9), (1, 0.0)):
+        p = oracle.params(d.shape[1], d.shape[0], 2.0, h_min=0.01, manning_n2=6.25e-4,
+                          itopo=itopo, dwall=1.0, form=form)
+        r = oracle.run(p, x, y, d, np.zeros_like(d), nsteps=1000)
+        for k in ("eta", "u", "v"):
+            assert np.abs(r[k]).max() <= tol, (form, k, np.abs(r[k]).max())
+
+
+# ----------------------------------------------------------------------------------------
+# Linear long waves travel at sqrt(g h): on a flat bottom a still Gaussian hump splits
+# into two halves moving at +-sqrt(gH) (d'Alembert). The scheme is second order in space
+# (section "Difference Scheme": "second-order accurate in space for a uniform grid").
+
+def dalembert_error(dx):
+    H, sigma, A = 10.0, 150.0, 1e-3
+    L = 6000.0
+    n = int(round(L / dx)) + 1
+    x = np.arange(n) * dx
+    c = math.sqrt(G * H)
+    dt = 0.5 * 10.0 / c * (dx / 10.0)
+    T = 1500.0 / c
+    steps = int(round(T / dt))
+    t = steps * dt
+    x0 = 3000.0
+    eta0 = A * np.exp(-(x - x0) ** 2 / (2 * sigma ** 2))
+    p = oracle.params(n, 1, dt, manning_n2=0.0, h_min=0.01)
+    r = oracle.run(p, x, np.zeros(1), np.full((1, n), H), eta0[None, :], nsteps=steps)
+    exact = 0.5 * A * (np.exp(-(x - x0 - c * t) ** 2 / (2 * sigma ** 2)) +
+                       np.exp(-(x - x0 + c * t) ** 2 / (2 * sigma ** 2)))
+    return np.abs(r["eta"][0] - exact).max() / A
+
+
+def test_dalembert_speed_and_second_order():
+    e10 = dalembert_error(10.0)           # sigma / dx = 15
+    e20 = dalembert_error(20.0)           # sigma / dx = 7.5
+    assert e10 < 0.01, e10
+    assert e20 / e10 > 3.0, (e20, e10)
+
+
+# ----------------------------------------------------------------------------------------
+# Dimensional splitting (eqs. eq2A/eq2B): for y-invariant data between reflecting north and
+# south walls the y-sweep is the identity, so every row of a 2D run equals the 1D run.
+
+def beach_1d(n=60):
+    x = np.arange(n) * 50.0
+    d = 8.0 - 10.0 * x / x[-1]
+    eta = 0.6 * np.exp(-(x - 800.0) ** 2 / (2 * 200.0 ** 2))
+    return x, d, eta
+
+
+@pytest.mark.parametrize("form,tol", [(1, 0.0), (0, 1e-12)])
+def test_1d_equals_2d_rows(form, tol):
+    x, d1, e1 = beach_1d()
+    n, ny, dt, steps = len(x), 7, 1.5, 150
+    kw = dict(h_min=0.01, manning_n2=6.25e-4, form=form)
+    r1 = oracle.run(oracle.params(n, 1, dt, **kw), x, np.zeros(1), d1[None, :], e1[None, :],
+                    nsteps=steps)
+    y = np.arange(ny) * 50.0
+    r2 = oracle.run(oracle.params(n, ny, dt, **kw), x, y, np.tile(d1, (ny, 1)),
+                    np.tile(e1, (ny, 1)), nsteps=steps)
+    wet = (r1["eta"][0] + d1 >= 0.01)
+    assert wet.sum() > 20 and (~wet).sum() > 3
+    for k in ("eta", "u"):
+        assert np.abs(r2[k] - r1[k][0][None, :]).max() <= tol
+    assert np.abs(r2["v"]).max() == 0.0
+
+
+@pytest.mark.parametrize("form,tol", [(1, 0.0), (0, 1e-12)])
+def test_1d_equals_2d_columns(form, tol):
+    y, d1, e1 = beach_1d()
+    n, nx, dt, steps = len(y), 7, 1.5, 150
+    kw = dict(h_min=0.01, manning_n2=6.25e-4, form=form)
+    r1 = oracle.run(oracle.params(1, n, dt, **kw), np.zeros(1), y, d1[:, None], e1[:, None],
+                    nsteps=steps)
+    x = np.arange(nx) * 50.0
+    r2 = oracle.run(oracle.params(nx, n, dt, **kw), x, y, np.tile(d1[:, None], (1, nx)),
+                    np.tile(e1[:, None], (1, nx)), nsteps=steps)
+    assert np.abs(r2["eta"] - r1["eta"]).max() <= tol
+    assert np.abs(r2["v"] - r1["v"]).max() <= tol
+    assert np.abs(r2["u"]).max() == 0.0
+
+
+# ----------------------------------------------------------------------------------------
+# Mass in a closed, fully wet flat basin: in the linear limit the update telescopes with the
+# mirror walls and conserves sum(eta); the scheme is in characteristic (non-conservative)
+# form, so the nonlinear drift is of the order of the wave steepness.
+
+def mass_drift(eps, form=0, nsteps=400):
+    nx, ny, H = 30, 24, 10.0
+    x = np.arange(nx) * 100.0
+    y = np.arange(ny) * 100.0
+    X, Y = np.meshgrid(x, y)
+    eta0 = eps * H * np.exp(-((X - 1200) ** 2 + (Y - 1100) ** 2) / (2 * 300.0 ** 2))
+    p = oracle.params(nx, ny, 3.0, manning_n2=0.0, form=form)
+    r = oracle.run(p, x, y, np.full((ny, nx), H), eta0, nsteps=nsteps)
+    return abs(r["eta"].sum() - eta0.sum()) / np.abs(eta0).sum()
+
+
+def test_mass_linear_limit():
+    lin = mass_drift(1e-6, form=1)
+    non = mass_drift(1e-2, form=1)
+    assert lin < 1e-6, lin
+    assert non > 100 * lin                 # the drift is a nonlinear effect
+    assert mass_drift(1e-6, form=0) < 1e-5
+
+
+# ----------------------------------------------------------------------------------------
+# Walls half a node from the last wet node (section "Numerics": "a half-node re-positioning
+# of the reflecting wall within a cell"; reading 3): the gravest seiche of a closed basin of
+# N nodes has length L = N dx and period 2 L / sqrt(g H) (a wall on the node would give
+# (N - 1) dx, 2.5 % shorter for N = 40).
+
+def test_standing_wave_wall_at_half_node():
+    N, dx, H, A = 40, 25.0, 10.0, 1e-4
+    L = N * dx
+    c = math.sqrt(G * H)
+    x = np.arange(N) * dx
+    dt = 0.25 * dx / c
+    T = 2 * L / c
+    eta0 = A * np.cos(np.pi * (x + dx / 2) / L)
+    p = oracle.params(N, 1, dt, manning_n2=0.0)
+    steps = int(2.6 * T / dt)
+    r = oracle.run(p, x, np.zeros(1), np.full((1, N), H), eta0[None, :], nsteps=steps,
+                   gout=1, gauges=[(0, 0)])
+    s = r["gauges"][:, 0, 0]
+    t = np.arange(len(s)) * dt
+    k = np.where((s[:-1] > 0) & (s[1:] <= 0))[0]         # downward zero crossings
+    tc = t[k] + dt * s[k] / (s[k] - s[k + 1])
+    period = np.diff(tc).mean()
+    assert abs(period / T - 1) < 3e-3, period / T
+
+
+# ----------------------------------------------------------------------------------------
+# Friction (reading 4): in a uniform flow no flux enters the interior, so the interior
+# velocity follows the explicit Euler step of u_t = -g n^2 u |u| / h^(4/3), and h is
+# untouched; the clamp keeps a thin fast layer from reversing.
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_friction_uniform_flow(form):
+    n2, H, dt, u0, nx = 6.25e-4, 2.0, 1.0, 1.5, 30
+    x = np.arange(nx) * 100.0
+    p = oracle.params(nx, nx, dt, manning_n2=n2, form=form)
+    r = oracle.run(p, x, x, np.full((nx, nx), H), np.zeros((nx, nx)),
+                   np.full((nx, nx), u0), nsteps=5)
+    u = u0
+    for _ in range(5):
+        u = u - dt * G * n2 * u * abs(u) / H ** (4.0 / 3.0)
+    c = (15, 15)
+    assert abs(r["u"][c] - u) <= 1e-13 * u
+    assert r["u"][c] < u0
+    assert abs(r["eta"][c]) <= (0.0 if form == 1 else 1e-13)
+
+
+def test_friction_clamp_never_reverses():
+    n, dt = 9, 1.0
+    p = line_params(n, dt, manning_n2=6.25e-4, h_min=0.01)
+    r = oracle.sweep_line(p, np.full(n - 1, 100.0), np.full(n, 0.02), np.zeros(n),
+                          np.full(n, 2.0), np.zeros(n))
+    assert abs(r["w"][4]) < 1e-14
+    p1 = line_params(n, dt, manning_n2=6.25e-4, h_min=0.01, form=1)
+    r1 = oracle.sweep_line(p1, np.full(n - 1, 100.0), np.full(n, 0.02), np.zeros(n),
+                           np.full(n, 2.0), np.zeros(n))
+    assert r1["w"][4] == 0.0
+
+
+# ----------------------------------------------------------------------------------------
+# Inundation algorithm, steps (a)-(e), applied by hand to 7-node lines.
+
+def sweep7(d, eta, w, t=None, itopo=1, dwall=0.0, dt=0.1):
+    n = len(d)
+    p = line_params(n, dt, h_min=0.01, manning_n2=0.0, itopo=itopo, dwall=dwall)
+    return oracle.sweep_line(p, np.full(n - 1, 10.0), np.array(d, float), np.array(eta, float),
+                             np.array(w, float), np.zeros(n) if t is None else np.array(t, float))
+
+
+def test_step_b_flooding_by_hand():
+    d = [5, 5, 5, -0.2, -1, -1, -1]
+    r = sweep7(d, [0.5, 0.5, 0.5, 0, 0, 0, 0], [0.3, 0.3, 0.3, 0, 0, 0, 0],
+               [0.1, 0.1, 0.1, 0, 0, 0, 0])
+    assert list(r["wet0"]) == [1, 1, 1, 0, 0, 0, 0]                 # (a): h = -0.2 < h_min
+    assert list(r["wet1"]) == [1, 1, 1, 1, 0, 0, 0]                 # (b): 0.5 - 0.2 > 0.01
+    assert r["src"][3] == 2
+    assert r["eta_b"][3] == 0.01 - (-0.2)                           # height h_min
+    assert r["w_b"][3] == 0.3 and r["t_b"][3] == 0.1                # neighbour's velocities
+    assert r["wet1"][4] == 0                                        # one ring per sweep
+    assert r["eta"][4] == 0.0 and r["w"][4] == 0.0
+
+
+def test_step_b_threshold_and_dry_velocity():
+    r = sweep7([5, 5, 5, -0.6, -1, -1, -1], [0.5, 0.5, 0.5, 0, 0, 0, 0],
+               [0.3, 0.3, 0.3, 0.7, 0.7, 0, 0])
+    assert r["wet1"][3] == 0                                        # 0.5 - 0.6 < h_min
+    assert r["w_b"][3] == 0.0 and r["w_b"][4] == 0.0                # (a): dry cells at rest
+
+
+def test_step_b_tie_break():
+    d = [5, 5, -0.1, 5, 5, 5, 5]
+    r = sweep7(d, [0.5, 0.5, 0, 0.8, 0.8, 0.8, 0.8], [0.2, 0.2, 0, -0.4, -0.4, -0.4, -0.4])
+    assert r["src"][2] == 3 and r["w_b"][2] == -0.4                 # larger eta wins
+    r = sweep7(d, [0.5, 0.5, 0, 0.5, 0.5, 0.5, 0.5], [0.2, 0.2, 0, -0.4, -0.4, -0.4, -0.4])
+    assert r["src"][2] == 1 and r["w_b"][2] == 0.2                  # tie: the left one
+
+
+def test_step_a_vertical_wall_mode():
+    # itopo = 0: nodes shallower than dwall are a permanent wall, even when covered
+    r = sweep7([5, 5, 0.5, 5, 5, 5, 5], [0.5, 0.5, 2.0, 0.5, 0.5, 0.5, 0.5],
+               [0.3] * 7, itopo=0, dwall=1.0)
+    assert r["wet0"][2] == 0 and r["wet1"][2] == 0
+    r = sweep7([5, 5, 0.5, 5, 5, 5, 5], [0.5, 0.5, 2.0, 0.5, 0.5, 0.5, 0.5], [0.3] * 7, itopo=1)
+    assert r["wet0"][2] == 1
+
+
+def test_step_e_cushion_limiter():
+    # height branch: the new cell (3, filled from 2) ends above half its neighbour after (d)
+    d = [0.559, 0.205, 0.142, -0.009, -1, -1, -1]
+    r = sweep7(d, [0.038, 0.263, 0.284, 0, 0, 0, 0], [1.73, -1.647, 2.98, 0, 0, 0, 0], dt=1.976)
+    assert r["src"][3] == 2
+    hj = r["eta"][2] + d[2]
+    assert r["eta_d"][3] + d[3] > hj / 2                             # the limiter fires
+    assert abs((r["eta"][3] + d[3]) - hj / 2) < 1e-15                # h_i = h_j / 2
+    # velocity branch: |u_i| > |u_j| after (d) is cut back to u_j
+    d = [1.6228, 1.6228, 1.6228, -0.0436, -1, -1, -1]
+    r = sweep7(d, [0.6066, 0.6066, 0.6066, 0, 0, 0, 0], [1.377, 1.377, 1.377, 0, 0, 0, 0],
+               dt=0.5664)
+    assert r["src"][3] == 2
+    assert abs(r["w_d"][3]) > abs(r["w"][2])
+    assert r["w"][3] == r["w"][2]
+    # no limiter: a new cell below half its neighbour keeps its (d) state
+    d = [10, 10, 10, -0.05, -1, -1, -1]
+    r = sweep7(d, [1.0, 1.0, 1.0, 0, 0, 0, 0], [3.0, 3.0, 3.0, 0, 0, 0, 0], dt=1.0)
+    assert r["src"][3] == 2
+    assert r["eta_d"][3] + d[3] <= (r["eta"][2] + d[2]) / 2
+    assert r["eta"][3] == r["eta_d"][3]
+
+
+def test_front_moves_at_most_one_cell_per_sweep():
+    # dam break onto a dry flat (section "Inundation algorithm": "the wet area is also
+    # expanded by no more than one cell on each side")
+    nx, ny = 40, 30
+    x = np.arange(nx) * 10.0
+    d = np.full((ny, nx), -0.001)
+    eta = np.zeros((ny, nx))
+    eta[10:20, 15:25] = 1.0
+    p = oracle.params(nx, ny, 0.1, h_min=0.01, manning_n2=0.0)
+    wet = lambda e: (e + d >= 0.01)
+    prev = wet(eta)
+    state = (eta, None, None)
+    for _ in range(8):
+        r = oracle.run(p, x, x, d, state[0], state[1], state[2], nsteps=1)
+        now = wet(r["eta"])
+        jj, ii = np.where(prev)
+        # bounding box grows by at most one cell in each direction per step (x then y sweep)
+        j2, i2 = np.where(now)
+        assert i2.min() >= ii.min() - 1 and i2.max() <= ii.max() + 1
+        assert j2.min() >= jj.min() - 1 and j2.max() <= jj.max() + 1
+        prev = now
+        state = (r["eta"], r["u"], r["v"])
+    assert prev.sum() > 100
+
+
+# ----------------------------------------------------------------------------------------
+# Depth-jump filter (eqs. dstab, newdw, newdc), by hand and by its post-conditions.
+
+def test_depth_filter_by_hand():
+    d = np.array([[100.0, 100, 100], [100, 1, 100], [100, 100, 100]])
+    out, n = oracle.depth_filter(d)
+    assert np.all(out == 100.0) and n == 2          # newdw: (10 + 10)^2 / 4
+    out, n = oracle.depth_filter(np.array([[-1.0, 1.0, 100.0]]))
+    assert list(out[0]) == [-1.0, 25.0, 100.0]       # newdc next to the coast: 100 / 2^2
+    out, _ = oracle.depth_filter(np.array([[-1.0, 0.05, 0.1, 0.1]]))
+    assert out[0, 1] == 0.1                          # minimal depth in wet nodes
+    out, _ = oracle.depth_filter(np.array([[4.0, 1.0, 4.0]]), alpha=2.0)
+    assert out[0, 1] == 1.0                          # ratio exactly alpha^2 is allowed
+
+
+def test_depth_filter_postconditions():
+    rng = np.random.default_rng(5)
+    d = 50.0 + 40.0 * rng.standard_normal((60, 50))
+    d[rng.random(d.shape) < 0.05] = 0.5              # shallow spikes
+    d[:, :5] = -3.0                                  # a coast
+    for alpha in (2.0, 2.5):
+        out, n = oracle.depth_filter(d, alpha=alpha)
+        assert n > 0
+        assert np.all(out[d <= 0] == d[d <= 0])      # land untouched
+        a2 = alpha * alpha
+        for arr in (out, out.T):
+            c, l, r = arr[:, 1:-1], arr[:, :-2], arr[:, 2:]
+            wet = c > 0
+            assert np.all(~(wet & (l > 0)) | (l <= a2 * c * (1 + 1e-12)))
+            assert np.all(~(wet & (r > 0)) | (r <= a2 * c * (1 + 1e-12)))
+        again, n2 = oracle.depth_filter(out, alpha=alpha)
+        assert n2 == 1 and np.array_equal(again, out)  # idempotent
+    smooth = np.full((20, 20), 30.0) + np.arange(20)[None, :]
+    out, n = oracle.depth_filter(smooth)
+    assert n == 1 and np.array_equal(out, smooth)   # untouched where dstab holds
+
+
+# ----------------------------------------------------------------------------------------
+# Spherical metrics (reading 7; the paper defers the equations to Titov & Gonzalez 1997):
+# the equatorial limit is the Cartesian grid with dx = R dlambda, and a zonal wave crosses
+# longitude 1 / cos(phi) times faster in degrees.
+
+R = 6371000.0
+
+
+def test_spherical_equator_limit():
+    n, m = 80, 11
+    dlam = 0.01
+    lon = 150.0 + np.arange(n) * dlam
+    lat = (np.arange(m) - m // 2) * 0.01
+    xs = np.radians(lon - lon[0]) * R
+    ys = np.radians(lat - lat[0]) * R
+    H = 100.0
+    X, Y = np.meshgrid(xs, ys)
+    eta0 = 0.5 * np.exp(-((X - xs[40]) ** 2 + (Y - ys[5]) ** 2) / (2 * 3000.0 ** 2))
+    dt = 0.5 * xs[1] / math.sqrt(G * H)
+    rs = oracle.run(oracle.params(n, m, dt, coords=0, manning_n2=0.0), lon, lat,
+                    np.full((m, n), H), eta0, nsteps=40)
+    rc = oracle.run(oracle.params(n, m, dt, coords=1, manning_n2=0.0), xs, ys,
+                    np.full((m, n), H), eta0, nsteps=40)
+    assert np.abs(rs["eta"] - rc["eta"]).max() < 2e-4 * 0.5
+    assert np.abs(rs["eta"]).max() > 0.05
+
+
+def test_spherical_zonal_speed_scales_with_cos_lat():
+    n, m, H = 400, 5, 1000.0
+    dlam = 0.01
+    c = math.sqrt(G * H)
+    for phi in (0.0, 60.0):
+        lon = np.arange(n) * dlam
+        lat = phi + (np.arange(m) - m // 2) * dlam
+        dxm = R * math.cos(math.radians(phi)) * math.radians(dlam)
+        sig = 8 * dlam
+        eta0 = np.tile(1e-3 * np.exp(-(lon - lon[n // 2]) ** 2 / (2 * sig ** 2)), (m, 1))
+        dt = 0.4 * dxm / c
+        steps = 150
+        r = oracle.run(oracle.params(n, m, dt, coords=0, manning_n2=0.0), lon, lat,
+                       np.full((m, n), H), eta0, nsteps=steps)
+        row = r["eta"][m // 2]
+        assert np.isfinite(row).all()
+        right = np.argmax(row[n // 2:]) + n // 2
+        moved_deg = (right - n // 2) * dlam
+        expect_deg = math.degrees(c * steps * dt / (R * math.cos(math.radians(phi))))
+        assert abs(moved_deg - expect_deg) <= 1.5 * dlam, (phi, moved_deg, expect_deg)
+
+
+# ----------------------------------------------------------------------------------------
+# Outputs (section "Running Options": maxout, gout, bndout).
+
+def test_gauges_maxwave_and_bilinear_boundary():
+    import workloads
+    nx, ny = 30, 20
+    x = 100.0 * np.arange(nx)
+    y = 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = np.full((ny, nx), 10.0)
+    lin = 1e-3 * (0.5 * X - 0.25 * Y + 30.0)          # a linear field is reproduced exactly
+    nests = [workloads.Nest(x0=250.0, y0=330.0, dx=40.0, dy=25.0, nx=11, ny=9)]
+    p = oracle.params(nx, ny, 2.0, manning_n2=0.0)
+    r0 = oracle.run(p, x, y, d, lin, nsteps=0, bndout=1, nests=nests)
+    W, E, S, N = r0["boundary"][0]
+    n = nests[0]
+    ys = n.y0 + n.dy * np.arange(n.ny)
+    xs = n.x0 + n.dx * np.arange(n.nx)
+    f = lambda a, b: 1e-3 * (0.5 * a - 0.25 * b + 30.0)
+    assert np.allclose(W[0, 2], f(n.x0, ys), rtol=0, atol=1e-15)
+    assert np.allclose(E[0, 2], f(n.x0 + 10 * n.dx, ys), rtol=0, atol=1e-15)
+    assert np.allclose(S[0, 2], f(xs, n.y0), rtol=0, atol=1e-15)
+    assert np.allclose(N[0, 2], f(xs, n.y0 + 8 * n.dy), rtol=0, atol=1e-15)
+    assert W.shape == (1, 3, 9) and S.shape == (1, 3, 11)          # vals(tim, uvq, pnt)
+    # a running case: gauges every step from step 0, max-wave every step
+    eta0 = 0.3 * np.exp(-((X - 1500) ** 2 + (Y - 1000) ** 2) / (2 * 300.0 ** 2))
+    gauges = [(15, 10), (5, 3), (29, 19)]
+    r = oracle.run(p, x, y, d, eta0, nsteps=30, gout=1, gauges=gauges, maxout=1, bndout=3,
+                   nests=nests)
+    g = r["gauges"]
+    assert g.shape == (31, 3, 3)
+    assert np.array_equal(g[0, :, 0], [eta0[10, 15], eta0[3, 5], eta0[19, 29]])
+    for k, (ix, iy) in enumerate(gauges):
+        assert r["eta_max"][iy, ix] == g[:, k, 0].max()
+    assert r["boundary"][0][0].shape[0] == 11                      # steps 0, 3, ..., 30
+
+
+# ----------------------------------------------------------------------------------------
+# Tangent-linear model (branches frozen on the primal) against central differences.
+
+def test_tlm_matches_central_differences():
+    nx, ny = 36, 24
+    x = 100.0 * np.arange(nx)
+    y = 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = 12.0 - 16.0 * X / x[-1]
+    d, _ = oracle.depth_filter(d)
+    eta0 = 0.4 * np.exp(-((X - 1000) ** 2 + (Y - 1200) ** 2) / (2 * 250.0 ** 2))
+    dirn = np.exp(-((X - 1100) ** 2 + (Y - 1000) ** 2) / (2 * 300.0 ** 2))
+    gauges = [(20, 12), (25, 5), (10, 20)]
+    p = oracle.params(nx, ny, 2.0, manning_n2=6.25e-4, h_min=0.01)
+    steps = 60
+    gval, gtan, _, _ = oracle.run_tlm(p, x, y, d, eta0, dirn, nsteps=steps, gauges=gauges)
+    h = 1e-3
+    rp = oracle.run(p, x, y, d, eta0 + h * dirn, nsteps=steps, gout=1, gauges=gauges)
+    rm = oracle.run(p, x, y, d, eta0 - h * dirn, nsteps=steps, gout=1, gauges=gauges)
+    fd = (rp["gauges"][:, :, 0] - rm["gauges"][:, :, 0]) / (2 * h)
+    scale = np.abs(gtan).max()
+    assert scale > 1e-3
+    assert np.abs(fd - gtan).max() <= 1e-5 * scale, np.abs(fd - gtan).max() / scale
+    r0 = oracle.run(p, x, y, d, eta0, nsteps=steps, gout=1, gauges=gauges)
+    assert np.array_equal(r0["gauges"][:, :, 0], gval)
+
+
+# ----------------------------------------------------------------------------------------
+# eq. (pq3): the transverse velocity is carried by the along-sweep flow, v_t = -u v_x.
+
+def test_transverse_velocity_advected_by_u():
+    n, dx, H, U = 400, 10.0, 10.0, 2.0
+    x = np.arange(n) * dx
+    v0 = 0.1 * np.exp(-(x - 2000.0) ** 2 / (2 * 100.0 ** 2))
+    dt = 0.5 * dx / (U + math.sqrt(G * H))
+    steps = int(100.0 / dt)
+    p = oracle.params(n, 1, dt, manning_n2=0.0)
+    r = oracle.run(p, x, np.zeros(1), np.full((1, n), H), np.zeros((1, n)),
+                   np.full((1, n), U), v0[None, :], nsteps=steps)
+    v = r["v"][0]
+    shift = (np.argmax(v) - np.argmax(v0)) * dx
+    assert abs(shift - U * steps * dt) <= 1.0 * dx
+    assert abs(v.max() / v0.max() - 1) < 0.05
+    p0 = oracle.params(n, 1, dt, manning_n2=0.0, transverse=0)
+    r0 = oracle.run(p0, x, np.zeros(1), np.full((1, n), H), np.zeros((1, n)),
+                    np.full((1, n), U), v0[None, :], nsteps=steps)
+    assert np.array_equal(r0["v"][0][1:-1], v0[1:-1])       # switched off: v stays put
+
+
+# ----------------------------------------------------------------------------------------
+# Spherical continuity (reading 7): with the term h v tan(phi)/R the area-weighted volume
+# sum(eta cos(phi)) of a closed basin is kept in the linear limit; without it, or with the
+# wrong sign, it drifts by the order of the meridional transport.
+
+def test_spherical_area_weighted_mass():
+    n, dlat, H = 40, 0.05, 1000.0
+    lon = 140 + np.arange(n) * dlat
+    lat = 30 + np.arange(n) * dlat
+    LON, LAT = np.meshgrid(lon, lat)
+    eta0 = 1e-3 * np.exp(-((LON - lon[n // 2]) ** 2 + (LAT - lat[n // 3]) ** 2) / (2 * (4 * dlat) ** 2))
+    dsmin = R * math.cos(math.radians(lat[-1])) * math.radians(dlat)
+    dt = 0.5 * dsmin / math.sqrt(G * H)
+    r = oracle.run(oracle.params(n, n, dt, coords=0, manning_n2=0.0), lon, lat,
+                   np.full((n, n), H), eta0, nsteps=300)
+    w = np.cos(np.radians(LAT))
+    drift_area = abs((r["eta"] * w).sum() - (eta0 * w).sum()) / np.abs(eta0 * w).sum()
+    drift_plain = abs(r["eta"].sum() - eta0.sum()) / np.abs(eta0).sum()
+    assert drift_area < 1e-4, drift_area
+    assert drift_plain > 50 * drift_area
+
+
+def test_maxwave_ignores_dry_cells():
+    nx, ny = 20, 12
+    x = 100.0 * np.arange(nx)
+    X, Y = np.meshgrid(x, x[:ny])
+    d = np.where(X > 1500.0, -2.0, 8.0)
+    eta0 = 0.2 * np.exp(-((X - 700) ** 2 + (Y - 500) ** 2) / (2 * 200.0 ** 2))
+    r = oracle.run(oracle.params(nx, ny, 2.0, manning_n2=0.0), x, x[:ny], d, eta0, nsteps=5,
+                   maxout=1)
+    fmax = np.finfo(np.float32).max
+    assert np.all(r["eta_max"][d < -1] == -fmax) and np.all(r["speed_max"][d < -1] == 0)
+    assert np.all(r["eta_max"][d > 0] >= eta0[d > 0])
