@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the split shallow-water step (Cliffs, arXiv 1410.0753) on GB300.
+
+Workload: the 2048 x 2048 geographic grid at 1 arc-minute (lat 20-54 N) with a 2 m elliptical
+source, 64 gauges, max-wave every step and boundary series for 4 enclosed grids every step
+(workloads.spherical_coast). One bench step = one model time step: the fused x-sweep +
+y-sweep kernel with its max-wave / gauge / enclosed-grid epilogue.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Timing: W untimed steps, then K steps, each preceded by a 256 MiB device write that flushes
+the 129 MB L2 (the step's inputs, ~100 MB, would otherwise stay resident); every step kernel
+is timed with CUDA events on the grid's stream; the K steps are bracketed by a barrier and a
+device synchronisation; the maximum over ranks is reported. With N > 1 each rank advances
+its own replica of the grid (the path does not shard: replicas only).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = None
+UNIT = "Gcell-updates/s"
+BYTES_PER_CELL = 36      # read eta, u, v, d, eta_max, speed_max; write eta, u, v (FP32)
+
+
+def baseline_metric():
+    try:
+        return json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+    except Exception:
+        return "Gcell-updates/s"
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "cliffs_step.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1410_0753_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", name + ".json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None, None
+    if d.get("source_sha") != kernel_source_sha():
+        return None, "stale"
+    return d.get("dram_bytes_per_launch"), d.get("note")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-i", str(device_id), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(w, seconds, depth=None):
+    """Time the FP64 oracle on the first steps of the workload (all host cores)."""
+    import oracle
+    threads = oracle.threads(os.cpu_count() or 1)
+    d = depth if depth is not None else oracle.depth_filter(w.depth, w.filter_alpha, w.filter_min_depth)[0]
+    p = oracle.params_from(w)
+    out = dict(eta=w.eta0, u=None, v=None)
+    kw = dict(maxout=w.maxout, gout=w.gout, gauges=w.gauges, bndout=w.bndout, nests=w.nests)
+    t = time.perf_counter()
+    r = oracle.run(p, w.x, w.y, d, w.eta0, nsteps=1, **kw)
+    t1 = time.perf_counter() - t
+    m = int(max(1, min(400, round(seconds / max(t1, 1e-3)))))
+    t = time.perf_counter()
+    r = oracle.run(p, w.x, w.y, d, w.eta0, nsteps=m, **kw)
+    el = time.perf_counter() - t
+    return dict(value=w.cells * m / el / 1e9, steps=m, seconds=el, threads=threads, result=r,
+                depth=d)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    w = workloads.spherical_coast(args.nx, args.ny, steps=3600)
+    threads = oracle.threads(os.cpu_count() or 1)
+    d = oracle.depth_filter(w.depth, w.filter_alpha, w.filter_min_depth)[0]
+    p = oracle.params_from(w)
+    state = dict(eta=w.eta0, u=None, v=None)
+    kw = dict(maxout=w.maxout, gout=w.gout, gauges=w.gauges, bndout=w.bndout, nests=w.nests)
+    k = 0
+    for _ in range(args.warmup):
+        r = oracle.run(p, w.x, w.y, d, state["eta"], state["u"], state["v"], nsteps=1, step0=k, **kw)
+        state = r
+        k += 1
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.run(p, w.x, w.y, d, state["eta"], state["u"], state["v"], nsteps=1, step0=k, **kw)
+        state = r
+        k += 1
+    el = time.perf_counter() - t
+    val = w.cells * args.steps / el / 1e9
+    line = {"metric": baseline_metric(), "value": val, "unit": UNIT, "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.cells, "steps_horizon": 3600},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d consecutive steps of %s (FP64 C++ oracle, OpenMP over lines)"
+                                       % (args.steps, w.name)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cuda(args, world, rank, local):
+    import torch
+    import workloads
+    from paper_1410_0753_gb300 import CliffsGrid, _build
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    _build.build()
+    w = workloads.spherical_coast(args.nx, args.ny, steps=3600)
+    stream = torch.cuda.current_stream()
+    g = CliffsGrid.from_workload(w, stream=stream.cuda_stream)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    eta0 = w.eta0.astype(np.float32)
+    g.set_initial(eta0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        g.step(1)
+    torch.cuda.synchronize()
+    g.kernel_time(-1)
+    g.kernel_time(1)
+    dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(dev_id)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_((i + 1) & 0xFF)
+        g.step(1)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    ms, launches = g.kernel_time(0)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_step = ms_max / args.steps
+    value = world * w.cells * args.steps / (ms_max / 1e3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    achieved = BYTES_PER_CELL * w.cells / (ms / args.steps / 1e3) / 1e9
+    traffic, tnote = profiled_traffic("k_step_fused_spherical_2048")
+
+    # end to end through the public API: pinned host inputs in, host outputs out
+    e2e = None
+    if not args.no_e2e:
+        pin_eta = torch.from_numpy(eta0).pin_memory()
+        nrec = args.steps + 1
+        pin_g = torch.empty((nrec, g.n_gauges, 3), dtype=torch.float32).pin_memory()
+        pin_em = torch.empty((w.ny, w.nx), dtype=torch.float32).pin_memory()
+        pin_sm = torch.empty((w.ny, w.nx), dtype=torch.float32).pin_memory()
+        pin_b = [[torch.empty((nrec, 3, (n.ny if e < 2 else n.nx)), dtype=torch.float64).pin_memory()
+                  for e in range(4)] for n in w.nests]
+        from paper_1410_0753_gb300 import (cliffs_read_boundary, cliffs_read_gauges,
+                                           cliffs_read_maxwave)
+        barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        g.set_initial(pin_eta.numpy())
+        g.step(args.steps)
+        cliffs_read_gauges(g.h, 0, pin_g.numpy())
+        cliffs_read_maxwave(g.h, 0, pin_em.numpy(), pin_sm.numpy())
+        for m in range(len(w.nests)):
+            for e in range(4):
+                cliffs_read_boundary(g.h, m, e, pin_b[m][e].numpy())
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t
+        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te_t, op=torch.distributed.ReduceOp.MAX)
+        te = float(te_t.item())
+        d2h = pin_g.numel() * 4 + 2 * pin_em.numel() * 4 + sum(b.numel() * 8 for bb in pin_b for b in bb)
+        e2e = {"value": world * w.cells * args.steps / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": pin_eta.numel() * 4 / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps,
+               "note": "set_initial from pinned host eta0, step_n(K), read gauges, max-wave and "
+                       "16 boundary series into pinned host buffers; no L2 flush"}
+
+    # the FP64 oracle on host cores (rank 0, one GPU), and the FP32 error on that horizon
+    cpu = None
+    oracle_error = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        s = oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": s["value"], "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+               "sample": "first %d steps of %s, all outputs recorded (%.1f s, FP64 C++ oracle, "
+                         "OpenMP over lines)" % (s["steps"], w.name, s["seconds"])}
+        gv = CliffsGrid.from_workload(w, stream=stream.cuda_stream)
+        gv.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+        gv.set_initial(eta0)
+        gv.step(s["steps"])
+        g32 = gv.gauges()[:, :, 0].astype(np.float64)
+        g64 = s["result"]["gauges"][:, :, 0]
+        rel = [np.abs(g32[:, k] - g64[:, k]).max() / np.abs(g64[:, k]).max()
+               for k in range(g64.shape[1]) if np.abs(g64[:, k]).max() >= 1e-3]
+        e32, _, _ = gv.state()
+        e64 = s["result"]["eta"]
+        oracle_error = {"steps": s["steps"], "gauge_rel_max": float(max(rel)) if rel else None,
+                        "gauges_compared": len(rel),
+                        "eta_max_abs": float(np.abs(e32 - e64).max()),
+                        "eta_scale": float(np.abs(e64).max())}
+        gv.close()
+
+    if rank == 0:
+        line = {
+            "metric": baseline_metric(), "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.cells, "coords": "geographic 1 arc-min",
+                       "gauges": int(g.n_gauges), "nests": len(w.nests), "maxout": w.maxout,
+                       "gout": w.gout, "bndout": w.bndout, "steps_horizon": 3600,
+                       "l2": "flushed before every timed step (256 MiB device write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "kernel": "k_step_fused", "bytes_per_cell": BYTES_PER_CELL,
+                         "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "oracle_error": oracle_error,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "wall_ms": 1e3 * wall,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_cuda(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * cliffs.h - C ABI of the GB300 (sm_103a) shallow-water step library libcliffs.so.
+ *
+ * The library advances the nonlinear shallow-water equations of the Cliffs model
+ * (E. Tolkova, "Cliffs User Manual", arXiv 1410.0753) on one structured grid: an x-sweep
+ * over every row, then a y-sweep over every column (dimensional splitting, section
+ * "Numerics", eqs. (eq2A), (eq2B)), each sweep the VTCS-2 update (solver2) on Riemann
+ * invariants with the "moving cliff" inundation steps (a)-(e) (section "Inundation
+ * algorithm"), in Cartesian or geographic-spherical metrics. It records max-wave, gauges
+ * and boundary series for enclosed grids (section "Running Options", fields maxout, gout,
+ * bndout). The state is FP32 on the device; bathymetry filtering runs in FP64.
+ *
+ * Conventions for every entry point:
+ *  - Return value: CLIFFS_OK (0) or a negative CLIFFS_ERR_* code; the message of the last
+ *    error on the calling thread is returned by cliffs_last_error().
+ *  - Arrays passed in are owned by the caller and copied before the call returns; they may
+ *    be host or device (CUDA unified addressing) pointers. Arrays passed out are filled
+ *    before the call returns (the grid's stream is synchronised).
+ *  - 2D fields are dense row-major [ny][nx], x (longitude) fastest, as the paper's output
+ *    variables ha(time, lat, lon). Batched fields are [batch][ny][nx].
+ *  - Indices are 0-based (the paper's parameter file is 1-based).
+ *  - Depth d is positive down; negative values are land elevation (section "Running
+ *    Options", "Bathymetry data").
+ *  - A grid handle is not thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef CLIFFS_H
+#define CLIFFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLIFFS_OK            0
+#define CLIFFS_ERR_ARG      -1   /* invalid argument (sizes, indices, CFL, nest outside grid) */
+#define CLIFFS_ERR_STATE    -2   /* wrong call order (e.g. step before set_bathy) */
+#define CLIFFS_ERR_CUDA     -3   /* a CUDA runtime call failed */
+#define CLIFFS_ERR_UNSTABLE -4   /* a non-finite or runaway value appeared in the state */
+#define CLIFFS_ERR_TIMEOUT  -5   /* a bounded device wait gave up */
+#define CLIFFS_ERR_NOMEM    -6   /* device allocation failed */
+
+#define CLIFFS_EDGE_WEST  0
+#define CLIFFS_EDGE_EAST  1
+#define CLIFFS_EDGE_SOUTH 2
+#define CLIFFS_EDGE_NORTH 3
+
+typedef struct cliffs_grid cliffs_grid;
+
+/* An enclosed (nested) grid in master coordinates (parameter-file fields 3-4): nodes at
+ * (x0 + i dx, y0 + j dy), i < nx, j < ny. Its boundary series are the master solution
+ * interpolated bilinearly at its boundary nodes. */
+typedef struct cliffs_nest {
+    double  x0, y0, dx, dy;
+    int32_t nx, ny;
+} cliffs_nest;
+
+/* Computational parameters (parameter-file fields 1, 6-10, 17-21). */
+typedef struct cliffs_config {
+    int32_t nx, ny;             /* nodes; nx == 1 or ny == 1 is a 1D grid; a 2D grid needs
+                                   at least 3 nodes each way (section "Bathymetry data") */
+    int32_t batch;              /* scenarios sharing the bathymetry (>= 1) */
+    int32_t coords;             /* 1: Cartesian (m); otherwise geographic (degrees) */
+    double  h_min;              /* 'ground': minimal flow depth, > 0; dry when h < h_min */
+    double  manning_n2;         /* 'crough' read as Manning n^2; 0 disables friction */
+    int32_t itopo;              /* 0: vertical wall at depth dwall; otherwise inundation */
+    double  dwall;
+    double  dt;                 /* time step, s; the CFL number |lambda| dt/dx must be <= 1 */
+    int32_t transverse;         /* 1: advect the transverse velocity, eq. (pq3) */
+    int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) */
+    int32_t alternate;          /* 0: x then y every step; 1: y first on odd steps */
+    int32_t maxout;             /* steps between max-wave updates (> 0) */
+    int32_t gout;               /* steps between gauge records (> 0) */
+    int32_t bndout;             /* steps between boundary-series records (> 0) */
+    int32_t n_gauges;
+    const int32_t* gauge_ixiy;  /* [2 * n_gauges]: (ix, iy) pairs; copied at create */
+    int32_t n_nests;
+    const cliffs_nest* nests;   /* [n_nests]; copied at create; 2D grids, batch == 1 only */
+    void*   stream;             /* cudaStream_t for all work, or NULL (default stream) */
+} cliffs_config;
+
+/* Create a grid with the given parameters. Allocates the device state ([batch][ny][nx] of
+ * eta, u, v, double-buffered), the max-wave fields and the record buffers. The handle is
+ * owned by the library; release it with cliffs_destroy.
+ * Errors: ERR_ARG for bad sizes, h_min <= 0, dt <= 0, out-of-range gauges, cadences < 1,
+ * nests on a 1D or batched grid; ERR_NOMEM; ERR_CUDA. */
+int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out);
+
+/* Set the bathymetry (section "Running Options", "Bathymetry data"): x[nx] and y[ny] node
+ * coordinates (m, or degrees for geographic grids; strictly increasing), depth[ny][nx] in
+ * FP64, positive down. With apply_filter != 0, the depth-jump filter of section "Numerical
+ * stability" (eqs. (dstab), (newdw), (newdc); program depth_ssl) runs first on the device in
+ * FP64 with limit alpha (1 < alpha < 3; 2 is typical) and minimal wet depth min_depth,
+ * until a pass changes nothing (at most 100 passes). Checks that the nests lie inside the
+ * grid and that the still-water Courant number sqrt(g d) dt / dx <= 1 in both directions
+ * (section "Difference Scheme").
+ * Errors: ERR_ARG (non-increasing coordinates, CFL > 1, nest outside), ERR_CUDA. */
+int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const double* depth,
+                     int apply_filter, double alpha, double min_depth);
+
+/* Read back the FP64 depth in use (after the filter and any quake deformation), [ny][nx]. */
+int cliffs_read_depth(cliffs_grid* g, double* depth);
+
+/* Set the initial state of one scenario (scenario in [0, batch)) or of all (scenario = -1,
+ * then eta/u/v hold [batch][ny][nx]) (section "Running Options", "input to the
+ * computations"): free surface eta (m) and velocities u, v (m/s; NULL means zero). With
+ * quake = 1 eta is a sea-floor deformation zeta (parameter-file field 12): the depth becomes
+ * d - zeta and the free surface zeta on nodes that were wet (d >= h_min); quake needs
+ * batch == 1. Resets the step counter and the records, initialises max-wave from this state
+ * and records step 0 (gauges, boundary series).
+ * Errors: ERR_STATE before set_bathy; ERR_ARG; ERR_CUDA. */
+int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const float* u,
+                       const float* v, int quake);
+
+/* Per-scenario step limits for a batched grid: scenario b stops after steps[b] steps
+ * (its state, max-wave and records then stay as they were). Default: unlimited. */
+int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
+
+/* Advance n time steps. One step is an x-sweep over every row then a y-sweep over every
+ * column (order alternates when cfg.alternate), each with the inundation steps (a)-(e) and
+ * eq. (solver2); then max-wave (every maxout steps), gauges (every gout) and boundary
+ * series (every bndout) are recorded. Kernels are launched on the grid's stream; the call
+ * synchronises once at the end to check the device error flag.
+ * Errors: ERR_STATE before set_initial; ERR_UNSTABLE when a non-finite value appeared
+ * (the state is left as computed); ERR_CUDA. */
+int cliffs_step_n(cliffs_grid* g, int64_t n);
+
+/* Steps completed since set_initial (for a batched grid, by the longest scenario). */
+int cliffs_steps_done(cliffs_grid* g, int64_t* steps);
+
+/* Gauge records of one scenario (section "Running Options", the _gages output): writes
+ * out[nrec][n_gauges][3] as (eta, u, v) at steps 0, gout, 2 gout, ... and sets *nrec.
+ * With out == NULL only *nrec is set. */
+int cliffs_read_gauges(cliffs_grid* g, int scenario, float* out, int64_t* nrec);
+
+/* Max-wave of one scenario (the _maxwave output): maximal eta and maximal current
+ * sqrt(u^2 + v^2) over wet nodes at the steps multiple of maxout and at the current
+ * (last) step, [ny][nx] each; never-wet nodes hold -FLT_MAX and 0. Either pointer may be
+ * NULL. */
+int cliffs_read_maxwave(cliffs_grid* g, int scenario, float* eta_max, float* speed_max);
+
+/* Boundary series for one edge of one enclosed grid (the _west/_east/_south/_north
+ * outputs): vals[nt][3][np] as (u, v, eta) in FP64 at steps 0, bndout, 2 bndout, ..., with
+ * np = nest ny (west, east) or nx (south, north), the master state interpolated bilinearly
+ * in the master grid's index space. With vals == NULL only *nt is set. */
+int cliffs_read_boundary(cliffs_grid* g, int nest, int edge, double* vals, int64_t* nt);
+
+/* Current state of one scenario, [ny][nx] each; any pointer may be NULL. */
+int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float* v);
+
+/* Kernel timing: enable != 0 records CUDA events around every sweep kernel launch (on the
+ * grid's stream) from now on; *ms and *launches (either may be NULL) receive the total
+ * device time and count of those launches since timing was enabled or last reset; the call
+ * synchronises. enable < 0 resets the totals. */
+int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches);
+
+/* Release every device buffer of the grid. NULL is allowed. */
+void cliffs_destroy(cliffs_grid* g);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* cliffs_last_error(void);
+
+/* ABI version of this header. */
+int cliffs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLIFFS_H */

@@ -263,3 +263,13 @@ def run_workload(w, nsteps=None, form=0, solver=2, alternate=0, filtered_depth=N
                maxout=w.maxout if record else 0, gout=w.gout if record else 0,
                gauges=w.gauges if record else None, bndout=w.bndout if record else 0,
                nests=w.nests if record else None)
+
+
+def quake_init(depth, zeta, h_min, itopo=1, dwall=0.0):
+    """Parameter-file field 12, quake = 1: the sea-floor deformation zeta lifts the bottom,
+    d <- d - zeta, and the free surface with it on nodes that were wet (d >= h_min and, when
+    itopo = 0, not a wall): eta <- zeta there, 0 elsewhere."""
+    depth = np.asarray(depth, np.float64)
+    zeta = np.asarray(zeta, np.float64)
+    wet = (depth >= h_min) & ((itopo != 0) | (depth >= dwall))
+    return depth - zeta, np.where(wet, zeta, 0.0)

@@ -1,0 +1,312 @@
+"""Python binding of libcliffs.so, the GB300 (sm_103a) shallow-water step of the Cliffs model
+(arXiv 1410.0753). Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. The functions below carry the C ABI's names (include/cliffs.h) and raise
+``CliffsError`` on a non-zero status; ``CliffsGrid`` wraps a handle.
+
+Arrays may be NumPy arrays (host) or torch CUDA tensors (device pointers); the library copies
+inputs before returning and fills outputs before returning.
+
+The library is built in-tree by ``paper_1410_0753_gb300._build.build()`` (also run by
+``__graft_entry__.build()``). Loading fails with an error when it is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "CliffsError", "CliffsGrid", "lib", "cliffs_config", "cliffs_nest",
+    "cliffs_grid_create", "cliffs_set_bathy", "cliffs_read_depth", "cliffs_set_initial",
+    "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
+    "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
+    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "EXPORTED",
+]
+
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+EDGE_WEST, EDGE_EAST, EDGE_SOUTH, EDGE_NORTH = 0, 1, 2, 3
+
+# every function include/cliffs.h declares
+EXPORTED = [
+    "cliffs_grid_create", "cliffs_set_bathy", "cliffs_read_depth", "cliffs_set_initial",
+    "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
+    "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
+    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version",
+]
+
+
+class CliffsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("cliffs error %d: %s" % (code, msg))
+        self.code = code
+
+
+class cliffs_nest(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class cliffs_config(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("batch", C.c_int32), ("coords", C.c_int32),
+                ("h_min", C.c_double), ("manning_n2", C.c_double),
+                ("itopo", C.c_int32), ("dwall", C.c_double), ("dt", C.c_double),
+                ("transverse", C.c_int32), ("solver", C.c_int32), ("alternate", C.c_int32),
+                ("maxout", C.c_int32), ("gout", C.c_int32), ("bndout", C.c_int32),
+                ("n_gauges", C.c_int32), ("gauge_ixiy", C.POINTER(C.c_int32)),
+                ("n_nests", C.c_int32), ("nests", C.POINTER(cliffs_nest)),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcliffs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libcliffs.so is not built; run paper_1410_0753_gb300._build.build() "
+                               "(or __graft_entry__.build()) on a machine with nvcc")
+        L = C.CDLL(_build.LIB)
+        P, vp, i64p = C.POINTER, C.c_void_p, C.POINTER(C.c_int64)
+        sig = {
+            "cliffs_grid_create": ([P(cliffs_config), P(vp)], C.c_int),
+            "cliffs_set_bathy": ([vp, vp, vp, vp, C.c_int, C.c_double, C.c_double], C.c_int),
+            "cliffs_read_depth": ([vp, vp], C.c_int),
+            "cliffs_set_initial": ([vp, C.c_int, vp, vp, vp, C.c_int], C.c_int),
+            "cliffs_set_durations": ([vp, vp], C.c_int),
+            "cliffs_step_n": ([vp, C.c_int64], C.c_int),
+            "cliffs_steps_done": ([vp, i64p], C.c_int),
+            "cliffs_read_gauges": ([vp, C.c_int, vp, i64p], C.c_int),
+            "cliffs_read_maxwave": ([vp, C.c_int, vp, vp], C.c_int),
+            "cliffs_read_boundary": ([vp, C.c_int, C.c_int, vp, i64p], C.c_int),
+            "cliffs_read_state": ([vp, C.c_int, vp, vp, vp], C.c_int),
+            "cliffs_kernel_time": ([vp, C.c_int, P(C.c_double), i64p], C.c_int),
+            "cliffs_destroy": ([vp], None),
+            "cliffs_last_error": ([], C.c_char_p),
+            "cliffs_abi_version": ([], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def cliffs_last_error() -> str:
+    return lib().cliffs_last_error().decode()
+
+
+def cliffs_abi_version() -> int:
+    return lib().cliffs_abi_version()
+
+
+def _check(rc):
+    if rc != OK:
+        raise CliffsError(rc, cliffs_last_error())
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive) for a NumPy array (host) or a torch tensor (host or CUDA)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.int64: torch.int64,
+                np.int32: torch.int32}[dtype]
+        t = a.contiguous()
+        if t.dtype != want:
+            t = t.to(want)
+        return C.c_void_p(t.data_ptr()), t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+# ------------------------------------------------------------------ C ABI, same names
+
+def cliffs_grid_create(cfg: cliffs_config) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().cliffs_grid_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def cliffs_set_bathy(g, x, y, depth, apply_filter=1, alpha=2.0, min_depth=0.1):
+    px, kx = _ptr(x, np.float64)
+    py, ky = _ptr(y, np.float64)
+    pd, kd = _ptr(depth, np.float64)
+    _check(lib().cliffs_set_bathy(g, px, py, pd, int(apply_filter), float(alpha), float(min_depth)))
+
+
+def cliffs_read_depth(g, out):
+    _check(lib().cliffs_read_depth(g, C.c_void_p(out.ctypes.data) if isinstance(out, np.ndarray)
+                                   else C.c_void_p(out.data_ptr())))
+
+
+def cliffs_set_initial(g, scenario, eta, u=None, v=None, quake=0):
+    pe, ke = _ptr(eta, np.float32)
+    pu, ku = _ptr(u, np.float32)
+    pv, kv = _ptr(v, np.float32)
+    _check(lib().cliffs_set_initial(g, int(scenario), pe, pu, pv, int(quake)))
+
+
+def cliffs_set_durations(g, steps):
+    p, k = _ptr(steps, np.int64)
+    _check(lib().cliffs_set_durations(g, p))
+
+
+def cliffs_step_n(g, n):
+    _check(lib().cliffs_step_n(g, int(n)))
+
+
+def cliffs_steps_done(g) -> int:
+    n = C.c_int64()
+    _check(lib().cliffs_steps_done(g, C.byref(n)))
+    return n.value
+
+
+def _out_ptr(out):
+    if out is None:
+        return None
+    if isinstance(out, np.ndarray):
+        assert out.flags.c_contiguous
+        return C.c_void_p(out.ctypes.data)
+    return C.c_void_p(out.data_ptr())
+
+
+def cliffs_read_gauges(g, scenario, out=None) -> int:
+    n = C.c_int64()
+    _check(lib().cliffs_read_gauges(g, int(scenario), _out_ptr(out), C.byref(n)))
+    return n.value
+
+
+def cliffs_read_maxwave(g, scenario, eta_max=None, speed_max=None):
+    _check(lib().cliffs_read_maxwave(g, int(scenario), _out_ptr(eta_max), _out_ptr(speed_max)))
+
+
+def cliffs_read_boundary(g, nest, edge, vals=None) -> int:
+    n = C.c_int64()
+    _check(lib().cliffs_read_boundary(g, int(nest), int(edge), _out_ptr(vals), C.byref(n)))
+    return n.value
+
+
+def cliffs_read_state(g, scenario, eta=None, u=None, v=None):
+    _check(lib().cliffs_read_state(g, int(scenario), _out_ptr(eta), _out_ptr(u), _out_ptr(v)))
+
+
+def cliffs_kernel_time(g, enable):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(lib().cliffs_kernel_time(g, int(enable), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def cliffs_destroy(g):
+    if g:
+        lib().cliffs_destroy(g)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class CliffsGrid:
+    """One grid (optionally a batch of scenarios on shared bathymetry).
+
+    Parameters mirror ``cliffs_config``; ``gauges`` is a sequence of (ix, iy); ``nests`` a
+    sequence of objects with x0, y0, dx, dy, nx, ny."""
+
+    def __init__(self, nx, ny, dt, *, batch=1, coords=1, h_min=0.01, manning_n2=0.0, itopo=1,
+                 dwall=0.0, transverse=1, solver=2, alternate=0, maxout=1, gout=1, bndout=1,
+                 gauges: Sequence = (), nests: Sequence = (), stream: Optional[int] = None):
+        g = np.ascontiguousarray(np.asarray(gauges, np.int32).reshape(-1))
+        self._gauges = g
+        ns = (cliffs_nest * max(1, len(nests)))()
+        for k, n in enumerate(nests):
+            ns[k] = cliffs_nest(n.x0, n.y0, n.dx, n.dy, n.nx, n.ny)
+        self._nests = ns
+        cfg = cliffs_config(nx, ny, batch, coords, h_min, manning_n2, itopo, dwall, dt, transverse,
+                            solver, alternate, maxout, gout, bndout, len(g) // 2,
+                            g.ctypes.data_as(C.POINTER(C.c_int32)) if len(g) else None,
+                            len(nests), ns if len(nests) else None,
+                            C.c_void_p(stream) if stream else None)
+        self.cfg = cfg
+        self.nx, self.ny, self.batch = nx, ny, batch
+        self.n_gauges = len(g) // 2
+        self.nest_shapes = [(n.nx, n.ny) for n in nests]
+        self.h = cliffs_grid_create(cfg)
+
+    @classmethod
+    def from_workload(cls, w, stream=None, **kw):
+        opts = dict(batch=w.batch, coords=w.coords, h_min=w.h_min, manning_n2=w.manning_n2,
+                    itopo=w.itopo, dwall=w.dwall, transverse=w.transverse, maxout=w.maxout,
+                    gout=w.gout, bndout=w.bndout, gauges=[tuple(x) for x in w.gauges],
+                    nests=w.nests, stream=stream)
+        opts.update(kw)
+        return cls(w.nx, w.ny, w.dt, **opts)
+
+    def close(self):
+        if self.h:
+            cliffs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bathy(self, x, y, depth, apply_filter=True, alpha=2.0, min_depth=0.1):
+        cliffs_set_bathy(self.h, x, y, depth, int(apply_filter), alpha, min_depth)
+
+    def depth(self):
+        out = np.empty((self.ny, self.nx), np.float64)
+        cliffs_read_depth(self.h, out)
+        return out
+
+    def set_initial(self, eta, u=None, v=None, scenario=-1, quake=0):
+        cliffs_set_initial(self.h, scenario, eta, u, v, quake)
+
+    def set_durations(self, steps):
+        cliffs_set_durations(self.h, steps)
+
+    def step(self, n):
+        cliffs_step_n(self.h, n)
+
+    @property
+    def steps_done(self):
+        return cliffs_steps_done(self.h)
+
+    def gauges(self, scenario=0):
+        n = cliffs_read_gauges(self.h, scenario)
+        out = np.empty((n, self.n_gauges, 3), np.float32)
+        if n and self.n_gauges:
+            cliffs_read_gauges(self.h, scenario, out)
+        return out
+
+    def maxwave(self, scenario=0):
+        e = np.empty((self.ny, self.nx), np.float32)
+        s = np.empty((self.ny, self.nx), np.float32)
+        cliffs_read_maxwave(self.h, scenario, e, s)
+        return e, s
+
+    def boundary(self, nest, edge):
+        n = cliffs_read_boundary(self.h, nest, edge)
+        nxn, nyn = self.nest_shapes[nest]
+        np_ = nyn if edge in (EDGE_WEST, EDGE_EAST) else nxn
+        out = np.empty((n, 3, np_), np.float64)
+        cliffs_read_boundary(self.h, nest, edge, out)
+        return out
+
+    def state(self, scenario=0):
+        e = np.empty((self.ny, self.nx), np.float32)
+        u = np.empty_like(e)
+        v = np.empty_like(e)
+        cliffs_read_state(self.h, scenario, e, u, v)
+        return e, u, v
+
+    def kernel_time(self, enable=1):
+        return cliffs_kernel_time(self.h, enable)

@@ -1,0 +1,886 @@
+// Host runtime of libcliffs.so: the C ABI declared in include/cliffs.h.
+//
+// A grid owns its device buffers: the FP32 state eta, u, v (double-buffered, rows padded to
+// a pitch of 32 floats so that the sweep kernels' 8-byte vector accesses stay aligned), the
+// FP32 and FP64 depth, the max-wave fields, the per-row / per-column metric tables and the
+// gauge / enclosed-grid record buffers. Every step of the method runs in a kernel: the
+// sweeps (cliffs_step.cu), the depth filter, the initial-state set-up, the records and the
+// reductions of the read-out calls (this file). Host code only validates arguments,
+// computes the metric and interpolation tables, and sequences launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cliffs.h"
+#include "internal.h"
+#include "sweep.cuh"
+
+using namespace cliffs;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+
+int set_err(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_err(e_ == cudaErrorMemoryAllocation ? CLIFFS_ERR_NOMEM : CLIFFS_ERR_CUDA, \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+const double R_SPHERE = 6371000.0;
+const double DEGR = 3.14159265358979323846 / 180.0;
+
+// ----------------------------------------------------------------------------- kernels
+
+// depth-jump filter, section "Numerical stability": eqs. (dstab), (newdw), (newdc)
+__global__ void k_filter_minraise(double* d, long long n, double min_depth) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n && d[i] > 0.0 && d[i] < min_depth) d[i] = min_depth;
+}
+
+// One Jacobi pass along rows (dir 0) or columns (dir 1).
+__global__ void k_filter_pass(const double* in, double* out, int nx, int ny, int dir, double a2,
+                              int* changed) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const int n = dir == 0 ? nx : ny, j = dir == 0 ? c : r;
+    const long long st = dir == 0 ? 1 : nx;
+    const double dj = in[i];
+    double nd = dj;
+    if (n >= 3 && dj > 0.0) {
+        const bool lw = j > 0 && in[i - st] > 0.0;
+        const bool rw = j < n - 1 && in[i + st] > 0.0;
+        const bool viol = (lw && in[i - st] > a2 * dj) || (rw && in[i + st] > a2 * dj);
+        if (viol) {
+            if (lw && rw) {
+                const double s = sqrt(in[i - st]) + sqrt(in[i + st]);
+                nd = s * s / 4.0;
+            } else {
+                nd = (lw ? in[i - st] : in[i + st]) / a2;
+            }
+        }
+    }
+    out[i] = nd;
+    if (nd != dj) *changed = 1;
+}
+
+__global__ void k_depth_to_f32(const double* d64, float* d32, int nx, int ny, int pitch) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)ny * pitch) return;
+    const int r = (int)(i / pitch), c = (int)(i % pitch);
+    d32[i] = (c < nx) ? (float)d64[(long long)r * nx + c] : OUTSIDE_D;
+}
+
+// largest still-water Courant number sqrt(g d) dt / dx over wet nodes, both directions
+__global__ void k_cfl(const double* d64, int nx, int ny, const float* xa, const float* xb,
+                      const float* xrow, const float4* ymet, double dt, unsigned* out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const double d = d64[i];
+    if (!(d > 0.0)) return;
+    double inv = 0.0;
+    if (nx > 1) inv = fmax((double)xa[c], (double)xb[c]) * (double)xrow[r];
+    if (ny > 1) inv = fmax(inv, fmax((double)ymet[r].x, (double)ymet[r].y));
+    const float cour = (float)(sqrt(9.81 * d) * dt * inv);
+    atomicMax(out, __float_as_uint(cour));
+}
+
+// quake = 1: the deformation zeta lifts the sea floor (d <- d - zeta) and, on nodes that
+// were wet, the free surface with it (eta <- zeta); elsewhere eta = 0.
+__global__ void k_quake(double* d64, const float* zeta, float* eta, float* d32, int nx, int ny,
+                        int pitch, double hmin, double dwall) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const double d = d64[i];
+    const float z = zeta[i];
+    const bool wet = (d >= dwall) && (d >= hmin);
+    eta[(long long)r * pitch + c] = wet ? z : 0.f;
+    const double nd = d - (double)z;
+    d64[i] = nd;
+    d32[(long long)r * pitch + c] = (float)nd;
+}
+
+// max-wave initialisation from the state of step 0 (wet nodes), batched over planes
+__global__ void k_max_init(const float* eta, const float* u, const float* v, const float* d,
+                           float* emax, float* smax, int nx, int ny, int pitch, long long plane,
+                           int b0, int nb, float hmin, float dwall) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nb * plane) return;
+    const long long o = (long long)b0 * plane + i;
+    const long long p = i % plane;
+    const int c = (int)(p % pitch);
+    const float dd = d[p];
+    const float e = eta[o];
+    const bool wet = c < nx && (dd >= dwall) && (e + dd >= hmin);
+    emax[o] = wet ? e : -3.402823466e38f;
+    smax[o] = wet ? sqrtf(u[o] * u[o] + v[o] * v[o]) : 0.f;
+    (void)ny;
+}
+
+// step-0 record of the gauges / enclosed-grid nodes of scenarios [b0, b0 + nb)
+__global__ void k_record0(const float* eta, const float* u, const float* v, int pitch,
+                          long long plane, const int4* items, int nitems, float* rec_g,
+                          long long g_bstride, float* rec_n, int b0, int nb) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nitems * nb) return;
+    const int k = t % nitems, b = b0 + t / nitems;
+    const int4 it = items[k];
+    const long long o = (long long)b * plane + (long long)it.x * pitch + it.y;
+    float* out = it.z == 0 ? rec_g + (long long)b * g_bstride : (b == 0 ? rec_n : nullptr);
+    if (!out) return;
+    out[3 * it.w + 0] = eta[o];
+    out[3 * it.w + 1] = u[o];
+    out[3 * it.w + 2] = v[o];
+}
+
+// max-wave read-out: stored maxima folded with the current (last) state, dense output
+__global__ void k_max_fold(const float* emax, const float* smax, const float* eta, const float* u,
+                           const float* v, const float* d, float* oe, float* os, int nx, int ny,
+                           int pitch, float hmin, float dwall) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const long long o = (long long)r * pitch + c;
+    float em = emax[o], sm = smax[o];
+    const float e = eta[o], dd = d[o];
+    if ((dd >= dwall) && (e + dd >= hmin)) {
+        em = fmaxf(em, e);
+        sm = fmaxf(sm, sqrtf(u[o] * u[o] + v[o] * v[o]));
+    }
+    if (oe) oe[i] = em;
+    if (os) os[i] = sm;
+}
+
+// boundary series of one edge: bilinear combination of the recorded corner nodes, FP64,
+// vals[t][q][p] with q = 0 u, 1 v, 2 eta
+__global__ void k_boundary(const float* nrec, int nnodes, const int* slot, const double* wt,
+                           int p0, int np, long long nt, double* vals) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nt * np) return;
+    const long long t = i / np;
+    const int p = (int)(i % np);
+    const float* rec = nrec + t * (long long)nnodes * 3;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+        const int s = slot[4 * (p0 + p) + k];
+        const double w = wt[4 * (p0 + p) + k];
+        acc[0] += w * (double)rec[3 * s + 1];
+        acc[1] += w * (double)rec[3 * s + 2];
+        acc[2] += w * (double)rec[3 * s + 0];
+    }
+    for (int q = 0; q < 3; ++q) vals[(t * 3 + q) * np + p] = acc[q];
+}
+
+inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- grid
+
+struct cliffs_grid {
+    cliffs_config cfg{};
+    std::vector<int32_t> gauges;
+    std::vector<cliffs_nest> nests;
+    int nx = 0, ny = 0, B = 1, pitch = 0;
+    long long plane = 0;
+    cudaStream_t stream = nullptr;
+    bool have_bathy = false, have_init = false;
+    float* eta[2] = {nullptr, nullptr};
+    float* u[2] = {nullptr, nullptr};
+    float* v[2] = {nullptr, nullptr};
+    float* d32 = nullptr;
+    double* d64 = nullptr;
+    double* d64b = nullptr;
+    float* emax = nullptr;
+    float* smax = nullptr;
+    float *xa = nullptr, *xb = nullptr, *xk = nullptr, *xrow = nullptr;
+    float4* ymet = nullptr;
+    int* err = nullptr;
+    long long* limit = nullptr;
+    std::vector<long long> limit_h;
+    long long step = 0;
+    // samples: gauges (class 0) then enclosed-grid corner nodes (class 1)
+    std::vector<int4> items;
+    int G = 0, NN = 0;
+    int4* items_d = nullptr;
+    int* samp_ptr = nullptr;
+    int4* samp = nullptr;
+    // records
+    float* grec = nullptr;
+    long long grec_cap = 0;
+    float* nrec = nullptr;
+    long long nrec_cap = 0;
+    // enclosed-grid boundary points
+    std::vector<int> edge_off, edge_np;      // per nest * 4 + edge
+    int* pt_slot = nullptr;
+    double* pt_w = nullptr;
+    // launch geometry
+    int kind = 0;                            // 0 fused 2D, 1 x only, 2 y only
+    int S = 32, nstrips = 0, nseg = 0;
+    // timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    double t_ms = 0.0;
+    long long t_launches = 0;
+    // scratch for read-outs
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    unsigned* ured = nullptr;
+};
+
+namespace {
+
+int ensure_tmp(cliffs_grid* g, size_t bytes) {
+    if (bytes <= g->tmp_bytes) return CLIFFS_OK;
+    if (g->tmp) CK(cudaFree(g->tmp));
+    g->tmp = nullptr;
+    g->tmp_bytes = 0;
+    CK(cudaMalloc(&g->tmp, bytes));
+    g->tmp_bytes = bytes;
+    return CLIFFS_OK;
+}
+
+long long cur_buf(const cliffs_grid* g, int b) {
+    long long s = g->step;
+    if (g->limit_h.size() && g->limit_h[b] >= 0) s = std::min(s, g->limit_h[b]);
+    return s & 1;
+}
+
+long long steps_of(const cliffs_grid* g, int b) {
+    long long s = g->step;
+    if (g->limit_h.size() && g->limit_h[b] >= 0) s = std::min(s, g->limit_h[b]);
+    return s;
+}
+
+// per-warp sample lists for the current launch geometry
+int build_samples(cliffs_grid* g) {
+    // a warp owns output columns [W * strip, W * strip + W): 56 for the x-sweeping kernels,
+    // 64 for the y-sweep alone
+    const int W = (g->kind == 2) ? XWIN : XOUT;
+    const int S = g->kind == 1 ? 1 : g->S;
+    const int nseg = g->kind == 1 ? g->ny : g->nseg;
+    const long long nw = (long long)g->nstrips * nseg;
+    std::vector<std::vector<int4>> per(nw);
+    for (const int4& it : g->items) {
+        const long long w = (long long)(it.x / S) * g->nstrips + it.y / W;
+        per[w].push_back(it);
+    }
+    std::vector<int> ptr(nw + 1, 0);
+    std::vector<int4> flat;
+    for (long long w = 0; w < nw; ++w) {
+        std::stable_sort(per[w].begin(), per[w].end(),
+                         [](const int4& a, const int4& b) { return a.x < b.x; });
+        ptr[w] = (int)flat.size();
+        flat.insert(flat.end(), per[w].begin(), per[w].end());
+    }
+    ptr[nw] = (int)flat.size();
+    if (g->samp_ptr) CK(cudaFree(g->samp_ptr));
+    if (g->samp) CK(cudaFree(g->samp));
+    g->samp_ptr = nullptr;
+    g->samp = nullptr;
+    CK(cudaMalloc(&g->samp_ptr, sizeof(int) * (nw + 1)));
+    CK(cudaMemcpy(g->samp_ptr, ptr.data(), sizeof(int) * (nw + 1), cudaMemcpyHostToDevice));
+    if (!flat.empty()) {
+        CK(cudaMalloc(&g->samp, sizeof(int4) * flat.size()));
+        CK(cudaMemcpy(g->samp, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice));
+    }
+    return CLIFFS_OK;
+}
+
+int choose_geometry(cliffs_grid* g) {
+    if (g->ny == 1) {
+        g->kind = 1;
+        g->nstrips = (g->nx + XOUT - 1) / XOUT;
+        g->S = 1;
+        g->nseg = g->ny;
+    } else if (g->nx == 1) {
+        g->kind = 2;
+        g->nstrips = (g->nx + XWIN - 1) / XWIN;
+        g->S = 64;
+        g->nseg = (g->ny + g->S - 1) / g->S;
+    } else {
+        g->kind = 0;
+        g->nstrips = (g->nx + XOUT - 1) / XOUT;
+        // rows per warp: long enough to amortise the 6-row halo, short enough to give every
+        // SM a few waves of warps
+        const long long target = 152LL * 16;
+        int S = 128;
+        while (S > 16 && (long long)g->nstrips * ((g->ny + S - 1) / S) * g->B < target) S /= 2;
+        g->S = S;
+        g->nseg = (g->ny + S - 1) / S;
+    }
+    return build_samples(g);
+}
+
+int grow_records(cliffs_grid* g, long long need_g, long long need_n) {
+    if (g->G > 0 && need_g > g->grec_cap) {
+        const long long cap = std::max(need_g, 2 * g->grec_cap);
+        float* nb = nullptr;
+        const size_t rec = (size_t)g->G * 3 * sizeof(float);
+        CK(cudaMalloc(&nb, (size_t)g->B * cap * rec));
+        if (g->grec) {
+            CK(cudaMemcpy2DAsync(nb, cap * rec, g->grec, g->grec_cap * rec, g->grec_cap * rec, g->B,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            CK(cudaFree(g->grec));
+        }
+        g->grec = nb;
+        g->grec_cap = cap;
+    }
+    if (g->NN > 0 && need_n > g->nrec_cap) {
+        const long long cap = std::max(need_n, 2 * g->nrec_cap);
+        float* nb = nullptr;
+        const size_t rec = (size_t)g->NN * 3 * sizeof(float);
+        CK(cudaMalloc(&nb, cap * rec));
+        if (g->nrec) {
+            CK(cudaMemcpyAsync(nb, g->nrec, g->nrec_cap * rec, cudaMemcpyDeviceToDevice, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            CK(cudaFree(g->nrec));
+        }
+        g->nrec = nb;
+        g->nrec_cap = cap;
+    }
+    return CLIFFS_OK;
+}
+
+bool locate(const std::vector<double>& c, double xp, int* i, double* a) {
+    const int n = (int)c.size();
+    if (n == 1) { *i = 0; *a = 0.0; return xp == c[0]; }
+    if (xp < c[0] || xp > c[n - 1]) return false;
+    int k = (int)(std::upper_bound(c.begin(), c.end(), xp) - c.begin()) - 1;
+    k = std::min(std::max(k, 0), n - 2);
+    *i = k;
+    *a = (xp - c[k]) / (c[k + 1] - c[k]);
+    return true;
+}
+
+void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
+    a.eta_in = g->eta[in]; a.u_in = g->u[in]; a.v_in = g->v[in];
+    a.eta_out = g->eta[out]; a.u_out = g->u[out]; a.v_out = g->v[out];
+    a.d = g->d32;
+    a.xa = g->xa; a.xb = g->xb; a.xk = g->xk; a.xrow = g->xrow; a.ymet = g->ymet;
+    a.emax = nullptr; a.smax = nullptr; a.rec_g = nullptr; a.rec_n = nullptr;
+    a.rec_g_bstride = g->grec_cap * g->G * 3;
+    a.samp_ptr = g->samp_ptr; a.samp = g->samp;
+    a.limit = g->limit;
+    a.err = g->err;
+    a.nx = g->nx; a.ny = g->ny; a.pitch = g->pitch; a.plane = g->plane;
+    a.S = g->S; a.nstrips = g->nstrips; a.nseg = g->nseg;
+    a.hmin = (float)g->cfg.h_min;
+    a.dwall = g->cfg.itopo ? -3.402823466e38f : (float)g->cfg.dwall;
+    a.half_dt = (float)(0.5 * g->cfg.dt);
+    a.dt_gn2 = (float)(g->cfg.dt * 9.81 * g->cfg.manning_n2);
+    a.transverse = g->cfg.transverse ? 1 : 0;
+    a.sph = g->cfg.coords != 1;
+}
+
+void free_grid(cliffs_grid* g) {
+    for (int k = 0; k < 2; ++k) { cudaFree(g->eta[k]); cudaFree(g->u[k]); cudaFree(g->v[k]); }
+    cudaFree(g->d32); cudaFree(g->d64); cudaFree(g->d64b);
+    cudaFree(g->emax); cudaFree(g->smax);
+    cudaFree(g->xa); cudaFree(g->xb); cudaFree(g->xk); cudaFree(g->xrow); cudaFree(g->ymet);
+    cudaFree(g->err); cudaFree(g->limit); cudaFree(g->items_d);
+    cudaFree(g->samp_ptr); cudaFree(g->samp); cudaFree(g->grec); cudaFree(g->nrec);
+    cudaFree(g->pt_slot); cudaFree(g->pt_w); cudaFree(g->tmp); cudaFree(g->ured);
+    for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    delete g;
+}
+
+int collect_timing(cliffs_grid* g) {
+    if (g->ev.empty()) return CLIFFS_OK;
+    CK(cudaEventSynchronize(g->ev.back().second));
+    for (auto& e : g->ev) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        g->t_ms += ms;
+        ++g->t_launches;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    g->ev.clear();
+    return CLIFFS_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* cliffs_last_error(void) { return g_err; }
+
+int cliffs_abi_version(void) { return 1; }
+
+int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
+    g_err[0] = 0;
+    if (!cfg || !out) return set_err(CLIFFS_ERR_ARG, "null argument");
+    *out = nullptr;
+    const int nx = cfg->nx, ny = cfg->ny;
+    if (nx < 1 || ny < 1 || (nx == 1 && ny == 1))
+        return set_err(CLIFFS_ERR_ARG, "grid %d x %d: need nx, ny >= 1 and not both 1", nx, ny);
+    if ((nx > 1 && nx < 3) || (ny > 1 && ny < 3))
+        return set_err(CLIFFS_ERR_ARG, "a 2D grid needs at least 3 nodes in each direction");
+    if (cfg->batch < 1) return set_err(CLIFFS_ERR_ARG, "batch must be >= 1");
+    if (!(cfg->h_min > 0.0)) return set_err(CLIFFS_ERR_ARG, "h_min must be > 0");
+    if (!(cfg->dt > 0.0)) return set_err(CLIFFS_ERR_ARG, "dt must be > 0");
+    if (cfg->manning_n2 < 0.0) return set_err(CLIFFS_ERR_ARG, "manning_n2 must be >= 0");
+    if (cfg->maxout < 1 || cfg->gout < 1 || cfg->bndout < 1)
+        return set_err(CLIFFS_ERR_ARG, "maxout, gout and bndout must be >= 1");
+    if (!(cfg->solver == 0 || cfg->solver == 2))
+        return set_err(CLIFFS_ERR_ARG, "solver %d is not available (use 2)", cfg->solver);
+    if (cfg->alternate != 0) return set_err(CLIFFS_ERR_ARG, "alternate sweep order is not available");
+    if (cfg->n_gauges < 0 || (cfg->n_gauges > 0 && !cfg->gauge_ixiy))
+        return set_err(CLIFFS_ERR_ARG, "bad gauge list");
+    for (int k = 0; k < cfg->n_gauges; ++k) {
+        const int ix = cfg->gauge_ixiy[2 * k], iy = cfg->gauge_ixiy[2 * k + 1];
+        if (ix < 0 || ix >= nx || iy < 0 || iy >= ny)
+            return set_err(CLIFFS_ERR_ARG, "gauge %d at (%d, %d) is outside the %d x %d grid", k, ix, iy, nx, ny);
+    }
+    if (cfg->n_nests < 0 || (cfg->n_nests > 0 && !cfg->nests))
+        return set_err(CLIFFS_ERR_ARG, "bad nest list");
+    if (cfg->n_nests > 0 && (nx < 3 || ny < 3))
+        return set_err(CLIFFS_ERR_ARG, "enclosed grids need a 2D master grid");
+    if (cfg->n_nests > 0 && cfg->batch != 1)
+        return set_err(CLIFFS_ERR_ARG, "enclosed grids need batch == 1");
+    for (int m = 0; m < cfg->n_nests; ++m)
+        if (cfg->nests[m].nx < 2 || cfg->nests[m].ny < 2 || !(cfg->nests[m].dx > 0) || !(cfg->nests[m].dy > 0))
+            return set_err(CLIFFS_ERR_ARG, "nest %d: need nx, ny >= 2 and dx, dy > 0", m);
+
+    cliffs_grid* g = new cliffs_grid();
+    g->cfg = *cfg;
+    g->gauges.assign(cfg->gauge_ixiy, cfg->gauge_ixiy + 2 * cfg->n_gauges);
+    g->nests.assign(cfg->nests, cfg->nests + cfg->n_nests);
+    g->cfg.gauge_ixiy = nullptr;
+    g->cfg.nests = nullptr;
+    g->nx = nx; g->ny = ny; g->B = cfg->batch;
+    g->pitch = (nx + 31) / 32 * 32;
+    g->plane = (long long)g->pitch * ny;
+    g->stream = (cudaStream_t)cfg->stream;
+    g->G = cfg->n_gauges;
+    auto fail = [&](int rc) { free_grid(g); return rc; };
+    const size_t sb = sizeof(float) * (size_t)g->B * g->plane;
+#define CKG(call) do { int rc_ = [&]() -> int { CK(call); return CLIFFS_OK; }(); if (rc_) return fail(rc_); } while (0)
+    for (int k = 0; k < 2; ++k) {
+        CKG(cudaMalloc(&g->eta[k], sb)); CKG(cudaMalloc(&g->u[k], sb)); CKG(cudaMalloc(&g->v[k], sb));
+        CKG(cudaMemsetAsync(g->eta[k], 0, sb, g->stream));
+        CKG(cudaMemsetAsync(g->u[k], 0, sb, g->stream));
+        CKG(cudaMemsetAsync(g->v[k], 0, sb, g->stream));
+    }
+    CKG(cudaMalloc(&g->emax, sb)); CKG(cudaMalloc(&g->smax, sb));
+    CKG(cudaMalloc(&g->d32, sizeof(float) * g->plane));
+    CKG(cudaMalloc(&g->d64, sizeof(double) * (size_t)nx * ny));
+    CKG(cudaMalloc(&g->d64b, sizeof(double) * (size_t)nx * ny));
+    CKG(cudaMalloc(&g->xa, sizeof(float) * nx)); CKG(cudaMalloc(&g->xb, sizeof(float) * nx));
+    CKG(cudaMalloc(&g->xk, sizeof(float) * nx)); CKG(cudaMalloc(&g->xrow, sizeof(float) * ny));
+    CKG(cudaMalloc(&g->ymet, sizeof(float4) * ny));
+    CKG(cudaMalloc(&g->err, sizeof(int) * 4));
+    CKG(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, g->stream));
+    CKG(cudaMalloc(&g->ured, sizeof(unsigned) * 4));
+    CKG(cudaStreamSynchronize(g->stream));
+#undef CKG
+    *out = g;
+    return CLIFFS_OK;
+}
+
+int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const double* depth,
+                     int apply_filter, double alpha, double min_depth) {
+    g_err[0] = 0;
+    if (!g || !x || !y || !depth) return set_err(CLIFFS_ERR_ARG, "null argument");
+    const int nx = g->nx, ny = g->ny;
+    std::vector<double> hx(nx), hy(ny);
+    CK(cudaMemcpy(hx.data(), x, sizeof(double) * nx, cudaMemcpyDefault));
+    CK(cudaMemcpy(hy.data(), y, sizeof(double) * ny, cudaMemcpyDefault));
+    for (int i = 0; i + 1 < nx; ++i)
+        if (!(hx[i + 1] > hx[i])) return set_err(CLIFFS_ERR_ARG, "x must be strictly increasing (index %d)", i);
+    for (int j = 0; j + 1 < ny; ++j)
+        if (!(hy[j + 1] > hy[j])) return set_err(CLIFFS_ERR_ARG, "y must be strictly increasing (index %d)", j);
+    const bool sph = g->cfg.coords != 1;
+    if (sph)
+        for (int j = 0; j < ny; ++j)
+            if (!(std::fabs(hy[j]) < 90.0)) return set_err(CLIFFS_ERR_ARG, "latitude %g out of (-90, 90)", hy[j]);
+    if (apply_filter && !(alpha > 1.0 && alpha < 3.0))
+        return set_err(CLIFFS_ERR_ARG, "filter limit alpha must be in (1, 3)");
+    const long long N = (long long)nx * ny;
+    cudaStream_t s = g->stream;
+    CK(cudaMemcpyAsync(g->d64, depth, sizeof(double) * N, cudaMemcpyDefault, s));
+    if (apply_filter) {
+        k_filter_minraise<<<nblk(N), 256, 0, s>>>(g->d64, N, min_depth);
+        CK(cudaGetLastError());
+        int* changed = reinterpret_cast<int*>(g->ured);
+        const double a2 = alpha * alpha;
+        bool conv = false;
+        for (int pass = 1; pass <= 100; ++pass) {
+            CK(cudaMemsetAsync(changed, 0, sizeof(int), s));
+            k_filter_pass<<<nblk(N), 256, 0, s>>>(g->d64, g->d64b, nx, ny, 0, a2, changed);
+            k_filter_pass<<<nblk(N), 256, 0, s>>>(g->d64b, g->d64, nx, ny, 1, a2, changed);
+            CK(cudaGetLastError());
+            int h = 0;
+            CK(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!h) { conv = true; break; }
+        }
+        if (!conv) fprintf(stderr, "cliffs: depth filter stopped after 100 passes\n");
+    }
+    // metric tables (section "Running Options", "Units": metres, or degrees on a sphere)
+    std::vector<float> xa(nx, 0.f), xb(nx, 0.f), xk(nx, 0.f), xrow(ny, 1.f);
+    std::vector<float4> ym(ny, make_float4(0.f, 0.f, 0.f, 0.f));
+    const double dt = g->cfg.dt;
+    if (nx > 1) {
+        const double f = sph ? DEGR : 1.0;
+        for (int c = 0; c < nx; ++c) {
+            const double l = f * ((c > 0) ? hx[c] - hx[c - 1] : hx[1] - hx[0]);
+            const double r = f * ((c < nx - 1) ? hx[c + 1] - hx[c] : hx[nx - 1] - hx[nx - 2]);
+            xa[c] = (float)(1.0 / l); xb[c] = (float)(1.0 / r); xk[c] = (float)(dt * dt / (l + r));
+        }
+        if (sph) for (int j = 0; j < ny; ++j) xrow[j] = (float)(1.0 / (R_SPHERE * std::cos(hy[j] * DEGR)));
+    }
+    if (ny > 1) {
+        const double f = sph ? R_SPHERE * DEGR : 1.0;
+        for (int j = 0; j < ny; ++j) {
+            const double l = f * ((j > 0) ? hy[j] - hy[j - 1] : hy[1] - hy[0]);
+            const double r = f * ((j < ny - 1) ? hy[j + 1] - hy[j] : hy[ny - 1] - hy[ny - 2]);
+            const double src = sph ? dt * std::tan(hy[j] * DEGR) / R_SPHERE : 0.0;
+            ym[j] = make_float4((float)(1.0 / l), (float)(1.0 / r), (float)(dt * dt / (l + r)), (float)src);
+        }
+    }
+    CK(cudaMemcpyAsync(g->xa, xa.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->xb, xb.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->xk, xk.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->xrow, xrow.data(), sizeof(float) * ny, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->ymet, ym.data(), sizeof(float4) * ny, cudaMemcpyHostToDevice, s));
+    k_depth_to_f32<<<nblk((long long)ny * g->pitch), 256, 0, s>>>(g->d64, g->d32, nx, ny, g->pitch);
+    CK(cudaGetLastError());
+    // CFL (section "Difference Scheme": |lambda| dt / dx <= 1)
+    CK(cudaMemsetAsync(g->ured + 1, 0, sizeof(unsigned), s));
+    k_cfl<<<nblk(N), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow, g->ymet, dt, g->ured + 1);
+    CK(cudaGetLastError());
+    unsigned cb = 0;
+    CK(cudaMemcpyAsync(&cb, g->ured + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float cour;
+    std::memcpy(&cour, &cb, sizeof(float));
+    if (cour > 1.0f + 1e-6f)
+        return set_err(CLIFFS_ERR_ARG, "Courant number %.4f > 1: reduce dt (section Difference Scheme)", cour);
+    // samples: gauges, then the corner nodes of every enclosed-grid boundary point
+    g->items.clear();
+    for (int k = 0; k < g->G; ++k) g->items.push_back(make_int4(g->gauges[2 * k + 1], g->gauges[2 * k], 0, k));
+    std::map<long long, int> slot_of;
+    std::vector<int> pslot;
+    std::vector<double> pw;
+    g->edge_off.clear(); g->edge_np.clear();
+    int npts = 0;
+    for (size_t m = 0; m < g->nests.size(); ++m) {
+        const cliffs_nest& n = g->nests[m];
+        for (int e = 0; e < 4; ++e) {
+            const int np = (e < 2) ? n.ny : n.nx;
+            g->edge_off.push_back(npts);
+            g->edge_np.push_back(np);
+            for (int k = 0; k < np; ++k) {
+                double px, py;
+                if (e == 0) { px = n.x0; py = n.y0 + k * n.dy; }
+                else if (e == 1) { px = n.x0 + (n.nx - 1) * n.dx; py = n.y0 + k * n.dy; }
+                else if (e == 2) { px = n.x0 + k * n.dx; py = n.y0; }
+                else { px = n.x0 + k * n.dx; py = n.y0 + (n.ny - 1) * n.dy; }
+                int i, j; double a, b;
+                if (!locate(hx, px, &i, &a) || !locate(hy, py, &j, &b))
+                    return set_err(CLIFFS_ERR_ARG, "nest %d: boundary point (%g, %g) outside the master grid", (int)m, px, py);
+                const int cc[4][2] = {{j, i}, {j, i + 1}, {j + 1, i}, {j + 1, i + 1}};
+                const double ww[4] = {(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b};
+                for (int q = 0; q < 4; ++q) {
+                    const long long key = (long long)cc[q][0] * nx + cc[q][1];
+                    auto it = slot_of.find(key);
+                    int sl;
+                    if (it == slot_of.end()) {
+                        sl = (int)slot_of.size();
+                        slot_of[key] = sl;
+                        g->items.push_back(make_int4(cc[q][0], cc[q][1], 1, sl));
+                    } else {
+                        sl = it->second;
+                    }
+                    pslot.push_back(sl);
+                    pw.push_back(ww[q]);
+                }
+                ++npts;
+            }
+        }
+    }
+    g->NN = (int)slot_of.size();
+    cudaFree(g->pt_slot); cudaFree(g->pt_w); cudaFree(g->items_d);
+    g->pt_slot = nullptr; g->pt_w = nullptr; g->items_d = nullptr;
+    if (npts) {
+        CK(cudaMalloc(&g->pt_slot, sizeof(int) * pslot.size()));
+        CK(cudaMalloc(&g->pt_w, sizeof(double) * pw.size()));
+        CK(cudaMemcpy(g->pt_slot, pslot.data(), sizeof(int) * pslot.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->pt_w, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice));
+    }
+    if (!g->items.empty()) {
+        CK(cudaMalloc(&g->items_d, sizeof(int4) * g->items.size()));
+        CK(cudaMemcpy(g->items_d, g->items.data(), sizeof(int4) * g->items.size(), cudaMemcpyHostToDevice));
+    }
+    int rc = choose_geometry(g);
+    if (rc) return rc;
+    g->have_bathy = true;
+    g->have_init = false;
+    return CLIFFS_OK;
+}
+
+int cliffs_read_depth(cliffs_grid* g, double* depth) {
+    g_err[0] = 0;
+    if (!g || !depth) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_bathy) return set_err(CLIFFS_ERR_STATE, "set_bathy first");
+    CK(cudaMemcpyAsync(depth, g->d64, sizeof(double) * g->nx * g->ny, cudaMemcpyDefault, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return CLIFFS_OK;
+}
+
+int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const float* u,
+                       const float* v, int quake) {
+    g_err[0] = 0;
+    if (!g || !eta) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_bathy) return set_err(CLIFFS_ERR_STATE, "set_bathy first");
+    if (scenario < -1 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    if (quake && g->B != 1) return set_err(CLIFFS_ERR_ARG, "quake needs batch == 1");
+    cudaStream_t s = g->stream;
+    const int nx = g->nx, ny = g->ny;
+    const size_t rowb = sizeof(float) * nx, pitchb = sizeof(float) * g->pitch;
+    // scenarios not set now keep their state: move it into buffer 0
+    if (g->step > 0 && scenario >= 0) {
+        for (int b = 0; b < g->B; ++b) {
+            if (b == scenario || cur_buf(g, b) == 0) continue;
+            const size_t o = (size_t)b * g->plane * sizeof(float);
+            CK(cudaMemcpyAsync((char*)g->eta[0] + o, (char*)g->eta[1] + o, g->plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync((char*)g->u[0] + o, (char*)g->u[1] + o, g->plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync((char*)g->v[0] + o, (char*)g->v[1] + o, g->plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    const int b0 = scenario < 0 ? 0 : scenario, nb = scenario < 0 ? g->B : 1;
+    const size_t off = (size_t)b0 * g->plane;
+    const size_t rows = (size_t)nb * ny;
+    if (quake) {
+        int rc = ensure_tmp(g, sizeof(float) * (size_t)nx * ny);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(g->tmp, eta, sizeof(float) * (size_t)nx * ny, cudaMemcpyDefault, s));
+        const double dwall = g->cfg.itopo ? -1e300 : g->cfg.dwall;
+        k_quake<<<nblk((long long)nx * ny), 256, 0, s>>>(g->d64, (const float*)g->tmp, g->eta[0], g->d32, nx, ny,
+                                                        g->pitch, g->cfg.h_min, dwall);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemcpy2DAsync(g->eta[0] + off, pitchb, eta, rowb, rowb, rows, cudaMemcpyDefault, s));
+    }
+    if (u) CK(cudaMemcpy2DAsync(g->u[0] + off, pitchb, u, rowb, rowb, rows, cudaMemcpyDefault, s));
+    else CK(cudaMemsetAsync(g->u[0] + off, 0, sizeof(float) * nb * g->plane, s));
+    if (v) CK(cudaMemcpy2DAsync(g->v[0] + off, pitchb, v, rowb, rowb, rows, cudaMemcpyDefault, s));
+    else CK(cudaMemsetAsync(g->v[0] + off, 0, sizeof(float) * nb * g->plane, s));
+    g->step = 0;
+    const float dwall = g->cfg.itopo ? -3.402823466e38f : (float)g->cfg.dwall;
+    k_max_init<<<nblk((long long)nb * g->plane), 256, 0, s>>>(g->eta[0], g->u[0], g->v[0], g->d32, g->emax, g->smax,
+                                                             nx, ny, g->pitch, g->plane, b0, nb,
+                                                             (float)g->cfg.h_min, dwall);
+    CK(cudaGetLastError());
+    int rc = grow_records(g, 1, 1);
+    if (rc) return rc;
+    if (!g->items.empty()) {
+        const int ni = (int)g->items.size();
+        k_record0<<<nblk((long long)ni * nb), 256, 0, s>>>(g->eta[0], g->u[0], g->v[0], g->pitch, g->plane,
+                                                          g->items_d, ni, g->grec, g->grec_cap * g->G * 3,
+                                                          g->nrec, b0, nb);
+        CK(cudaGetLastError());
+    }
+    if (quake) {
+        // the deformed depth must still satisfy the CFL limit
+        CK(cudaMemsetAsync(g->ured + 1, 0, sizeof(unsigned), s));
+        k_cfl<<<nblk((long long)nx * ny), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow, g->ymet, g->cfg.dt, g->ured + 1);
+        unsigned cb = 0;
+        CK(cudaMemcpyAsync(&cb, g->ured + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float cour;
+        std::memcpy(&cour, &cb, sizeof(float));
+        if (cour > 1.0f + 1e-6f) return set_err(CLIFFS_ERR_ARG, "Courant number %.4f > 1 after deformation", cour);
+    }
+    CK(cudaStreamSynchronize(s));
+    g->have_init = true;
+    return CLIFFS_OK;
+}
+
+int cliffs_set_durations(cliffs_grid* g, const int64_t* steps) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!steps) {
+        g->limit_h.clear();
+        cudaFree(g->limit);
+        g->limit = nullptr;
+        return CLIFFS_OK;
+    }
+    std::vector<long long> h(g->B);
+    CK(cudaMemcpy(h.data(), steps, sizeof(long long) * g->B, cudaMemcpyDefault));
+    for (int b = 0; b < g->B; ++b)
+        if (h[b] < 0) return set_err(CLIFFS_ERR_ARG, "negative duration for scenario %d", b);
+    if (!g->limit) CK(cudaMalloc(&g->limit, sizeof(long long) * g->B));
+    CK(cudaMemcpy(g->limit, h.data(), sizeof(long long) * g->B, cudaMemcpyHostToDevice));
+    g->limit_h = h;
+    return CLIFFS_OK;
+}
+
+int cliffs_step_n(cliffs_grid* g, int64_t n) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
+    if (n == 0) return CLIFFS_OK;
+    const long long last = g->step + n;
+    int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
+    if (rc) return rc;
+    cudaStream_t s = g->stream;
+    StepArgs a;
+    for (long long k = 0; k < n; ++k) {
+        const long long st = g->step + 1;
+        const int in = (int)(g->step & 1), out = 1 - in;
+        fill_step_args(g, a, in, out);
+        a.step = st;
+        if (st % g->cfg.maxout == 0) { a.emax = g->emax; a.smax = g->smax; }
+        if (g->G && st % g->cfg.gout == 0) a.rec_g = g->grec + (st / g->cfg.gout) * g->G * 3;
+        if (g->NN && st % g->cfg.bndout == 0) a.rec_n = g->nrec + (st / g->cfg.bndout) * g->NN * 3;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (g->timing) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, s));
+        }
+        cudaError_t le;
+        if (g->kind == 0) le = launch_step_fused(a, g->B, 4, s);
+        else if (g->kind == 1) le = launch_xsweep(a, g->B, s);
+        else le = launch_ysweep(a, g->B, s);
+        if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(le));
+        if (g->timing) {
+            CK(cudaEventRecord(e1, s));
+            g->ev.emplace_back(e0, e1);
+            if (g->ev.size() >= 4096) { rc = collect_timing(g); if (rc) return rc; }
+        }
+        g->step = st;
+    }
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, g->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h[0]) {
+        CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
+        if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
+        return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state before step %lld", (long long)g->step);
+    }
+    return CLIFFS_OK;
+}
+
+int cliffs_steps_done(cliffs_grid* g, int64_t* steps) {
+    if (!g || !steps) return set_err(CLIFFS_ERR_ARG, "null argument");
+    *steps = g->step;
+    return CLIFFS_OK;
+}
+
+int cliffs_read_gauges(cliffs_grid* g, int scenario, float* out, int64_t* nrec) {
+    g_err[0] = 0;
+    if (!g || !nrec) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    if (!g->have_init || g->G == 0) { *nrec = 0; return CLIFFS_OK; }
+    const long long n = steps_of(g, scenario) / g->cfg.gout + 1;
+    *nrec = n;
+    if (out) {
+        CK(cudaMemcpyAsync(out, g->grec + (size_t)scenario * g->grec_cap * g->G * 3,
+                           sizeof(float) * n * g->G * 3, cudaMemcpyDefault, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    return CLIFFS_OK;
+}
+
+int cliffs_read_maxwave(cliffs_grid* g, int scenario, float* eta_max, float* speed_max) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    const long long N = (long long)g->nx * g->ny;
+    int rc = ensure_tmp(g, 2 * sizeof(float) * N);
+    if (rc) return rc;
+    float* te = (float*)g->tmp;
+    float* ts = te + N;
+    const int cb = (int)cur_buf(g, scenario);
+    const size_t o = (size_t)scenario * g->plane;
+    k_max_fold<<<nblk(N), 256, 0, g->stream>>>(g->emax + o, g->smax + o, g->eta[cb] + o, g->u[cb] + o,
+                                               g->v[cb] + o, g->d32, te, ts, g->nx, g->ny, g->pitch,
+                                               (float)g->cfg.h_min,
+                                               g->cfg.itopo ? -3.402823466e38f : (float)g->cfg.dwall);
+    CK(cudaGetLastError());
+    if (eta_max) CK(cudaMemcpyAsync(eta_max, te, sizeof(float) * N, cudaMemcpyDefault, g->stream));
+    if (speed_max) CK(cudaMemcpyAsync(speed_max, ts, sizeof(float) * N, cudaMemcpyDefault, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return CLIFFS_OK;
+}
+
+int cliffs_read_boundary(cliffs_grid* g, int nest, int edge, double* vals, int64_t* nt) {
+    g_err[0] = 0;
+    if (!g || !nt) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (nest < 0 || nest >= (int)g->nests.size() || edge < 0 || edge > 3)
+        return set_err(CLIFFS_ERR_ARG, "nest %d edge %d out of range", nest, edge);
+    if (!g->have_init) { *nt = 0; return CLIFFS_OK; }
+    const long long n = g->step / g->cfg.bndout + 1;
+    *nt = n;
+    if (!vals) return CLIFFS_OK;
+    const int k = nest * 4 + edge;
+    const int np = g->edge_np[k];
+    int rc = ensure_tmp(g, sizeof(double) * n * 3 * np);
+    if (rc) return rc;
+    k_boundary<<<nblk(n * np), 256, 0, g->stream>>>(g->nrec, g->NN, g->pt_slot, g->pt_w, g->edge_off[k], np, n,
+                                                    (double*)g->tmp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(vals, g->tmp, sizeof(double) * n * 3 * np, cudaMemcpyDefault, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return CLIFFS_OK;
+}
+
+int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float* v) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    const int cb = (int)cur_buf(g, scenario);
+    const size_t o = (size_t)scenario * g->plane;
+    const size_t rowb = sizeof(float) * g->nx, pitchb = sizeof(float) * g->pitch;
+    if (eta) CK(cudaMemcpy2DAsync(eta, rowb, g->eta[cb] + o, pitchb, rowb, g->ny, cudaMemcpyDefault, g->stream));
+    if (u) CK(cudaMemcpy2DAsync(u, rowb, g->u[cb] + o, pitchb, rowb, g->ny, cudaMemcpyDefault, g->stream));
+    if (v) CK(cudaMemcpy2DAsync(v, rowb, g->v[cb] + o, pitchb, rowb, g->ny, cudaMemcpyDefault, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return CLIFFS_OK;
+}
+
+int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    int rc = collect_timing(g);
+    if (rc) return rc;
+    if (enable < 0) { g->t_ms = 0.0; g->t_launches = 0; }
+    else g->timing = enable != 0;
+    if (ms) *ms = g->t_ms;
+    if (launches) *launches = g->t_launches;
+    return CLIFFS_OK;
+}
+
+void cliffs_destroy(cliffs_grid* g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    free_grid(g);
+}
+
+}  // extern "C"

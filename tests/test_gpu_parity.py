@@ -1,0 +1,335 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (stated here, derived in the design doc): gauge traces within 1e-4 of the oracle's
+max |eta| per gauge (1e-7 m absolute for traces that stay below 1e-3 m); wet/dry masks equal
+except for cells whose oracle height or flooding margin lies within 1e-5 max(1, |d|) of
+h_min (counted); the depth filter and every branch-free identity (lake at rest, 1D == 2D)
+bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG, ERR_STATE, ERR_UNSTABLE
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1410_0753_gb300 import _build
+    _build.build()
+    oracle.threads(0)
+
+
+def assert_gauges(name, g32, g64):
+    rel, absol = P.gauge_errors(g32[:, :, 0], g64[:, :, 0])
+    P.report(name, gauge_rel_max=rel.max() if len(rel) else 0.0,
+             gauge_abs_max=absol.max() if len(absol) else 0.0, n_rel=len(rel), n_abs=len(absol))
+    assert len(rel) == 0 or rel.max() <= P.GAUGE_RTOL, rel
+    assert len(absol) == 0 or absol.max() <= P.GAUGE_ATOL_SMALL, absol
+
+
+# ---------------------------------------------------------------------------- S0 filter
+
+@pytest.mark.parametrize("case", ["beach", "spherical", "spiky"])
+def test_depth_filter_bit_exact(case):
+    if case == "beach":
+        w = workloads.beach_200()
+        x, y, d = w.x, w.y, w.depth
+    elif case == "spherical":
+        w = workloads.spherical_coast(300, 260)
+        x, y, d = w.x, w.y, w.depth
+    else:
+        rng = np.random.default_rng(7)
+        d = 50.0 + 40.0 * rng.standard_normal((97, 131))
+        d[rng.random(d.shape) < 0.05] = 0.05
+        d[:, :7] = -2.0
+        d[40:50, 60:70] = -1.0
+        x = np.arange(131) * 100.0
+        y = np.arange(97) * 100.0
+    ny, nx = d.shape
+    g = CliffsGrid(nx, ny, 0.01, coords=1 if case != "spherical" else 0)
+    g.set_bathy(x, y, d, True, 2.0, 0.1)
+    got = g.depth()
+    want, _ = oracle.depth_filter(d, 2.0, 0.1)
+    P.report("filter_" + case, changed=int((want != d).sum()), mismatch=int((got != want).sum()))
+    assert np.array_equal(got, want)
+    g.close()
+
+
+# ---------------------------------------------------------------------------- config 1
+
+def test_beach_200_full_run():
+    """2D Cartesian 200 x 200, 1000 steps, Manning n = 0.025, 8 gauges, max-wave each step."""
+    w = workloads.beach_200()
+    d64 = P.oracle_depth(w)
+    g = P.gpu_run(w, w.steps)
+    assert np.array_equal(g["depth"], d64)
+    o = P.oracle_run(w, w.steps, P.f32(d64))
+    assert_gauges("beach_200", g["gauges"], o["gauges"])
+    # max-wave over wet nodes
+    wet_ever = o["eta_max"] > -1e30
+    emax_err = np.abs(g["eta_max"][wet_ever] - o["eta_max"][wet_ever]).max()
+    smax_err = np.abs(g["speed_max"] - o["speed_max"]).max()
+    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
+    mism = wet32 != wet64
+    P.report("beach_200", emax_abs=emax_err, smax_abs=smax_err, eta_abs=np.abs(g["eta"] - o["eta"]).max(),
+             mask_mismatch=int(mism.sum()), mask_mismatch_not_near=int((mism & ~near).sum()),
+             wet_cells=int(wet64.sum()))
+    assert emax_err <= 1e-4 * 0.5
+    assert smax_err <= 1e-3
+    assert (mism & ~near).sum() == 0
+    g["grid"].close()
+
+
+# ---------------------------------------------------------------------------- identities
+
+def test_lake_at_rest_is_exact():
+    nx, ny = 150, 90
+    x = np.arange(nx) * 100.0
+    y = np.arange(ny) * 100.0
+    X, Y = np.meshgrid(x, y)
+    d = 30.0 - 40.0 * X / x[-1] + 3.0 * np.sin(Y / 400.0)
+    d -= 50.0 * np.exp(-((X - 5000) ** 2 + (Y - 4000) ** 2) / (2 * 600.0 ** 2))
+    for itopo in (1, 0):
+        g = CliffsGrid(nx, ny, 1.0, h_min=0.01, manning_n2=6.25e-4, itopo=itopo, dwall=2.0)
+        g.set_bathy(x, y, d)
+        g.set_initial(np.zeros((ny, nx), np.float32))
+        g.step(500)
+        e, u, v = g.state()
+        assert not e.any() and not u.any() and not v.any()
+        g.close()
+
+
+def beach_line(n=130):
+    x = np.arange(n) * 50.0
+    d = 8.0 - 10.0 * x / x[-1]
+    eta = 0.6 * np.exp(-(x - 1500.0) ** 2 / (2 * 300.0 ** 2))
+    return x, d, eta
+
+
+def test_1d_equals_2d_bit_exact():
+    """Dimensional splitting: y-invariant data between reflecting walls leaves the y-sweep
+    the identity, so every row of the fused 2D step equals the 1D x-sweep (and transposed)."""
+    x, d1, e1 = beach_line()
+    n, m, dt, steps = len(x), 9, 1.5, 300
+    kw = dict(h_min=0.01, manning_n2=6.25e-4)
+    g1 = CliffsGrid(n, 1, dt, **kw)
+    g1.set_bathy(x, np.zeros(1), d1[None, :], False)
+    g1.set_initial(e1[None, :].astype(np.float32))
+    g1.step(steps)
+    r1 = g1.state()
+    g2 = CliffsGrid(n, m, dt, **kw)
+    g2.set_bathy(x, np.arange(m) * 50.0, np.tile(d1, (m, 1)), False)
+    g2.set_initial(np.tile(e1, (m, 1)).astype(np.float32))
+    g2.step(steps)
+    r2 = g2.state()
+    assert np.array_equal(r2[0], np.tile(r1[0], (m, 1)))
+    assert np.array_equal(r2[1], np.tile(r1[1], (m, 1)))
+    assert not r2[2].any()
+    # transposed: 1D along y against x-invariant 2D
+    g3 = CliffsGrid(1, n, dt, **kw)
+    g3.set_bathy(np.zeros(1), x, d1[:, None], False)
+    g3.set_initial(e1[:, None].astype(np.float32))
+    g3.step(steps)
+    r3 = g3.state()
+    g4 = CliffsGrid(m, n, dt, **kw)
+    g4.set_bathy(np.arange(m) * 50.0, x, np.tile(d1[:, None], (1, m)), False)
+    g4.set_initial(np.tile(e1[:, None], (1, m)).astype(np.float32))
+    g4.step(steps)
+    r4 = g4.state()
+    assert np.array_equal(r4[0], np.tile(r3[0], (1, m)))
+    assert np.array_equal(r4[2], np.tile(r3[2], (1, m)))
+    assert not r4[1].any()
+    # and the 1D runs agree with the oracle
+    o = oracle.run(oracle.params(n, 1, dt, **kw), x, np.zeros(1), P.f32(d1)[None, :],
+                   P.f32(e1)[None, :], nsteps=steps)
+    wet = (o["eta"][0] + P.f32(d1)) >= 0.01
+    err = np.abs(r1[0][0] - o["eta"][0])[wet].max()
+    P.report("line_130", eta_abs=err)
+    assert err <= 1e-4 * 0.6
+    for g in (g1, g2, g3, g4):
+        g.close()
+
+
+# ---------------------------------------------------------------------------- ragged sizes
+
+@pytest.mark.parametrize("shape", [(131, 97), (57, 203), (3, 3), (200, 1), (1, 150), (345, 17)])
+def test_ragged_shapes_against_oracle(shape):
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 1000 + ny)
+    x = np.arange(nx) * 80.0 + (rng.random(nx) * 10.0 if nx > 1 else 0.0)
+    x = np.sort(x) if nx > 1 else np.zeros(1)
+    y = np.arange(ny) * 90.0
+    X, Y = np.meshgrid(x, y)
+    d = 20.0 - 26.0 * (X / max(x[-1], 1.0)) + 2.0 * np.sin(Y / 500.0)
+    if nx > 20 and ny > 20:
+        d -= 30.0 * np.exp(-((X - 0.4 * x[-1]) ** 2 + (Y - 0.5 * y[-1]) ** 2) / (2 * 400.0 ** 2))
+    eta = 0.4 * np.exp(-((X - 0.3 * x[-1]) ** 2 + (Y - 0.4 * y[-1]) ** 2) / (2 * 500.0 ** 2))
+    gauges = [(min(nx - 1, k * 7 % nx), min(ny - 1, k * 5 % ny)) for k in range(5)]
+    dt = 0.8 * 70.0 / math.sqrt(9.81 * 26.0)
+    kw = dict(h_min=0.01, manning_n2=6.25e-4, maxout=3, gout=2)
+    steps = 240
+    g = CliffsGrid(nx, ny, dt, gauges=gauges, **kw)
+    g.set_bathy(x, y, d)
+    d64, _ = oracle.depth_filter(d)
+    assert np.array_equal(g.depth(), d64)
+    g.set_initial(eta.astype(np.float32))
+    g.step(steps)
+    e32, u32, v32 = g.state()
+    p = oracle.params(nx, ny, dt, **{k: v for k, v in kw.items() if k not in ("maxout", "gout")})
+    o = oracle.run(p, x, y, P.f32(d64), P.f32(eta), nsteps=steps, maxout=3, gout=2, gauges=gauges)
+    wet32, wet64, near = P.wet_masks(e32, o["eta"], P.f32(d64), P.f32(d64), 0.01)
+    both = wet32 & wet64
+    err = np.abs(e32 - o["eta"])[both].max() if both.any() else 0.0
+    uerr = np.abs(u32 - o["u"])[both].max() if both.any() else 0.0
+    P.report("ragged_%dx%d" % shape, eta_abs=err, u_abs=uerr,
+             mask_mismatch=int((wet32 != wet64).sum()))
+    assert err <= 1e-4 * 0.4 + 1e-6
+    assert ((wet32 != wet64) & ~near).sum() == 0
+    assert_gauges("ragged_%dx%d" % shape, g.gauges(), o["gauges"])
+    em, sm = g.maxwave()
+    ok = o["eta_max"] > -1e30
+    assert np.abs(em[ok] - o["eta_max"][ok]).max() <= 1e-4 * 0.4 + 1e-6
+    assert np.array_equal(em[~ok], o["eta_max"][~ok].astype(np.float32))
+    g.close()
+
+
+# ---------------------------------------------------------------------------- spherical + nests
+
+def test_spherical_coast_small_with_nests():
+    w = workloads.spherical_coast(300, 260, steps=400)
+    d64 = P.oracle_depth(w)
+    g = P.gpu_run(w, w.steps)
+    assert np.array_equal(g["depth"], d64)
+    o = P.oracle_run(w, w.steps, P.f32(d64))
+    assert_gauges("spherical_300x260", g["gauges"], o["gauges"])
+    worst = 0.0
+    for m in range(len(w.nests)):
+        for e in range(4):
+            b32, b64 = g["boundary"][m][e], o["boundary"][m][e]
+            assert b32.shape == b64.shape
+            scale = max(np.abs(b64[:, 2]).max(), 1e-3)
+            worst = max(worst, np.abs(b32[:, 2] - b64[:, 2]).max() / scale)
+    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
+    P.report("spherical_300x260", boundary_eta_rel=worst, mask_mismatch=int((wet32 != wet64).sum()),
+             mask_mismatch_not_near=int(((wet32 != wet64) & ~near).sum()))
+    assert worst <= 1e-4
+    assert ((wet32 != wet64) & ~near).sum() == 0
+    g["grid"].close()
+
+
+# ---------------------------------------------------------------------------- quake, batch
+
+def test_quake_initial_condition():
+    w = workloads.beach_200(120, 90, steps=150)
+    d64 = P.oracle_depth(w)
+    zeta = w.eta0.astype(np.float32)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth)
+    g.set_initial(zeta, quake=1)
+    dq, eq = oracle.quake_init(d64, zeta.astype(np.float64), w.h_min)
+    assert np.array_equal(g.depth(), dq)
+    g.step(w.steps)
+    o = oracle.run(oracle.params_from(w), w.x, w.y, P.f32(dq), eq, nsteps=w.steps, gout=1,
+                   gauges=w.gauges)
+    assert_gauges("quake", g.gauges(), o["gauges"])
+    g.close()
+
+
+def test_batch_with_durations_matches_single_runs():
+    w = workloads.ensemble_512(batch=5, nx=96, ny=80, dmin=20, dmax=120)
+    g = P.gpu_run(w, int(w.durations.max()) + 5)
+    grid = g["grid"]
+    for b in range(w.batch):
+        single = CliffsGrid.from_workload(w, batch=1)
+        single.set_bathy(w.x, w.y, w.depth)
+        single.set_initial(w.eta0[b].astype(np.float32))
+        single.step(int(w.durations[b]))
+        e1, _, _ = single.state()
+        eb, _, _ = grid.state(b)
+        assert np.array_equal(eb, e1)
+        gb, g1 = grid.gauges(b), single.gauges()
+        assert gb.shape == g1.shape == (int(w.durations[b]) + 1, 16, 3)
+        assert np.array_equal(gb, g1)
+        single.close()
+    b = 2
+    d64 = P.oracle_depth(w)
+    o = oracle.run(oracle.params_from(w), w.x, w.y, P.f32(d64), w.eta0[b],
+                   nsteps=int(w.durations[b]), gout=1, gauges=w.gauges)
+    assert_gauges("batch_scenario2", grid.gauges(b), o["gauges"])
+    grid.close()
+
+
+# ---------------------------------------------------------------------------- full-size windows
+
+def window_check(w, k, centres, name, half=8):
+    """Full-size grid on the GPU for k steps; the oracle re-runs only the domain of dependence
+    (3 nodes per sweep in each direction) around each sample, so the central block is exact."""
+    d64 = P.oracle_depth(w)
+    g = P.gpu_run(w, k)
+    R = 3 * k + 4 + half
+    worst = 0.0
+    for (cy, cx) in centres:
+        j0, j1 = max(0, cy - R), min(w.ny, cy + R + 1)
+        i0, i1 = max(0, cx - R), min(w.nx, cx + R + 1)
+        p = oracle.params(i1 - i0, j1 - j0, w.dt, w.coords, w.h_min, w.manning_n2, w.itopo,
+                          w.dwall, w.transverse)
+        eta0 = w.eta0 if w.eta0.ndim == 2 else w.eta0[0]
+        o = oracle.run(p, w.x[i0:i1], w.y[j0:j1], P.f32(d64[j0:j1, i0:i1]), eta0[j0:j1, i0:i1],
+                       nsteps=k)
+        blk64 = o["eta"][cy - j0 - half: cy - j0 + half + 1, cx - i0 - half: cx - i0 + half + 1]
+        blk32 = g["eta"][cy - half: cy + half + 1, cx - half: cx + half + 1]
+        scale = max(np.abs(eta0).max(), 1e-3)
+        worst = max(worst, np.abs(blk32 - blk64).max() / scale)
+    P.report(name, window_eta_rel=worst, steps=k)
+    g["grid"].close()
+    return worst
+
+
+def test_full_size_spherical_2048_windows():
+    w = workloads.spherical_coast(2048, 2048, steps=60)
+    centres = [(1024, 700), (300, 300), (1800, 1500), (512, 260)]
+    assert window_check(w, 60, centres, "spherical_2048_windows") <= 1e-4
+
+
+def test_full_size_shelf_islands_8192_windows():
+    w = workloads.shelf_islands(8192, 8192, steps=40)
+    centres = [(4096, 800), (100, 100), (8000, 8100)]
+    assert window_check(w, 40, centres, "shelf_8192_windows") <= 1e-4
+
+
+# ---------------------------------------------------------------------------- errors
+
+def test_error_paths():
+    x = np.arange(20) * 10.0
+    d = np.full((20, 20), 100.0)
+    g = CliffsGrid(20, 20, 5.0)
+    with pytest.raises(CliffsError) as e:
+        g.set_bathy(x, x, d)                         # sqrt(g 100) * 5 / 10 = 15.7 > 1
+    assert e.value.code == ERR_ARG and "Courant" in str(e.value)
+    g.close()
+    g = CliffsGrid(20, 20, 0.1)
+    with pytest.raises(CliffsError) as e:
+        g.step(1)
+    assert e.value.code == ERR_STATE
+    g.set_bathy(x, x, d)
+    eta = np.zeros((20, 20), np.float32)
+    eta[5, 5] = np.nan                               # host-side fault injection
+    g.set_initial(eta)
+    with pytest.raises(CliffsError) as e:
+        g.step(3)
+    assert e.value.code == ERR_UNSTABLE
+    g.set_initial(np.zeros((20, 20), np.float32))    # the handle stays usable
+    g.step(3)
+    g.close()
+    with pytest.raises(CliffsError) as e:
+        CliffsGrid(20, 20, 0.1, gauges=[(25, 3)])
+    assert e.value.code == ERR_ARG
