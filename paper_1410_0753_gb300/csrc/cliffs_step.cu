@@ -145,6 +145,10 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepArgs a) {
                 mB.inv_l *= f; mB.inv_r *= f; mB.k2 *= f;
             }
             xsweep_pair(eA, uA, vA_, dA, eB, uB, vB_, dB, mA, mB, K, lane);
+            // a non-finite x-sweep result would read as a dry node in the y-sweep and be
+            // refilled by step (b) there, so it is checked here, before that happens
+            if (own && cA < a.nx) bad |= !(fabsf(eA) < 1e5f && fabsf(uA) < 1e5f && fabsf(vA_) < 1e5f);
+            if (own && cA + 1 < a.nx) bad |= !(fabsf(eB) < 1e5f && fabsf(uB) < 1e5f && fabsf(vB_) < 1e5f);
         }
         const float4 m2 = __ldg(a.ymet + min(max(k - 2, 0), a.ny - 1));
         float oeA, owA, otA, oeB, owB, otB;

@@ -270,40 +270,78 @@ def test_batch_with_durations_matches_single_runs():
 
 # ---------------------------------------------------------------------------- full-size windows
 
-def window_check(w, k, centres, name, half=8):
+def window_check(w, k, centres, name, eta0=None, half=8):
     """Full-size grid on the GPU for k steps; the oracle re-runs only the domain of dependence
     (3 nodes per sweep in each direction) around each sample, so the central block is exact."""
     d64 = P.oracle_depth(w)
+    if eta0 is not None:
+        w.eta0 = eta0
     g = P.gpu_run(w, k)
     R = 3 * k + 4 + half
-    worst = 0.0
+    eta0 = w.eta0 if w.eta0.ndim == 2 else w.eta0[0]
+    scale = max(np.abs(eta0).max(), 1e-3)
+    worst, moved, wetdry = 0.0, 0.0, 0
     for (cy, cx) in centres:
         j0, j1 = max(0, cy - R), min(w.ny, cy + R + 1)
         i0, i1 = max(0, cx - R), min(w.nx, cx + R + 1)
         p = oracle.params(i1 - i0, j1 - j0, w.dt, w.coords, w.h_min, w.manning_n2, w.itopo,
                           w.dwall, w.transverse)
-        eta0 = w.eta0 if w.eta0.ndim == 2 else w.eta0[0]
-        o = oracle.run(p, w.x[i0:i1], w.y[j0:j1], P.f32(d64[j0:j1, i0:i1]), eta0[j0:j1, i0:i1],
-                       nsteps=k)
-        blk64 = o["eta"][cy - j0 - half: cy - j0 + half + 1, cx - i0 - half: cx - i0 + half + 1]
-        blk32 = g["eta"][cy - half: cy + half + 1, cx - half: cx + half + 1]
-        scale = max(np.abs(eta0).max(), 1e-3)
+        dwin = P.f32(d64[j0:j1, i0:i1])
+        o = oracle.run(p, w.x[i0:i1], w.y[j0:j1], dwin, eta0[j0:j1, i0:i1], nsteps=k)
+        sl64 = (slice(cy - j0 - half, cy - j0 + half + 1), slice(cx - i0 - half, cx - i0 + half + 1))
+        sl32 = (slice(cy - half, cy + half + 1), slice(cx - half, cx + half + 1))
+        blk64, blk32 = o["eta"][sl64], g["eta"][sl32]
         worst = max(worst, np.abs(blk32 - blk64).max() / scale)
-    P.report(name, window_eta_rel=worst, steps=k)
+        moved = max(moved, np.abs(blk64 - eta0[sl32]).max() / scale)
+        wet32, wet64, near = P.wet_masks(blk32, blk64, dwin[sl64], dwin[sl64], w.h_min)
+        assert ((wet32 != wet64) & ~near).sum() == 0
+        wetdry += int((~wet64).sum())
+    P.report(name, window_eta_rel=worst, moved_rel=moved, dry_cells_sampled=wetdry, steps=k)
+    assert moved > 1e-3                    # the sampled blocks do carry the wave
     g["grid"].close()
-    return worst
+    return worst, wetdry
 
 
 def test_full_size_spherical_2048_windows():
-    w = workloads.spherical_coast(2048, 2048, steps=60)
-    centres = [(1024, 700), (300, 300), (1800, 1500), (512, 260)]
-    assert window_check(w, 60, centres, "spherical_2048_windows") <= 1e-4
+    w = workloads.spherical_coast(2048, 2048, steps=150)
+    jc, ic = np.unravel_index(np.argmax(w.eta0), w.eta0.shape)
+    centres = [(jc, ic), (jc + 40, ic + 60), (jc - 50, ic - 40)]
+    worst, _ = window_check(w, 150, centres, "spherical_2048_windows")
+    assert worst <= 1e-4
+
+
+def test_full_size_spherical_2048_shoreline_windows():
+    """Same full-size launch, with a 3 m hump on the coast so the sampled blocks flood and dry."""
+    w = workloads.spherical_coast(2048, 2048, steps=100)
+    j = np.arange(w.ny)
+    d = w.depth
+    row = 1300
+    ic = int(np.argmax(d[row] > 0))                      # first wet node east of the coast
+    J, I = np.meshgrid(j, np.arange(w.nx), indexing="ij")
+    hump = 3.0 * np.exp(-((J - row) ** 2 + (I - ic - 10) ** 2) / (2 * 12.0 ** 2))
+    worst, dry = window_check(w, 100, [(row, ic), (row + 15, ic - 5)], "spherical_2048_shore",
+                              eta0=P.f32(hump))
+    assert dry > 0 and worst <= 1e-4
 
 
 def test_full_size_shelf_islands_8192_windows():
     w = workloads.shelf_islands(8192, 8192, steps=40)
-    centres = [(4096, 800), (100, 100), (8000, 8100)]
-    assert window_check(w, 40, centres, "shelf_8192_windows") <= 1e-4
+    centres = [(4096, 800), (2000, 860), (7000, 760)]
+    worst, _ = window_check(w, 40, centres, "shelf_8192_windows")
+    assert worst <= 1e-4
+
+
+def test_full_size_shelf_islands_8192_island_windows():
+    w = workloads.shelf_islands(8192, 8192, steps=60)
+    land = w.depth < 0
+    jj, ii = np.nonzero(land)
+    k = len(jj) // 2
+    cy, cx = int(jj[k]), int(ii[k])
+    J, I = np.ogrid[:w.ny, :w.nx]
+    hump = 2.0 * np.exp(-((J - cy) ** 2 + (I - cx) ** 2) / (2 * 60.0 ** 2))
+    worst, dry = window_check(w, 60, [(cy, cx), (cy + 30, cx + 30)], "shelf_8192_island",
+                              eta0=P.f32(hump))
+    assert dry > 0 and worst <= 1e-4
 
 
 # ---------------------------------------------------------------------------- errors
@@ -321,9 +359,11 @@ def test_error_paths():
         g.step(1)
     assert e.value.code == ERR_STATE
     g.set_bathy(x, x, d)
-    eta = np.zeros((20, 20), np.float32)
-    eta[5, 5] = np.nan                               # host-side fault injection
-    g.set_initial(eta)
+    # host-side fault injection: a NaN velocity in a wet cell (a NaN surface would read as
+    # a dry cell, which step (b) refills at h_min)
+    u = np.zeros((20, 20), np.float32)
+    u[5, 5] = np.nan
+    g.set_initial(np.zeros((20, 20), np.float32), u)
     with pytest.raises(CliffsError) as e:
         g.step(3)
     assert e.value.code == ERR_UNSTABLE
