@@ -154,6 +154,30 @@ int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float*
  * synchronises. enable < 0 resets the totals. */
 int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches);
 
+/* The depth-jump filter of cliffs_set_bathy for callers that cannot allocate device
+ * memory. The paper has no counterpart of this entry point; it serves code that must not
+ * call cudaMalloc or cudaFree: code running while a CUDA stream is being captured (the
+ * allocation calls are not permitted then), hosts that hand out all device memory from
+ * their own pool and forbid hidden allocations, and callers that cannot afford the
+ * device-wide synchronisation cudaFree implies. It allocates nothing: its scratch (a second
+ * FP64 Jacobi buffer and a flag) is one static device array of CLIFFS_NOALLOC_MAX_CELLS
+ * doubles (8 MiB) that every GPU loading the library holds until the process exits.
+ *   depth   [ny][nx] FP64 input depth, positive down (host or device memory)
+ *   out     [ny][nx] FP64 filtered depth, DEVICE memory owned by the caller (may equal depth
+ *           when depth is device memory; must not overlap it otherwise)
+ *   alpha, min_depth  as in cliffs_set_bathy; stream: cudaStream_t or NULL
+ *   passes  receives the passes made (-1: stopped at the 100-pass cap); may be NULL
+ * The result is bit-identical to the filter cliffs_set_bathy applies. nx * ny larger than
+ * CLIFFS_NOALLOC_MAX_CELLS returns CLIFFS_ERR_ARG with the limit in cliffs_last_error().
+ * The first call on each device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. Every call on a device shares the one array and leaves its last contents there
+ * (the flag is cleared before each pass): calls that overlap on the GPU (other streams or
+ * threads) race and give wrong results. The call synchronises the stream once per pass. */
+#define CLIFFS_NOALLOC_MAX_CELLS (1 << 20)
+int cliffs_depth_filter_noalloc(const double* depth, double* out, int32_t nx, int32_t ny,
+                                double alpha, double min_depth, void* stream, int32_t* passes);
+
 /* Release every device buffer of the grid. NULL is allowed. */
 void cliffs_destroy(cliffs_grid* g);
 

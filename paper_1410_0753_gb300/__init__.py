@@ -25,7 +25,8 @@ __all__ = [
     "cliffs_grid_create", "cliffs_set_bathy", "cliffs_read_depth", "cliffs_set_initial",
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
-    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "EXPORTED",
+    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
+    "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -36,7 +37,7 @@ EXPORTED = [
     "cliffs_grid_create", "cliffs_set_bathy", "cliffs_read_depth", "cliffs_set_initial",
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
-    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version",
+    "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
 ]
 
 
@@ -90,6 +91,8 @@ def lib():
             "cliffs_destroy": ([vp], None),
             "cliffs_last_error": ([], C.c_char_p),
             "cliffs_abi_version": ([], C.c_int),
+            "cliffs_depth_filter_noalloc": ([vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                             vp, C.POINTER(C.c_int32)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -204,6 +207,17 @@ def cliffs_kernel_time(g, enable):
     n = C.c_int64()
     _check(lib().cliffs_kernel_time(g, int(enable), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def cliffs_depth_filter_noalloc(depth, out, nx, ny, alpha=2.0, min_depth=0.1, stream=None) -> int:
+    """Depth filter into caller-owned device memory ``out`` with no device allocation (see
+    include/cliffs.h). Returns the passes made."""
+    pd, kd = _ptr(depth, np.float64)
+    n = C.c_int32()
+    _check(lib().cliffs_depth_filter_noalloc(pd, _out_ptr(out), int(nx), int(ny), float(alpha),
+                                             float(min_depth), C.c_void_p(stream) if stream else None,
+                                             C.byref(n)))
+    return n.value
 
 
 def cliffs_destroy(g):

@@ -193,6 +193,10 @@ inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
+void cliffs::set_last_error(const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 // ----------------------------------------------------------------------------- grid
 
 struct cliffs_grid {

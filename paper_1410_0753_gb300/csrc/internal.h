@@ -40,6 +40,9 @@ struct StepArgs {
 
 enum { ERRF_NONFINITE = 1, ERRF_TIMEOUT = 2 };
 
+// message returned by cliffs_last_error() on the calling thread (cliffs_api.cu)
+void set_last_error(const char* msg);
+
 // launchers (cliffs_step.cu)
 cudaError_t launch_step_fused(const StepArgs& a, int batch, int wpb, cudaStream_t s);
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s);
