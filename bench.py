@@ -195,6 +195,8 @@ def run_cuda(args, world, rank, local):
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
     eta0 = w.eta0.astype(np.float32)
     g.set_initial(eta0)
+    tune = g.autotune(3)                  # rows per warp of the fused step, by measurement
+    rows_per_warp = min(tune, key=tune.get) if tune else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -300,6 +302,7 @@ def run_cuda(args, world, rank, local):
                        "gauges": int(g.n_gauges), "nests": len(w.nests), "maxout": w.maxout,
                        "gout": w.gout, "bndout": w.bndout, "steps_horizon": 3600,
                        "l2": "flushed before every timed step (256 MiB device write)",
+                       "rows_per_warp": rows_per_warp,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

@@ -125,6 +125,25 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
  * (the state is left as computed); ERR_CUDA. */
 int cliffs_step_n(cliffs_grid* g, int64_t n);
 
+/* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
+ * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
+ * longer warps). Each candidate S is timed over `trials` launches (after one warm-up) that
+ * read the current state and write scratch planes, with max-wave and records off; the
+ * fastest is kept for later steps. The grid's state, maxima and records are unchanged.
+ * Optional outputs: cand[] and us[] (capacity 16) receive the candidates and their best
+ * times in microseconds, *ncand their count (0 for 1D grids, which have no tile shape).
+ * Errors: ERR_STATE before set_initial; ERR_NOMEM; ERR_CUDA; ERR_TIMEOUT. */
+int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32_t* ncand);
+
+/* Fault injection for tests of the bounded waits (no counterpart in the paper): the next
+ * step launch of a 2D grid makes every shared-memory ring slot expect 16 bytes more than
+ * its copies deliver, with waits limited to `cycles` clock cycles. Each wait then expires,
+ * the kernel drains its copies (bounded), sets the timeout flag and returns; later launches
+ * of the same call return at once; cliffs_step_n returns CLIFFS_ERR_TIMEOUT and the grid
+ * stays usable (its state is whatever the interrupted step left). No GPU fault or hang is
+ * involved. Errors: ERR_ARG (no grid, cycles <= 0, 1D grid). */
+int cliffs_inject_wait_expiry(cliffs_grid* g, int64_t cycles);
+
 /* Steps completed since set_initial (for a batched grid, by the longest scenario). */
 int cliffs_steps_done(cliffs_grid* g, int64_t* steps);
 

@@ -26,7 +26,7 @@ __all__ = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
-    "EXPORTED",
+    "cliffs_inject_wait_expiry", "cliffs_autotune", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -38,6 +38,7 @@ EXPORTED = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
+    "cliffs_inject_wait_expiry", "cliffs_autotune",
 ]
 
 
@@ -93,6 +94,8 @@ def lib():
             "cliffs_abi_version": ([], C.c_int),
             "cliffs_depth_filter_noalloc": ([vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                              vp, C.POINTER(C.c_int32)], C.c_int),
+            "cliffs_inject_wait_expiry": ([vp, C.c_int64], C.c_int),
+            "cliffs_autotune": ([vp, C.c_int, vp, vp, C.POINTER(C.c_int32)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -220,6 +223,21 @@ def cliffs_depth_filter_noalloc(depth, out, nx, ny, alpha=2.0, min_depth=0.1, st
     return n.value
 
 
+def cliffs_autotune(g, trials=3):
+    """Time the candidate tile shapes on the current state and keep the fastest; returns
+    {rows_per_warp: microseconds}."""
+    cand = np.zeros(16, np.int32)
+    us = np.zeros(16, np.float64)
+    n = C.c_int32()
+    _check(lib().cliffs_autotune(g, int(trials), C.c_void_p(cand.ctypes.data),
+                                 C.c_void_p(us.ctypes.data), C.byref(n)))
+    return {int(cand[i]): float(us[i]) for i in range(n.value)}
+
+
+def cliffs_inject_wait_expiry(g, cycles):
+    _check(lib().cliffs_inject_wait_expiry(g, int(cycles)))
+
+
 def cliffs_destroy(g):
     if g:
         lib().cliffs_destroy(g)
@@ -324,3 +342,6 @@ class CliffsGrid:
 
     def kernel_time(self, enable=1):
         return cliffs_kernel_time(self.h, enable)
+
+    def autotune(self, trials=3):
+        return cliffs_autotune(self.h, trials)

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "cliffs.h"
 #include "internal.h"
 #include "sweep.cuh"
@@ -218,11 +220,12 @@ struct cliffs_grid {
     float *xa = nullptr, *xb = nullptr, *xk = nullptr, *xrow = nullptr;
     float4* ymet = nullptr;
     int* err = nullptr;
+    long long inject_cycles = 0;             // armed by cliffs_inject_wait_expiry
     long long* limit = nullptr;
     std::vector<long long> limit_h;
     long long step = 0;
     // samples: gauges (class 0) then enclosed-grid corner nodes (class 1)
-    std::vector<int4> items;
+    std::vector<int4> samples;
     int G = 0, NN = 0;
     int4* items_d = nullptr;
     int* samp_ptr = nullptr;
@@ -236,9 +239,15 @@ struct cliffs_grid {
     std::vector<int> edge_off, edge_np;      // per nest * 4 + edge
     int* pt_slot = nullptr;
     double* pt_w = nullptr;
+    // TMA descriptors: [k] reads buffer k as the step input
+    StepMaps maps[2];
     // launch geometry
     int kind = 0;                            // 0 fused 2D, 1 x only, 2 y only
     int S = 32, nstrips = 0, nseg = 0;
+    int S_hard = 32;                         // rows per warp in strips with dry nodes / edges
+    std::vector<unsigned char> hard;         // per strip: dry nodes in its window, or an edge
+    std::vector<int4> items;                 // fused kernel work items (strip, r0, r1, 0)
+    int4* items_dev = nullptr;
     // timing
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -281,10 +290,30 @@ int build_samples(cliffs_grid* g) {
     const int W = (g->kind == 2) ? XWIN : XOUT;
     const int S = g->kind == 1 ? 1 : g->S;
     const int nseg = g->kind == 1 ? g->ny : g->nseg;
-    const long long nw = (long long)g->nstrips * nseg;
+    long long nw = (long long)g->nstrips * nseg;
+    // kind 0: warp index of (row, strip) from the item table
+    std::vector<std::vector<int>> seg_start;
+    std::vector<std::vector<int>> seg_item;
+    if (g->kind == 0) {
+        nw = (long long)g->items.size();
+        seg_start.assign(g->nstrips, {});
+        seg_item.assign(g->nstrips, {});
+        for (size_t i = 0; i < g->items.size(); ++i) {
+            seg_start[g->items[i].x].push_back(g->items[i].y);
+            seg_item[g->items[i].x].push_back((int)i);
+        }
+    }
     std::vector<std::vector<int4>> per(nw);
-    for (const int4& it : g->items) {
-        const long long w = (long long)(it.x / S) * g->nstrips + it.y / W;
+    for (const int4& it : g->samples) {
+        long long w;
+        if (g->kind == 0) {
+            const int st = it.y / W;
+            const auto& v = seg_start[st];
+            const int k = (int)(std::upper_bound(v.begin(), v.end(), it.x) - v.begin()) - 1;
+            w = seg_item[st][k];
+        } else {
+            w = (long long)(it.x / S) * g->nstrips + it.y / W;
+        }
         per[w].push_back(it);
     }
     std::vector<int> ptr(nw + 1, 0);
@@ -309,6 +338,32 @@ int build_samples(cliffs_grid* g) {
     return CLIFFS_OK;
 }
 
+// Work items of the fused kernel: every strip is cut into segments of S rows, or S_hard
+// rows in strips whose window holds dry nodes or reaches past the domain edge (their warps
+// take the wet/dry correction paths on every row, so shorter segments even out the time
+// the warps of one launch take).
+int set_rows_per_warp(cliffs_grid* g, int S, int S_hard) {
+    g->S = S;
+    g->S_hard = S_hard;
+    g->nseg = (g->ny + S - 1) / S;
+    if (g->kind == 0) {
+        g->items.clear();
+        for (int st = 0; st < g->nstrips; ++st) {
+            const int h = g->hard.empty() ? 0 : g->hard[st];
+            const int seg = h ? S_hard : S;
+            for (int r0 = 0; r0 < g->ny; r0 += seg)
+                g->items.push_back(make_int4(st, r0, std::min(r0 + seg, g->ny), 0));
+        }
+        cudaFree(g->items_dev);
+        g->items_dev = nullptr;
+        CK(cudaMalloc(&g->items_dev, sizeof(int4) * g->items.size()));
+        CK(cudaMemcpy(g->items_dev, g->items.data(), sizeof(int4) * g->items.size(), cudaMemcpyHostToDevice));
+    }
+    return build_samples(g);
+}
+
+int hard_rows(int S) { return std::max(8, (S * 3 / 4) & ~1); }
+
 int choose_geometry(cliffs_grid* g) {
     if (g->ny == 1) {
         g->kind = 1;
@@ -323,13 +378,29 @@ int choose_geometry(cliffs_grid* g) {
     } else {
         g->kind = 0;
         g->nstrips = (g->nx + XOUT - 1) / XOUT;
-        // rows per warp: long enough to amortise the 6-row halo, short enough to give every
-        // SM a few waves of warps
-        const long long target = 152LL * 16;
-        int S = 128;
-        while (S > 16 && (long long)g->nstrips * ((g->ny + S - 1) / S) * g->B < target) S /= 2;
-        g->S = S;
-        g->nseg = (g->ny + S - 1) / S;
+        // rows per warp S: each warp walks S + 6 rows (3-row halo above and below), so the
+        // cost of one wave of warps is ~ S + 6; pick S minimising waves * (S + 6) with the
+        // resident warps the occupancy calculator reports (ties go to the larger S)
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long resident = (long long)std::max(1, nsm) *
+                                   std::max(1, fused_blocks_per_sm(g->cfg.coords != 1)) *
+                                   fused_warps_per_block();
+        int nhard = 0;
+        for (int st = 0; st < g->nstrips; ++st) nhard += g->hard[st];
+        const int cand[] = {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+        double best = 1e300;
+        int bestS = 32;
+        for (int S : cand) {
+            if (S > 2 * g->ny && S != 16) break;
+            const int Sh = hard_rows(S);
+            const long long warps = ((long long)(g->nstrips - nhard) * ((g->ny + S - 1) / S) +
+                                     (long long)nhard * ((g->ny + Sh - 1) / Sh)) * g->B;
+            const double cost = (double)((warps + resident - 1) / resident) * (S + 6);
+            if (cost <= best) { best = cost; bestS = S; }
+        }
+        return set_rows_per_warp(g, bestS, hard_rows(bestS));
     }
     return build_samples(g);
 }
@@ -376,11 +447,53 @@ bool locate(const std::vector<double>& c, double xp, int* i, double* a) {
     return true;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// a [batch][ny][pitch] FP32 tensor (batch 1 for the depth) read in 64 x 2 x 1 boxes;
+// out-of-range boxes fill with zeros
+int make_map(CUtensorMap* m, const float* base, int rank, int pitch, int ny, int batch) {
+    auto fn = encode_fn();
+    if (!fn) return set_err(CLIFFS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)ny, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)TMA_BOX_COLS, (cuuint32_t)TMA_BOX_ROWS, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(CLIFFS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return CLIFFS_OK;
+}
+
+int make_maps(cliffs_grid* g) {
+    for (int k = 0; k < 2; ++k) {
+        StepMaps& M = g->maps[k];
+        int rc = make_map(&M.e, g->eta[k], 3, g->pitch, g->ny, g->B);
+        if (!rc) rc = make_map(&M.u, g->u[k], 3, g->pitch, g->ny, g->B);
+        if (!rc) rc = make_map(&M.v, g->v[k], 3, g->pitch, g->ny, g->B);
+        if (!rc) rc = make_map(&M.d, g->d32, 3, g->pitch, g->ny, 1);
+        if (!rc) rc = make_map(&M.em, g->emax, 3, g->pitch, g->ny, g->B);
+        if (!rc) rc = make_map(&M.sm, g->smax, 3, g->pitch, g->ny, g->B);
+        if (rc) return rc;
+    }
+    return CLIFFS_OK;
+}
+
 void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.eta_in = g->eta[in]; a.u_in = g->u[in]; a.v_in = g->v[in];
     a.eta_out = g->eta[out]; a.u_out = g->u[out]; a.v_out = g->v[out];
     a.d = g->d32;
-    a.xa = g->xa; a.xb = g->xb; a.xk = g->xk; a.xrow = g->xrow; a.ymet = g->ymet;
+    a.xa = g->xa; a.xb = g->xb; a.xk = g->xk; a.xrow = g->xrow + MET_PAD; a.ymet = g->ymet + MET_PAD;
     a.emax = nullptr; a.smax = nullptr; a.rec_g = nullptr; a.rec_n = nullptr;
     a.rec_g_bstride = g->grec_cap * g->G * 3;
     a.samp_ptr = g->samp_ptr; a.samp = g->samp;
@@ -388,12 +501,15 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.err = g->err;
     a.nx = g->nx; a.ny = g->ny; a.pitch = g->pitch; a.plane = g->plane;
     a.S = g->S; a.nstrips = g->nstrips; a.nseg = g->nseg;
+    a.items = g->items_dev; a.nitems = (int)g->items.size();
     a.hmin = (float)g->cfg.h_min;
     a.dwall = g->cfg.itopo ? -3.402823466e38f : (float)g->cfg.dwall;
     a.half_dt = (float)(0.5 * g->cfg.dt);
     a.dt_gn2 = (float)(g->cfg.dt * 9.81 * g->cfg.manning_n2);
     a.transverse = g->cfg.transverse ? 1 : 0;
     a.sph = g->cfg.coords != 1;
+    a.wait_cycles = 2000000000LL;            // about a second at the GB300's clocks
+    a.tx_pad = 0;
 }
 
 void free_grid(cliffs_grid* g) {
@@ -401,7 +517,7 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->d32); cudaFree(g->d64); cudaFree(g->d64b);
     cudaFree(g->emax); cudaFree(g->smax);
     cudaFree(g->xa); cudaFree(g->xb); cudaFree(g->xk); cudaFree(g->xrow); cudaFree(g->ymet);
-    cudaFree(g->err); cudaFree(g->limit); cudaFree(g->items_d);
+    cudaFree(g->err); cudaFree(g->limit); cudaFree(g->items_d); cudaFree(g->items_dev);
     cudaFree(g->samp_ptr); cudaFree(g->samp); cudaFree(g->grec); cudaFree(g->nrec);
     cudaFree(g->pt_slot); cudaFree(g->pt_w); cudaFree(g->tmp); cudaFree(g->ured);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -492,13 +608,17 @@ int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
     CKG(cudaMalloc(&g->d64, sizeof(double) * (size_t)nx * ny));
     CKG(cudaMalloc(&g->d64b, sizeof(double) * (size_t)nx * ny));
     CKG(cudaMalloc(&g->xa, sizeof(float) * nx)); CKG(cudaMalloc(&g->xb, sizeof(float) * nx));
-    CKG(cudaMalloc(&g->xk, sizeof(float) * nx)); CKG(cudaMalloc(&g->xrow, sizeof(float) * ny));
-    CKG(cudaMalloc(&g->ymet, sizeof(float4) * ny));
+    CKG(cudaMalloc(&g->xk, sizeof(float) * nx)); CKG(cudaMalloc(&g->xrow, sizeof(float) * (ny + 2 * MET_PAD)));
+    CKG(cudaMalloc(&g->ymet, sizeof(float4) * (ny + 2 * MET_PAD)));
     CKG(cudaMalloc(&g->err, sizeof(int) * 4));
     CKG(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, g->stream));
     CKG(cudaMalloc(&g->ured, sizeof(unsigned) * 4));
     CKG(cudaStreamSynchronize(g->stream));
 #undef CKG
+    if (nx >= 3 && ny >= 3) {
+        int rc = make_maps(g);
+        if (rc) { free_grid(g); return rc; }
+    }
     *out = g;
     return CLIFFS_OK;
 }
@@ -567,13 +687,23 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
     CK(cudaMemcpyAsync(g->xa, xa.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(g->xb, xb.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(g->xk, xk.data(), sizeof(float) * nx, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(g->xrow, xrow.data(), sizeof(float) * ny, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(g->ymet, ym.data(), sizeof(float4) * ny, cudaMemcpyHostToDevice, s));
+    // row tables padded by MET_PAD rows on each side (edge rows repeated), so that the
+    // kernels index them without clamping
+    std::vector<float> xrow_p(ny + 2 * MET_PAD);
+    std::vector<float4> ym_p(ny + 2 * MET_PAD);
+    for (int j = 0; j < ny + 2 * MET_PAD; ++j) {
+        const int jj = std::min(std::max(j - MET_PAD, 0), ny - 1);
+        xrow_p[j] = xrow[jj];
+        ym_p[j] = ym[jj];
+    }
+    CK(cudaMemcpyAsync(g->xrow, xrow_p.data(), sizeof(float) * xrow_p.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->ymet, ym_p.data(), sizeof(float4) * ym_p.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
     k_depth_to_f32<<<nblk((long long)ny * g->pitch), 256, 0, s>>>(g->d64, g->d32, nx, ny, g->pitch);
     CK(cudaGetLastError());
     // CFL (section "Difference Scheme": |lambda| dt / dx <= 1)
     CK(cudaMemsetAsync(g->ured + 1, 0, sizeof(unsigned), s));
-    k_cfl<<<nblk(N), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow, g->ymet, dt, g->ured + 1);
+    k_cfl<<<nblk(N), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow + MET_PAD, g->ymet + MET_PAD, dt, g->ured + 1);
     CK(cudaGetLastError());
     unsigned cb = 0;
     CK(cudaMemcpyAsync(&cb, g->ured + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -583,8 +713,8 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
     if (cour > 1.0f + 1e-6f)
         return set_err(CLIFFS_ERR_ARG, "Courant number %.4f > 1: reduce dt (section Difference Scheme)", cour);
     // samples: gauges, then the corner nodes of every enclosed-grid boundary point
-    g->items.clear();
-    for (int k = 0; k < g->G; ++k) g->items.push_back(make_int4(g->gauges[2 * k + 1], g->gauges[2 * k], 0, k));
+    g->samples.clear();
+    for (int k = 0; k < g->G; ++k) g->samples.push_back(make_int4(g->gauges[2 * k + 1], g->gauges[2 * k], 0, k));
     std::map<long long, int> slot_of;
     std::vector<int> pslot;
     std::vector<double> pw;
@@ -614,7 +744,7 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
                     if (it == slot_of.end()) {
                         sl = (int)slot_of.size();
                         slot_of[key] = sl;
-                        g->items.push_back(make_int4(cc[q][0], cc[q][1], 1, sl));
+                        g->samples.push_back(make_int4(cc[q][0], cc[q][1], 1, sl));
                     } else {
                         sl = it->second;
                     }
@@ -634,9 +764,24 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
         CK(cudaMemcpy(g->pt_slot, pslot.data(), sizeof(int) * pslot.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(g->pt_w, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice));
     }
-    if (!g->items.empty()) {
-        CK(cudaMalloc(&g->items_d, sizeof(int4) * g->items.size()));
-        CK(cudaMemcpy(g->items_d, g->items.data(), sizeof(int4) * g->items.size(), cudaMemcpyHostToDevice));
+    if (!g->samples.empty()) {
+        CK(cudaMalloc(&g->items_d, sizeof(int4) * g->samples.size()));
+        CK(cudaMemcpy(g->items_d, g->samples.data(), sizeof(int4) * g->samples.size(), cudaMemcpyHostToDevice));
+    }
+    if (nx >= 3 && ny >= 3) {
+        // strips whose 64-column window holds a node that is dry at rest (d < h_min), or
+        // reaches past the domain edge
+        std::vector<double> hd((size_t)nx * ny);
+        CK(cudaMemcpy(hd.data(), g->d64, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost));
+        const int nstrips = (nx + XOUT - 1) / XOUT;
+        g->hard.assign(nstrips, 0);
+        for (int st = 0; st < nstrips; ++st) {
+            const int c0 = st * XOUT - 4, c1 = c0 + XWIN;
+            if (c0 < 0 || c1 > nx) { g->hard[st] = 1; continue; }
+            for (int j = 0; j < ny && !g->hard[st]; ++j)
+                for (int c = c0; c < c1; ++c)
+                    if (hd[(size_t)j * nx + c] < g->cfg.h_min) { g->hard[st] = 1; break; }
+        }
     }
     int rc = choose_geometry(g);
     if (rc) return rc;
@@ -700,8 +845,8 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
     CK(cudaGetLastError());
     int rc = grow_records(g, 1, 1);
     if (rc) return rc;
-    if (!g->items.empty()) {
-        const int ni = (int)g->items.size();
+    if (!g->samples.empty()) {
+        const int ni = (int)g->samples.size();
         k_record0<<<nblk((long long)ni * nb), 256, 0, s>>>(g->eta[0], g->u[0], g->v[0], g->pitch, g->plane,
                                                           g->items_d, ni, g->grec, g->grec_cap * g->G * 3,
                                                           g->nrec, b0, nb);
@@ -710,7 +855,7 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
     if (quake) {
         // the deformed depth must still satisfy the CFL limit
         CK(cudaMemsetAsync(g->ured + 1, 0, sizeof(unsigned), s));
-        k_cfl<<<nblk((long long)nx * ny), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow, g->ymet, g->cfg.dt, g->ured + 1);
+        k_cfl<<<nblk((long long)nx * ny), 256, 0, s>>>(g->d64, nx, ny, g->xa, g->xb, g->xrow + MET_PAD, g->ymet + MET_PAD, g->cfg.dt, g->ured + 1);
         unsigned cb = 0;
         CK(cudaMemcpyAsync(&cb, g->ured + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -761,6 +906,12 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
         if (st % g->cfg.maxout == 0) { a.emax = g->emax; a.smax = g->smax; }
         if (g->G && st % g->cfg.gout == 0) a.rec_g = g->grec + (st / g->cfg.gout) * g->G * 3;
         if (g->NN && st % g->cfg.bndout == 0) a.rec_n = g->nrec + (st / g->cfg.bndout) * g->NN * 3;
+        if (g->inject_cycles > 0) {
+            // fault injection: every ring slot of this launch waits for bytes that never come
+            a.wait_cycles = g->inject_cycles;
+            a.tx_pad = 16;
+            g->inject_cycles = 0;
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (g->timing) {
             CK(cudaEventCreate(&e0));
@@ -768,7 +919,7 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
             CK(cudaEventRecord(e0, s));
         }
         cudaError_t le;
-        if (g->kind == 0) le = launch_step_fused(a, g->B, 4, s);
+        if (g->kind == 0) le = launch_step_fused(a, g->maps[in], g->B, s);
         else if (g->kind == 1) le = launch_xsweep(a, g->B, s);
         else le = launch_ysweep(a, g->B, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(le));
@@ -787,6 +938,81 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
         if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
         return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state before step %lld", (long long)g->step);
     }
+    return CLIFFS_OK;
+}
+
+int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32_t* ncand) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    if (g->kind != 0) {                       // 1D grids have no tile shape to choose
+        if (ncand) *ncand = 0;
+        return CLIFFS_OK;
+    }
+    if (trials < 1) trials = 3;
+    cudaStream_t s = g->stream;
+    // scratch output planes: the trial steps read the current state and write elsewhere,
+    // with max-wave and records off, so the grid's state and outputs are untouched
+    const size_t pb = sizeof(float) * (size_t)g->B * g->plane;
+    float* scratch = nullptr;
+    CK(cudaMalloc(&scratch, 3 * pb));
+    const int cur = (int)(g->step & 1);
+    StepArgs a;
+    fill_step_args(g, a, cur, 1 - cur);
+    a.eta_out = scratch;
+    a.u_out = scratch + (size_t)g->B * g->plane;
+    a.v_out = scratch + 2 * (size_t)g->B * g->plane;
+    a.step = g->step + 1;
+    const int list[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
+    const int oldS = g->S;
+    int bestS = oldS, n = 0;
+    double best = 1e300;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = CLIFFS_OK;
+    for (int S : list) {
+        if (S > 2 * g->ny && S != list[0]) break;
+        rc = set_rows_per_warp(g, S, hard_rows(S));
+        if (rc) break;
+        a.S = g->S; a.nseg = g->nseg; a.samp_ptr = g->samp_ptr; a.samp = g->samp;
+        a.items = g->items_dev; a.nitems = (int)g->items.size();
+        float tbest = 1e30f;
+        for (int t = 0; t <= trials; ++t) {             // the first launch warms up
+            cudaEventRecord(e0, s);
+            cudaError_t le = launch_step_fused(a, g->maps[cur], g->B, s);
+            cudaEventRecord(e1, s);
+            if (le != cudaSuccess) { rc = set_err(CLIFFS_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(le)); break; }
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_err(CLIFFS_ERR_CUDA, "autotune sync"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (t > 0) tbest = std::min(tbest, ms);
+        }
+        if (rc) break;
+        if (cand) cand[n] = S;
+        if (us) us[n] = 1e3 * tbest;
+        ++n;
+        if (tbest < best) { best = tbest; bestS = S; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    int h[4] = {0, 0, 0, 0};
+    cudaMemcpy(h, g->err, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaMemset(g->err, 0, sizeof(h));
+    const int rc2 = set_rows_per_warp(g, rc ? oldS : bestS, hard_rows(rc ? oldS : bestS));
+    if (ncand) *ncand = n;
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up during autotuning");
+    return CLIFFS_OK;
+}
+
+int cliffs_inject_wait_expiry(cliffs_grid* g, int64_t cycles) {
+    g_err[0] = 0;
+    if (!g || cycles <= 0) return set_err(CLIFFS_ERR_ARG, "need a grid and a positive cycle limit");
+    if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the bounded waits belong to the 2D step kernel");
+    g->inject_cycles = cycles;
     return CLIFFS_OK;
 }
 

@@ -2,39 +2,88 @@
 //
 //  k_step_fused  one full step (x-sweep then y-sweep) per launch. A warp owns a strip of
 //                56 output columns and S output rows. It walks the rows of its strip from
-//                r0-3 to r0+S+2: each row is loaded once (64 columns, 2 per lane, 8-byte
-//                vector loads, the next row prefetched), x-swept across the warp with
-//                shuffles, and pushed into a per-column register pipeline that finishes the
-//                y-sweep three rows behind. The step reads eta, u, v, d and writes eta, u, v
-//                once per cell (28 B/cell-update plus the halo), fused with the max-wave
-//                update and the gauge / enclosed-grid sampling of that step.
+//                r0-3 to r0+S+2. Each row (64 columns of eta, u, v, d and, when max-wave is
+//                due, the max-wave rows three rows behind) arrives in shared memory by TMA
+//                (cp.async.bulk.tensor) through a 4-slot ring per warp with one mbarrier per
+//                slot; one lane keeps the ring RING rows ahead. The row is x-swept across the
+//                warp with shuffles and pushed into a per-column register pipeline that
+//                finishes the y-sweep three rows behind. The step reads eta, u, v, d and
+//                writes eta, u, v once per cell (28 B/cell-update plus the halo), fused with
+//                the max-wave update (+8 B) and the gauge / enclosed-grid sampling.
 //  k_xsweep      x-sweep alone (1D grids along x).
 //  k_ysweep      y-sweep alone (1D grids along y).
+// Every mbarrier wait is bounded (about a second of clock); on expiry the warp raises the
+// timeout flag, drains the copies it issued (again bounded) and returns.
 #include "internal.h"
 #include "sweep.cuh"
 
 namespace cliffs {
 
-__device__ __forceinline__ SweepConst sweep_const(const StepArgs& a) {
-    return SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+constexpr int RING = 4;                       // slots in flight per warp
+constexpr int SLOT_ROWS = TMA_BOX_ROWS;       // rows per slot (one TMA box each array)
+static_assert(TMA_BOX_COLS == XWIN, "a TMA box spans the warp's window");
+constexpr int NARR = 6;                       // eta, u, v, d, eta_max, speed_max
+constexpr int ARR_FLOATS = SLOT_ROWS * XWIN;
+constexpr int SLOT_FLOATS = NARR * ARR_FLOATS;
+constexpr int WARP_RING_BYTES = RING * SLOT_FLOATS * 4;
+constexpr int FUSED_WARPS = 4;
+constexpr int FUSED_SMEM = FUSED_WARPS * (WARP_RING_BYTES + RING * 8);
+
+// ------------------------------------------------------------------ TMA / mbarrier (PTX)
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return r != 0;
+}
+// bounded wait for the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long long limit) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(b, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_row3(float* dst, const CUtensorMap* m, uint64_t* b, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(b)), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
-// Nodes (r, c) and (r, c+1) of the step input; nodes outside the domain get depth
-// OUTSIDE_D (dry, never wetted) and zero state. c is even and rows are padded to an even
-// pitch, so the 8-byte loads stay aligned and inside the allocation.
+// ------------------------------------------------------------------ epilogue
+// Nodes (r, c) and (r, c+1) of the step input, for the kernels without TMA; nodes outside
+// the domain get depth OUTSIDE_D (dry, never wetted) and zero state.
 __device__ __forceinline__ void load_pair(const StepArgs& a, size_t boff, int r, int c,
-                                          float& e0, float& u0, float& v0, float& d0,
-                                          float& e1, float& u1, float& v1, float& d1) {
-    e0 = u0 = v0 = e1 = u1 = v1 = 0.f;
-    d0 = d1 = OUTSIDE_D;
+                                          float2& E, float2& U, float2& V, float2& D) {
+    E = U = V = make_float2(0.f, 0.f);
+    D = make_float2(OUTSIDE_D, OUTSIDE_D);
     if (r >= 0 && r < a.ny && c >= 0 && c < a.nx) {
         const size_t o = (size_t)r * a.pitch + c;
-        const float2 e = __ldg(reinterpret_cast<const float2*>(a.eta_in + boff + o));
-        const float2 u = __ldg(reinterpret_cast<const float2*>(a.u_in + boff + o));
-        const float2 v = __ldg(reinterpret_cast<const float2*>(a.v_in + boff + o));
-        const float2 d = __ldg(reinterpret_cast<const float2*>(a.d + o));
-        e0 = e.x; u0 = u.x; v0 = v.x; d0 = d.x;
-        if (c + 1 < a.nx) { e1 = e.y; u1 = u.y; v1 = v.y; d1 = d.y; }
+        E = __ldg(reinterpret_cast<const float2*>(a.eta_in + boff + o));
+        U = __ldg(reinterpret_cast<const float2*>(a.u_in + boff + o));
+        V = __ldg(reinterpret_cast<const float2*>(a.v_in + boff + o));
+        D = __ldg(reinterpret_cast<const float2*>(a.d + o));
+        if (c + 1 >= a.nx) { E.y = U.y = V.y = 0.f; D.y = OUTSIDE_D; }
     }
 }
 
@@ -44,124 +93,247 @@ __device__ __forceinline__ void max_upd(float& em, float& sm, float e, float u, 
     if (!((d >= a.dwall) && (e + d >= a.hmin))) return;
     if (e > em) { em = e; ch = true; }
     const float s2 = fmaf(u, u, v * v);
-    if (s2 > sm * sm) { sm = fmaxf(sm, sqrtf(s2)); ch = true; }
+    if (s2 > sm * sm) { sm = fmaxf(sm, s2 * rsqrt_approx(fmaxf(s2, 1e-30f))); ch = true; }
 }
 
-// Store a finished pair of nodes of row r and apply the step's max-wave update.
-__device__ __forceinline__ void emit_pair(const StepArgs& a, size_t boff, int r, int c,
-                                          bool va, bool vb,
-                                          float eA, float uA, float vA, float dA,
-                                          float eB, float uB, float vB, float dB, int& bad) {
+__device__ __forceinline__ int runaway(float e, float u, float v) {
+    return !(fabsf(e) + fabsf(u) + fabsf(v) < 3e5f);
+}
+
+// Store a finished pair of nodes of row r. With max-wave due, (em, sm) hold the stored
+// maxima of the pair (loaded beforehand) and are written back where they grow.
+__device__ __forceinline__ void emit_pair(const StepArgs& a, size_t o, bool va, bool vb,
+                                          float2 E, float2 U, float2 V, float2 D,
+                                          bool withmax, float2 em, float2 sm, int& bad) {
     if (!va) return;
-    const size_t o = boff + (size_t)r * a.pitch + c;
     if (vb) {
-        *reinterpret_cast<float2*>(a.eta_out + o) = make_float2(eA, eB);
-        *reinterpret_cast<float2*>(a.u_out + o) = make_float2(uA, uB);
-        *reinterpret_cast<float2*>(a.v_out + o) = make_float2(vA, vB);
+        *reinterpret_cast<float2*>(a.eta_out + o) = E;
+        *reinterpret_cast<float2*>(a.u_out + o) = U;
+        *reinterpret_cast<float2*>(a.v_out + o) = V;
+        bad |= runaway(E.x, U.x, V.x) | runaway(E.y, U.y, V.y);
     } else {
-        a.eta_out[o] = eA; a.u_out[o] = uA; a.v_out[o] = vA;
+        a.eta_out[o] = E.x; a.u_out[o] = U.x; a.v_out[o] = V.x;
+        bad |= runaway(E.x, U.x, V.x);
     }
-    bad |= !(fabsf(eA) < 1e5f && fabsf(uA) < 1e5f && fabsf(vA) < 1e5f);
-    if (vb) bad |= !(fabsf(eB) < 1e5f && fabsf(uB) < 1e5f && fabsf(vB) < 1e5f);
-    if (a.emax) {
+    if (withmax) {
         bool ch = false;
-        if (vb) {
-            float2 em = *reinterpret_cast<float2*>(a.emax + o);
-            float2 sm = *reinterpret_cast<float2*>(a.smax + o);
-            max_upd(em.x, sm.x, eA, uA, vA, dA, a, ch);
-            max_upd(em.y, sm.y, eB, uB, vB, dB, a, ch);
-            if (ch) {
+        max_upd(em.x, sm.x, E.x, U.x, V.x, D.x, a, ch);
+        if (vb) max_upd(em.y, sm.y, E.y, U.y, V.y, D.y, a, ch);
+        if (ch) {
+            if (vb) {
                 *reinterpret_cast<float2*>(a.emax + o) = em;
                 *reinterpret_cast<float2*>(a.smax + o) = sm;
+            } else {
+                a.emax[o] = em.x; a.smax[o] = sm.x;
             }
-        } else {
-            float em = a.emax[o], sm = a.smax[o];
-            max_upd(em, sm, eA, uA, vA, dA, a, ch);
-            if (ch) { a.emax[o] = em; a.smax[o] = sm; }
         }
     }
 }
 
-// Gauge / enclosed-grid node samples of row r owned by this warp (sorted by row).
-__device__ __forceinline__ void emit_samples(const StepArgs& a, int b, int& sp, int se, int r,
-                                             int c0, int lane,
-                                             float eA, float uA, float vA,
-                                             float eB, float uB, float vB) {
-    while (sp < se) {
-        const int4 it = __ldg(a.samp + sp);
-        if (it.x != r) break;
-        const int rel = it.y - c0;
-        if ((rel >> 1) == lane) {
-            const bool isB = rel & 1;
-            float* out = (it.z == 0) ? (a.rec_g ? a.rec_g + (long long)b * a.rec_g_bstride : nullptr)
-                                     : a.rec_n;
-            if (out) {
-                out[3 * it.w + 0] = isB ? eB : eA;
-                out[3 * it.w + 1] = isB ? uB : uA;
-                out[3 * it.w + 2] = isB ? vB : vA;
+// Gauge / enclosed-grid node samples owned by this warp, sorted by row. The warp keeps 32
+// consecutive sample records in registers (lane l holds record base + l). For a row with
+// samples, every lane whose record belongs to that row fetches the node's values from the
+// lane that owns the node by shuffle and writes the record, so all samples of a row go out
+// together; `next` holds the row of the next sample so rows without samples cost a compare.
+struct Samples {
+    int sp, se, base, next;
+    int4 mine;
+
+    __device__ __forceinline__ void load(const StepArgs& a, int lane) {
+        base = sp;
+        mine = (sp + lane < se) ? __ldg(a.samp + sp + lane) : make_int4(0x7fffffff, 0, 0, 0);
+    }
+    __device__ __forceinline__ void init(const StepArgs& a, int gw, int lane) {
+        sp = se = base = 0;
+        next = 0x7fffffff;
+        mine = make_int4(0x7fffffff, 0, 0, 0);
+        if (a.samp_ptr && (a.rec_g || a.rec_n)) {
+            sp = a.samp_ptr[gw];
+            se = a.samp_ptr[gw + 1];
+            if (sp < se) {
+                load(a, lane);
+                next = __shfl_sync(FULL, mine.x, 0);
             }
         }
-        ++sp;
     }
-}
+    __device__ __forceinline__ void emit(const StepArgs& a, int b, int r, int c0, int lane,
+                                         float2 E, float2 U, float2 V) {
+        if (r != next) return;
+        while (true) {
+            const bool mineRow = lane >= sp - base && mine.x == r;
+            const int rel = mine.y - c0;
+            const int src = mineRow ? (rel >> 1) & 31 : lane;
+            const float ex = __shfl_sync(FULL, E.x, src), ey = __shfl_sync(FULL, E.y, src);
+            const float ux = __shfl_sync(FULL, U.x, src), uy = __shfl_sync(FULL, U.y, src);
+            const float vx = __shfl_sync(FULL, V.x, src), vy = __shfl_sync(FULL, V.y, src);
+            if (mineRow) {
+                const bool isB = rel & 1;
+                float* out = (mine.z == 0) ? (a.rec_g ? a.rec_g + (long long)b * a.rec_g_bstride : nullptr)
+                                           : a.rec_n;
+                if (out) {
+                    out[3 * mine.w + 0] = isB ? ey : ex;
+                    out[3 * mine.w + 1] = isB ? uy : ux;
+                    out[3 * mine.w + 2] = isB ? vy : vx;
+                }
+            }
+            sp += __popc(__ballot_sync(FULL, mineRow));
+            if (sp >= se) { next = 0x7fffffff; return; }
+            if (sp - base < 32) {                  // the next record is cached: a later row
+                next = __shfl_sync(FULL, mine.x, sp - base);
+                return;
+            }
+            load(a, lane);                         // the row's records run past the cache
+            next = __shfl_sync(FULL, mine.x, 0);
+            if (next != r) return;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ fused step
+// The work of one warp of k_step_fused: strip `strip`, output rows [r0, r1), walked as
+// row pairs k0 + 2j, k0 + 2j + 1, one pair per ring slot.
+template <bool SPH>
+struct FusedWarp {
+    const StepMaps& M;
+    const StepArgs& a;
+    SweepConst K;
+    float* ring;
+    uint64_t* bar;
+    int lane, b, c0, cA, r0, r1, k0, npairs;
+    size_t orow;               // output offset of row r0 (scenario plane + column)
+    bool withmax, colA, colB, vA, vB, edge;
+    unsigned tx, nbox;
+    XMet2 m0;
+    YMarch2 ym;
+    Samples smp;
+    int bad;
+
+    __device__ __forceinline__ FusedWarp(const StepMaps& M_, const StepArgs& a_) : M(M_), a(a_) {}
+
+    // lanes 0..nbox-1 each start one 64 x 2 box of row pair j into its ring slot
+    __device__ __forceinline__ void issue(int j) {
+        const int slot = j % RING;
+        const int row = k0 + SLOT_ROWS * j;
+        if (lane == 0) mbar_arrive_tx(&bar[slot], tx);
+        if (lane < (int)nbox) {
+            fence_proxy_async();
+            tma_row3(ring + slot * SLOT_FLOATS + lane * ARR_FLOATS, &M.e + lane, &bar[slot], c0,
+                     lane >= 4 ? row - 3 : row, lane == 3 ? 0 : b);
+        }
+    }
+
+    // one row k held at `s` (row h of its slot)
+    template <int PH>
+    __device__ __forceinline__ void row(int k, const float* s) {
+        float2 E = reinterpret_cast<const float2*>(s + 0 * ARR_FLOATS)[lane];
+        float2 U = reinterpret_cast<const float2*>(s + 1 * ARR_FLOATS)[lane];
+        float2 V = reinterpret_cast<const float2*>(s + 2 * ARR_FLOATS)[lane];
+        float2 D = reinterpret_cast<const float2*>(s + 3 * ARR_FLOATS)[lane];
+        const float4 m2 = __ldg(a.ymet + k - 2);
+        const bool rowin = k >= 0 && k < a.ny;
+        if (edge || !rowin) {
+            if (!(rowin && colA)) { E.x = U.x = V.x = 0.f; D.x = OUTSIDE_D; }
+            if (!(rowin && colB)) { E.y = U.y = V.y = 0.f; D.y = OUTSIDE_D; }
+        }
+        if (rowin) {
+            XMet2 m = m0;
+            if (SPH) {
+                const float2 f = v2(__ldg(a.xrow + k));
+                m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
+            }
+            xsweep2(E, U, V, D, m, K, lane);
+        }
+        // y-sweep input of row k: eta, w = v, t = u
+        const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
+        // a non-finite x-sweep result reads as a dry node in the y-sweep and would be
+        // refilled by step (b) there: it is flagged here
+        if (vA && !oA) bad |= !(fabsf(E.x) < 1e5f);
+        if (vB && !oB) bad |= !(fabsf(E.y) < 1e5f);
+        const int r = k - 3;
+        ym.template push<PH, SPH>(E, V, U, D, oA, oB, m2, K, vA, vB,
+            [&](float2 oe, float2 ow, float2 ot, float2 od) {
+                if (r >= r0 && r < r1) {
+                    float2 em = make_float2(0.f, 0.f), sm = em;
+                    if (withmax) {
+                        em = reinterpret_cast<const float2*>(s + 4 * ARR_FLOATS)[lane];
+                        sm = reinterpret_cast<const float2*>(s + 5 * ARR_FLOATS)[lane];
+                    }
+                    emit_pair(a, orow + (size_t)(r - r0) * a.pitch, vA, vB, oe, ot, ow, od,
+                              withmax, em, sm, bad);
+                    smp.emit(a, b, r, c0, lane, oe, ot, ow);
+                }
+            });
+    }
+};
 
 template <bool SPH>
-__global__ void __launch_bounds__(128) k_step_fused(const StepArgs a) {
+__global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
+k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * FUSED_WARPS + wib;
     const int b = blockIdx.y;
-    if (gw >= a.nstrips * a.nseg) return;
+    if (gw >= a.nitems) return;
     if (a.limit && a.step > a.limit[b]) return;
-    const int strip = gw % a.nstrips, seg = gw / a.nstrips;
-    const int c0 = strip * XOUT - 4;
-    const int cA = c0 + 2 * lane;
-    const int r0 = seg * a.S, r1 = min(r0 + a.S, a.ny);
-    const size_t boff = (size_t)b * a.plane;
-    const SweepConst K = sweep_const(a);
-    XMet mA0{0.f, 0.f, 0.f}, mB0{0.f, 0.f, 0.f};
-    if (cA >= 0 && cA < a.nx) mA0 = XMet{__ldg(a.xa + cA), __ldg(a.xb + cA), __ldg(a.xk + cA)};
-    if (cA + 1 >= 0 && cA + 1 < a.nx)
-        mB0 = XMet{__ldg(a.xa + cA + 1), __ldg(a.xb + cA + 1), __ldg(a.xk + cA + 1)};
+    // a wait of an earlier launch expired: do not start new copies
+    if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
+    FusedWarp<SPH> W(M, a);
+    W.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    W.ring = reinterpret_cast<float*>(smem_raw + wib * WARP_RING_BYTES);
+    W.bar = reinterpret_cast<uint64_t*>(smem_raw + FUSED_WARPS * WARP_RING_BYTES) + wib * RING;
+    const int4 item = __ldg(a.items + gw);          // (strip, first row, end row)
+    W.lane = lane;
+    W.b = b;
+    W.c0 = item.x * XOUT - 4;
+    W.cA = W.c0 + 2 * lane;
+    W.r0 = item.y;
+    W.r1 = item.z;
+    W.k0 = W.r0 - 3;
+    W.npairs = (W.r1 + 3 - W.k0 + 1) / 2;
+    W.orow = (size_t)b * a.plane + (size_t)W.r0 * a.pitch + W.cA;
+    W.withmax = a.emax != nullptr;
+    W.nbox = W.withmax ? 6u : 4u;
+    W.tx = W.nbox * ARR_FLOATS * 4u + a.tx_pad;
+    W.colA = W.cA >= 0 && W.cA < a.nx;
+    W.colB = W.cA + 1 >= 0 && W.cA + 1 < a.nx;
     const bool own = lane >= 2 && lane < 30;
-    const bool vA = own && cA < a.nx;
-    const bool vB = own && cA + 1 < a.nx;
-    int sp = 0, se = 0;
-    if (a.samp_ptr && (a.rec_g || a.rec_n)) { sp = a.samp_ptr[gw]; se = a.samp_ptr[gw + 1]; }
-    YMarch ya, yb;
-    ya.init();
-    yb.init();
-    int bad = 0;
-    float pe0, pu0, pv0, pd0, pe1, pu1, pv1, pd1;
-    load_pair(a, boff, r0 - 3, cA, pe0, pu0, pv0, pd0, pe1, pu1, pv1, pd1);
-    for (int k = r0 - 3; k < r1 + 3; ++k) {
-        float eA = pe0, uA = pu0, vA_ = pv0, dA = pd0;
-        float eB = pe1, uB = pu1, vB_ = pv1, dB = pd1;
-        if (k + 1 < r1 + 3) load_pair(a, boff, k + 1, cA, pe0, pu0, pv0, pd0, pe1, pu1, pv1, pd1);
-        if (k >= 0 && k < a.ny) {
-            XMet mA = mA0, mB = mB0;
-            if (SPH) {
-                const float f = __ldg(a.xrow + k);
-                mA.inv_l *= f; mA.inv_r *= f; mA.k2 *= f;
-                mB.inv_l *= f; mB.inv_r *= f; mB.k2 *= f;
-            }
-            xsweep_pair(eA, uA, vA_, dA, eB, uB, vB_, dB, mA, mB, K, lane);
-            // a non-finite x-sweep result would read as a dry node in the y-sweep and be
-            // refilled by step (b) there, so it is checked here, before that happens
-            if (own && cA < a.nx) bad |= !(fabsf(eA) < 1e5f && fabsf(uA) < 1e5f && fabsf(vA_) < 1e5f);
-            if (own && cA + 1 < a.nx) bad |= !(fabsf(eB) < 1e5f && fabsf(uB) < 1e5f && fabsf(vB_) < 1e5f);
-        }
-        const float4 m2 = __ldg(a.ymet + min(max(k - 2, 0), a.ny - 1));
-        float oeA, owA, otA, oeB, owB, otB;
-        const float odA = ya.dd3, odB = yb.dd3;
-        ya.push(eA, vA_, uA, dA, m2, K, oeA, owA, otA);
-        yb.push(eB, vB_, uB, dB, m2, K, oeB, owB, otB);
-        const int r = k - 3;
-        if (r >= r0 && r < r1) {
-            emit_pair(a, boff, r, cA, vA, vB, oeA, otA, owA, odA, oeB, otB, owB, odB, bad);
-            if (sp < se) emit_samples(a, b, sp, se, r, c0, lane, oeA, otA, owA, oeB, otB, owB);
-        }
+    W.vA = own && W.colA;
+    W.vB = own && W.colB;
+    W.edge = W.c0 < 0 || W.c0 + XWIN > a.nx;
+    W.bad = 0;
+    if (lane == 0) {
+        for (int s = 0; s < RING; ++s) mbar_init(&W.bar[s], 1);
+        fence_mbar_init();
     }
-    if (bad) atomicOr(a.err, ERRF_NONFINITE);
+    __syncwarp();
+    for (int j = 0; j < min(RING, W.npairs); ++j) W.issue(j);
+    float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
+    if (W.colA) { il.x = __ldg(a.xa + W.cA); ir.x = __ldg(a.xb + W.cA); k2.x = __ldg(a.xk + W.cA); }
+    if (W.colB) { il.y = __ldg(a.xa + W.cA + 1); ir.y = __ldg(a.xb + W.cA + 1); k2.y = __ldg(a.xk + W.cA + 1); }
+    W.m0 = XMet2{il, ir, k2};
+    W.smp.init(a, gw, lane);
+    W.ym.init();
+    int j = 0;
+    for (; j < W.npairs; ++j) {
+        const int slot = j % RING;
+        const bool ok = mbar_wait(&W.bar[slot], (unsigned)(j / RING) & 1u, a.wait_cycles);
+        if (!__all_sync(FULL, ok)) break;
+        const float* s = W.ring + slot * SLOT_FLOATS;
+        const int k = W.k0 + SLOT_ROWS * j;
+        W.template row<0>(k, s);
+        W.template row<1>(k + 1, s + XWIN);
+        __syncwarp();
+        if (j + RING < W.npairs) W.issue(j + RING);
+    }
+    if (j < W.npairs) {
+        // a wait expired at pair j: pairs j .. j+RING-1 may still be in flight; let each
+        // land (bounded) before the warp leaves
+        for (int i = j; i < min(j + RING, W.npairs); ++i)
+            mbar_wait(&W.bar[i % RING], (unsigned)(i / RING) & 1u, a.wait_cycles);
+        W.bad |= 2;
+    }
+    if (W.bad) atomicOr(a.err, (W.bad & 2) ? (ERRF_TIMEOUT | ERRF_NONFINITE) : ERRF_NONFINITE);
 }
 
 // x-sweep alone: one warp per (row, strip of 56 columns).
@@ -176,75 +348,133 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     const int c0 = strip * XOUT - 4;
     const int cA = c0 + 2 * lane;
     const size_t boff = (size_t)b * a.plane;
-    const SweepConst K = sweep_const(a);
-    XMet mA{0.f, 0.f, 0.f}, mB{0.f, 0.f, 0.f};
-    if (cA >= 0 && cA < a.nx) mA = XMet{a.xa[cA], a.xb[cA], a.xk[cA]};
-    if (cA + 1 >= 0 && cA + 1 < a.nx) mB = XMet{a.xa[cA + 1], a.xb[cA + 1], a.xk[cA + 1]};
+    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
+    if (cA >= 0 && cA < a.nx) { il.x = a.xa[cA]; ir.x = a.xb[cA]; k2.x = a.xk[cA]; }
+    if (cA + 1 >= 0 && cA + 1 < a.nx) { il.y = a.xa[cA + 1]; ir.y = a.xb[cA + 1]; k2.y = a.xk[cA + 1]; }
+    XMet2 m{il, ir, k2};
     if (SPH) {
-        const float f = a.xrow[r];
-        mA.inv_l *= f; mA.inv_r *= f; mA.k2 *= f;
-        mB.inv_l *= f; mB.inv_r *= f; mB.k2 *= f;
+        const float2 f = v2(a.xrow[r]);
+        m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
     }
-    float eA, uA, vA_, dA, eB, uB, vB_, dB;
-    load_pair(a, boff, r, cA, eA, uA, vA_, dA, eB, uB, vB_, dB);
-    xsweep_pair(eA, uA, vA_, dA, eB, uB, vB_, dB, mA, mB, K, lane);
+    float2 E, U, V, D;
+    load_pair(a, boff, r, cA, E, U, V, D);
+    xsweep2(E, U, V, D, m, K, lane);
     const bool own = lane >= 2 && lane < 30;
+    const bool va = own && cA < a.nx, vb = own && cA + 1 < a.nx;
     int bad = 0;
-    emit_pair(a, boff, r, cA, own && cA < a.nx, own && cA + 1 < a.nx,
-              eA, uA, vA_, dA, eB, uB, vB_, dB, bad);
-    if (a.samp_ptr && (a.rec_g || a.rec_n)) {
-        int sp = a.samp_ptr[gw];
-        const int se = a.samp_ptr[gw + 1];
-        if (sp < se) emit_samples(a, b, sp, se, r, c0, lane, eA, uA, vA_, eB, uB, vB_);
+    const size_t o = boff + (size_t)r * a.pitch + cA;
+    float2 em = make_float2(0.f, 0.f), sm = em;
+    const bool withmax = a.emax != nullptr;
+    if (withmax && va) {
+        em.x = a.emax[o]; sm.x = a.smax[o];
+        if (vb) { em.y = a.emax[o + 1]; sm.y = a.smax[o + 1]; }
     }
+    emit_pair(a, o, va, vb, E, U, V, D, withmax, em, sm, bad);
+    Samples smp;
+    smp.init(a, gw, lane);
+    smp.emit(a, b, r, c0, lane, E, U, V);
     if (bad) atomicOr(a.err, ERRF_NONFINITE);
 }
 
 // y-sweep alone: one warp per (strip of 64 columns, S rows).
+template <bool SPH>
+struct YOnly {
+    const StepArgs& a;
+    SweepConst K;
+    int lane, b, c0, cA, r0, r1;
+    size_t boff;
+    bool vA, vB, withmax;
+    YMarch2 ym;
+    Samples smp;
+    int bad;
+    __device__ __forceinline__ YOnly(const StepArgs& a_) : a(a_) {}
+    template <int PH>
+    __device__ __forceinline__ void row(int k) {
+        float2 E, U, V, D;
+        load_pair(a, boff, k, cA, E, U, V, D);
+        const float4 m2 = __ldg(a.ymet + k - 2);
+        const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
+        const int r = k - 3;
+        ym.template push<PH, SPH>(E, V, U, D, oA, oB, m2, K, vA, vB,
+            [&](float2 oe, float2 ow, float2 ot, float2 od) {
+                if (r >= r0 && r < r1) {
+                    const size_t o = boff + (size_t)r * a.pitch + cA;
+                    float2 em = make_float2(0.f, 0.f), sm = em;
+                    if (withmax && vA) {
+                        em.x = a.emax[o]; sm.x = a.smax[o];
+                        if (vB) { em.y = a.emax[o + 1]; sm.y = a.smax[o + 1]; }
+                    }
+                    emit_pair(a, o, vA, vB, oe, ot, ow, od, withmax, em, sm, bad);
+                    smp.emit(a, b, r, c0, lane, oe, ot, ow);
+                }
+            });
+    }
+};
+
+template <bool SPH>
 __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int b = blockIdx.y;
     if (gw >= a.nstrips * a.nseg) return;
     if (a.limit && a.step > a.limit[b]) return;
+    YOnly<SPH> Y(a);
+    Y.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
     const int strip = gw % a.nstrips, seg = gw / a.nstrips;
-    const int c0 = strip * XWIN;
-    const int cA = c0 + 2 * lane;
-    const int r0 = seg * a.S, r1 = min(r0 + a.S, a.ny);
-    const size_t boff = (size_t)b * a.plane;
-    const SweepConst K = sweep_const(a);
-    const bool vA = cA < a.nx, vB = cA + 1 < a.nx;
-    int sp = 0, se = 0;
-    if (a.samp_ptr && (a.rec_g || a.rec_n)) { sp = a.samp_ptr[gw]; se = a.samp_ptr[gw + 1]; }
-    YMarch ya, yb;
-    ya.init();
-    yb.init();
-    int bad = 0;
-    for (int k = r0 - 3; k < r1 + 3; ++k) {
-        float eA, uA, vA_, dA, eB, uB, vB_, dB;
-        load_pair(a, boff, k, cA, eA, uA, vA_, dA, eB, uB, vB_, dB);
-        const float4 m2 = __ldg(a.ymet + min(max(k - 2, 0), a.ny - 1));
-        float oeA, owA, otA, oeB, owB, otB;
-        const float odA = ya.dd3, odB = yb.dd3;
-        ya.push(eA, vA_, uA, dA, m2, K, oeA, owA, otA);
-        yb.push(eB, vB_, uB, dB, m2, K, oeB, owB, otB);
-        const int r = k - 3;
-        if (r >= r0 && r < r1) {
-            emit_pair(a, boff, r, cA, vA, vB, oeA, otA, owA, odA, oeB, otB, owB, odB, bad);
-            if (sp < se) emit_samples(a, b, sp, se, r, c0, lane, oeA, otA, owA, oeB, otB, owB);
-        }
+    Y.lane = lane;
+    Y.b = b;
+    Y.c0 = strip * XWIN;
+    Y.cA = Y.c0 + 2 * lane;
+    Y.r0 = seg * a.S;
+    Y.r1 = min(Y.r0 + a.S, a.ny);
+    Y.boff = (size_t)b * a.plane;
+    Y.vA = Y.cA < a.nx;
+    Y.vB = Y.cA + 1 < a.nx;
+    Y.withmax = a.emax != nullptr;
+    Y.bad = 0;
+    Y.smp.init(a, gw, lane);
+    Y.ym.init();
+    int k = Y.r0 - 3;
+    for (; k + 1 < Y.r1 + 3; k += 2) {
+        Y.template row<0>(k);
+        Y.template row<1>(k + 1);
     }
-    if (bad) atomicOr(a.err, ERRF_NONFINITE);
+    if (k < Y.r1 + 3) Y.template row<0>(k);
+    if (Y.bad) atomicOr(a.err, ERRF_NONFINITE);
 }
 
-cudaError_t launch_step_fused(const StepArgs& a, int batch, int wpb, cudaStream_t s) {
-    (void)wpb;
-    const int nw = a.nstrips * a.nseg;
-    const dim3 grid((nw + 3) / 4, batch);
-    if (a.sph) k_step_fused<true><<<grid, 128, 0, s>>>(a);
-    else k_step_fused<false><<<grid, 128, 0, s>>>(a);
+// ------------------------------------------------------------------ launchers
+// the ring needs more than the default 48 KB of dynamic shared memory per block
+static cudaError_t fused_smem_optin() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaErrorNotReady) {
+        done = cudaFuncSetAttribute(k_step_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(k_step_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+    }
+    return done;
+}
+
+cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s) {
+    const cudaError_t e = fused_smem_optin();
+    if (e != cudaSuccess) return e;
+    const int nw = a.nitems;
+    const dim3 grid((nw + FUSED_WARPS - 1) / FUSED_WARPS, batch);
+    if (a.sph) k_step_fused<true><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
+    else k_step_fused<false><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
     return cudaGetLastError();
 }
+
+int fused_blocks_per_sm(bool sph) {
+    if (fused_smem_optin() != cudaSuccess) return 1;
+    int nb = 0;
+    if (sph) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<true>, FUSED_WARPS * 32, FUSED_SMEM);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<false>, FUSED_WARPS * 32, FUSED_SMEM);
+    return nb;
+}
+
+int fused_warps_per_block() { return FUSED_WARPS; }
 
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s) {
     const int nw = a.nstrips * a.ny;
@@ -257,7 +487,8 @@ cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s) {
 cudaError_t launch_ysweep(const StepArgs& a, int batch, cudaStream_t s) {
     const int nw = a.nstrips * a.nseg;
     const dim3 grid((nw + 3) / 4, batch);
-    k_ysweep<<<grid, 128, 0, s>>>(a);
+    if (a.sph) k_ysweep<true><<<grid, 128, 0, s>>>(a);
+    else k_ysweep<false><<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

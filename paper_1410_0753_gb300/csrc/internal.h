@@ -1,6 +1,7 @@
 // Internal interface between the host runtime (cliffs_api.cu) and the kernel translation
 // units. Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,8 +19,9 @@ struct StepArgs {
     float* eta_out; float* u_out; float* v_out;
     const float* d;                  // [ny][pitch], FP32 depth
     const float* xa; const float* xb; const float* xk;   // [nx] per-column x metric
-    const float* xrow;               // [ny] row factor of the x metric (1 or 1/(R cos phi))
-    const float4* ymet;              // [ny] (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R)
+    // per-row tables, valid for row indices -MET_PAD .. ny + MET_PAD - 1 (edge rows repeated)
+    const float* xrow;               // row factor of the x metric (1 or 1/(R cos phi))
+    const float4* ymet;              // (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R)
     float* emax; float* smax;        // max-wave fields, or null when not due this step
     float* rec_g;                    // gauge record row of this step (scenario 0) or null
     float* rec_n;                    // enclosed-grid node record row or null
@@ -31,20 +33,35 @@ struct StepArgs {
     int* err;                        // device error flags
     int nx, ny, pitch;
     long long plane;
-    int S;                           // output rows per warp (fused / y kernels)
+    int S;                           // output rows per warp (y kernel)
     int nstrips, nseg;
+    const int4* items;               // fused kernel: per warp (strip, first row, end row)
+    int nitems;
     float hmin, dwall, half_dt, dt_gn2;
     int transverse;
     int sph;                         // geographic grid: x metric scaled per row
+    long long wait_cycles;           // limit of every mbarrier wait (clock cycles)
+    unsigned tx_pad;                 // extra bytes each ring slot expects (fault injection; 0)
 };
 
 enum { ERRF_NONFINITE = 1, ERRF_TIMEOUT = 2 };
+constexpr int MET_PAD = 8;
+constexpr int TMA_BOX_COLS = 64;   // columns of one TMA box (a warp's window)
+constexpr int TMA_BOX_ROWS = 2;    // rows of one TMA box (one ring slot)
 
 // message returned by cliffs_last_error() on the calling thread (cliffs_api.cu)
 void set_last_error(const char* msg);
 
+// TMA descriptors of the fused step's inputs: eta, u, v, eta_max, speed_max as 3D
+// [batch][ny][pitch] tensors and d as a 2D [ny][pitch] tensor, each read as 64 x 1 boxes.
+struct StepMaps {
+    CUtensorMap e, u, v, d, em, sm;
+};
+
 // launchers (cliffs_step.cu)
-cudaError_t launch_step_fused(const StepArgs& a, int batch, int wpb, cudaStream_t s);
+cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s);
+int fused_blocks_per_sm(bool sph);
+int fused_warps_per_block();
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s);
 cudaError_t launch_ysweep(const StepArgs& a, int batch, cudaStream_t s);
 

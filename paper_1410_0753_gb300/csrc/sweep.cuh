@@ -18,6 +18,12 @@
 // and recover by increments (eqs. (stateu), (stateh)): du = (dp + dq)/2, dc = (dp - dq)/4,
 // deta = dc (2c + dc)/g. At rest every term is exactly zero, so the lake at rest is kept
 // bit for bit.
+//
+// Layout of the work. Every lane owns two neighbouring nodes (columns A and B of its pair)
+// and evaluates the update of both with packed FP32x2 instructions (add/mul/fma .f32x2).
+// Steps (b), (c) and (e) are corrections applied per node, and only inside warp-uniform
+// branches taken when some node of the warp needs them (a dry node that can flood, a wet
+// node next to a dry one, a newly wetted node), so open water runs the update alone.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,92 +45,117 @@ struct SweepConst {
     int   transverse; // eq. (pq3) on/off
 };
 
-// post-(b) state of a node
-struct Node {
-    float eta, w, t, d, c;   // c = sqrt(g h), meaningful only when wet
-    bool  wet;               // wet after (b)
-    int   dir;               // -1 / +1: wetted in (b) from the left / right neighbour
-};
+// ------------------------------------------------------------------ packed FP32x2
+__device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, v2(-1.f), a); }
 
-struct Flux { float p, q, t; };
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// x^(-4/3) for x > 0 from the hardware base-2 logarithm and exponential
+__device__ __forceinline__ float pow_m43(float x) {
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l *= -4.0f / 3.0f;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
+
+// c = sqrt(g h) of both nodes (h > 0 for wet nodes; dry nodes give NaN and are not used)
+__device__ __forceinline__ float2 wave_speed2(float2 h) {
+    const float2 gh = mul2(v2(GRAV), h);
+    return mul2(gh, make_float2(rsqrt_approx(gh.x), rsqrt_approx(gh.y)));
+}
+__device__ __forceinline__ float wave_speed(float h) {
+    const float gh = GRAV * h;
+    return gh * rsqrt_approx(gh);
+}
 
 __device__ __forceinline__ bool wet_mark(float eta, float d, const SweepConst& K) {
     return (d >= K.dwall) && (eta + d >= K.hmin);              // (a): dry when h < h_min
 }
 
-// (b) for a node that is dry at the start of the sweep. Neighbours: start-of-sweep eta, w,
-// t and wet mark. The wetter neighbour (larger eta) wins, the left one on a tie.
-__device__ __forceinline__ void flood(Node& n, float eL, float wL, float tL, bool oL,
-                                      float eR, float wR, float tR, bool oR,
-                                      const SweepConst& K) {
-    if (n.wet) return;
-    n.w = 0.f;                                                 // a dry node is at rest
-    n.t = 0.f;
-    if (!(n.d >= K.dwall)) return;
-    const bool okL = oL && (eL + n.d > K.hmin);
-    const bool okR = oR && (eR + n.d > K.hmin);
-    if (okL || okR) {
-        const bool useR = okR && (!okL || eR > eL);
-        n.eta = K.hmin - n.d;                                  // height h_min
-        n.w = useR ? wR : wL;
-        n.t = useR ? tR : tL;
-        n.wet = true;
-        n.dir = useR ? 1 : -1;
-    }
-}
+struct Flux2 { float2 p, q, t; };
 
-// eq. (eqQ) for p and q and the eq. (pq3) flux for t across the interface between node a
-// (left) and node b (right), perturbation form, divided by the interval.
-__device__ __forceinline__ Flux iface(const Node& a, const Node& b, float inv_ds) {
-    const float deta = b.eta - a.eta;
-    const float sc = b.c + a.c;
-    const float dc = __fdividef(GRAV * (deta + (b.d - a.d)), sc);
-    const float sw = b.w + a.w;
-    const float hdw = 0.5f * (b.w - a.w);
-    const float y = sw * dc;
-    const float z = GRAV * deta;
-    Flux F;
-    F.p = fmaf(hdw, sw + sc, z + y) * inv_ds;
-    F.q = fmaf(hdw, sw - sc, z - y) * inv_ds;
-    F.t = 0.5f * sw * (b.t - a.t) * inv_ds;
+// eq. (eqQ) for p and q and the eq. (pq3) flux for t across two interfaces at once, each
+// between a left node a and a right node b, perturbation form, divided by the interval.
+__device__ __forceinline__ Flux2 iface2(float2 ea, float2 wa, float2 ta, float2 da, float2 ca,
+                                        float2 eb, float2 wb, float2 tb, float2 db, float2 cb,
+                                        float2 inv_ds) {
+    const float2 deta = sub2(eb, ea);
+    const float2 sc = add2(cb, ca);
+    const float2 num = mul2(v2(GRAV), add2(deta, sub2(db, da)));
+    const float2 dc = mul2(num, make_float2(rcp_approx(sc.x), rcp_approx(sc.y)));
+    const float2 sw = add2(wb, wa);
+    const float2 hdw = mul2(v2(0.5f), sub2(wb, wa));
+    const float2 y = mul2(sw, dc);
+    const float2 z = mul2(v2(GRAV), deta);
+    Flux2 F;
+    F.p = mul2(fma2(hdw, add2(sw, sc), add2(z, y)), inv_ds);
+    F.q = mul2(fma2(hdw, sub2(sw, sc), sub2(z, y)), inv_ds);
+    F.t = mul2(mul2(mul2(v2(0.5f), sw), sub2(tb, ta)), inv_ds);
     return F;
 }
 
-// The same fluxes when the neighbour is the mirror ghost of n (eta_g = eta, d_g = d,
-// w_g = -w, t_g = t): a wall on the left of n, or on its right.
-__device__ __forceinline__ Flux ghost_left(const Node& n, float inv_ds) {
-    const float f = 2.f * n.w * n.c * inv_ds;
-    return Flux{f, -f, 0.f};
+// Fluxes when the neighbour is the mirror ghost of the node (eta_g = eta, d_g = d,
+// w_g = -w, t_g = t): a wall on its left gives (2wc, -2wc, 0)/dx, on its right the negation.
+__device__ __forceinline__ void ghost_left(float w, float c, float inv, float& p, float& q, float& t) {
+    const float f = 2.f * w * c * inv;
+    p = f; q = -f; t = 0.f;
 }
-__device__ __forceinline__ Flux ghost_right(const Node& n, float inv_ds) {
-    const float f = 2.f * n.w * n.c * inv_ds;
-    return Flux{-f, f, 0.f};
+__device__ __forceinline__ void ghost_right(float w, float c, float inv, float& p, float& q, float& t) {
+    const float f = 2.f * w * c * inv;
+    p = -f; q = f; t = 0.f;
 }
 
-// (d): eq. (solver2) at a wet node given its left and right interface fluxes.
-//   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep, else 0.
+// (d): eq. (solver2) at two nodes given their left and right interface fluxes.
+//   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep (SRC).
 // Friction: alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3) at time level n on both p and q,
 // clamped so that |alpha dt| <= |w|.
-__device__ __forceinline__ void node_update(const Node& n, const Flux& L, const Flux& R,
-                                            float k2, float sdt, const SweepConst& K,
-                                            float& eta2, float& w2, float& t2) {
-    const float lp = n.w + n.c;
-    const float lq = n.w - n.c;
-    float adt = 0.f;
+template <bool SRC>
+__device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float2 d, float2 c,
+                                             const Flux2& L, const Flux2& R, float2 k2, float2 sdt,
+                                             const SweepConst& K,
+                                             float2& e2, float2& w2, float2& t2) {
+    const float2 lp = add2(w, c);
+    const float2 lq = sub2(w, c);
+    const float2 nh = v2(-K.half_dt);
+    float2 dp = fma2(mul2(lp, k2), sub2(R.p, L.p), mul2(nh, add2(L.p, R.p)));
+    float2 dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(nh, add2(L.q, R.q)));
     if (K.dt_gn2 > 0.f) {
-        const float h = n.eta + n.d;
-        const float s = sqrtf(fmaf(n.w, n.w, n.t * n.t));
-        adt = __fdividef(K.dt_gn2 * n.w * s, h * cbrtf(h));
-        if (fabsf(adt) > fabsf(n.w)) adt = n.w;
+        const float2 h = add2(e, d);
+        const float2 s2 = fma2(w, w, mul2(t, t));
+        const float2 s = mul2(s2, make_float2(rsqrt_approx(fmaxf(s2.x, 1e-30f)),
+                                              rsqrt_approx(fmaxf(s2.y, 1e-30f))));
+        float2 adt = mul2(mul2(mul2(v2(K.dt_gn2), w), s), make_float2(pow_m43(h.x), pow_m43(h.y)));
+        if (fabsf(adt.x) > fabsf(w.x)) adt.x = w.x;
+        if (fabsf(adt.y) > fabsf(w.y)) adt.y = w.y;
+        dp = sub2(dp, adt);
+        dq = sub2(dq, adt);
     }
-    const float src = sdt * n.c * n.w;
-    const float dp = -K.half_dt * (L.p + R.p) + lp * k2 * (R.p - L.p) - adt + src;
-    const float dq = -K.half_dt * (L.q + R.q) + lq * k2 * (R.q - L.q) - adt - src;
-    const float du = 0.5f * (dp + dq);
-    const float dc = 0.25f * (dp - dq);
-    w2 = n.w + du;
-    eta2 = n.eta + dc * (2.f * n.c + dc) * INV_GRAV;
-    t2 = K.transverse ? n.t - K.half_dt * (L.t + R.t) + n.w * k2 * (R.t - L.t) : n.t;
+    if (SRC) {
+        const float2 src = mul2(mul2(sdt, c), w);
+        dp = add2(dp, src);
+        dq = sub2(dq, src);
+    }
+    const float2 du = mul2(v2(0.5f), add2(dp, dq));
+    const float2 dc = mul2(v2(0.25f), sub2(dp, dq));
+    w2 = add2(w, du);
+    e2 = fma2(mul2(dc, fma2(v2(2.f), c, dc)), v2(INV_GRAV), e);
+    if (K.transverse)
+        t2 = fma2(mul2(w, k2), sub2(R.t, L.t), fma2(nh, add2(L.t, R.t), t));
+    else
+        t2 = t;
 }
 
 // (e): a node wetted in (b) against its source neighbour's state after (d).
@@ -134,121 +165,212 @@ __device__ __forceinline__ void cushion(float& e, float& w, float d, float hj, f
     if (fabsf(w) > fabsf(wj)) w = wj;
 }
 
-struct XMet { float inv_l, inv_r, k2; };   // 1/dx_{j-1}, 1/dx_j, dt^2/(dx_{j-1}+dx_j)
-
-// x-sweep of one row segment held by a warp: lane l has nodes A (window column 2l) and
-// B (2l+1). Neighbours across lanes come by shuffles. On return (eA,wA,tA) and (eB,wB,tB)
-// hold the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each
-// side lack their 3-node dependency radius).
-__device__ __forceinline__ void xsweep_pair(float& eA, float& wA, float& tA, float dA,
-                                            float& eB, float& wB, float& tB, float dB,
-                                            const XMet& mA, const XMet& mB,
-                                            const SweepConst& K, int lane) {
-    const bool oA = wet_mark(eA, dA, K), oB = wet_mark(eB, dB, K);
-    const unsigned bA = __ballot_sync(FULL, oA), bB = __ballot_sync(FULL, oB);
-    Node nA{eA, wA, tA, dA, 0.f, oA, 0};
-    Node nB{eB, wB, tB, dB, 0.f, oB, 0};
-    if ((bA & bB) != FULL) {
-        const float eL = __shfl_up_sync(FULL, eB, 1), wL = __shfl_up_sync(FULL, wB, 1);
-        const float tL = __shfl_up_sync(FULL, tB, 1);
-        const float eR = __shfl_down_sync(FULL, eA, 1), wR = __shfl_down_sync(FULL, wA, 1);
-        const float tR = __shfl_down_sync(FULL, tA, 1);
-        const bool oL = lane > 0 && ((bB >> (lane - 1)) & 1u);
-        const bool oR = lane < 31 && ((bA >> (lane + 1)) & 1u);
-        flood(nA, eL, wL, tL, oL, eB, wB, tB, oB, K);
-        flood(nB, eA, wA, tA, oA, eR, wR, tR, oR, K);
-    }
-    nA.c = sqrtf(GRAV * (nA.eta + nA.d));
-    nB.c = sqrtf(GRAV * (nB.eta + nB.d));
-    // post-(b) state of the right neighbour of B (node A of lane + 1)
-    Node nR;
-    nR.eta = __shfl_down_sync(FULL, nA.eta, 1);
-    nR.w = __shfl_down_sync(FULL, nA.w, 1);
-    nR.t = __shfl_down_sync(FULL, nA.t, 1);
-    nR.d = __shfl_down_sync(FULL, nA.d, 1);
-    nR.c = __shfl_down_sync(FULL, nA.c, 1);
-    const unsigned wA1 = __ballot_sync(FULL, nA.wet), wB1 = __ballot_sync(FULL, nB.wet);
-    nR.wet = lane < 31 && ((wA1 >> (lane + 1)) & 1u);
-    const bool wetL = lane > 0 && ((wB1 >> (lane - 1)) & 1u);
-    const Flux fAB = iface(nA, nB, mA.inv_r);
-    const Flux fBR = iface(nB, nR, mB.inv_r);
-    Flux fLA;
-    fLA.p = __shfl_up_sync(FULL, fBR.p, 1);
-    fLA.q = __shfl_up_sync(FULL, fBR.q, 1);
-    fLA.t = __shfl_up_sync(FULL, fBR.t, 1);
-    float e2A = nA.eta, w2A = nA.w, t2A = nA.t;
-    float e2B = nB.eta, w2B = nB.w, t2B = nB.t;
-    if (nA.wet) {
-        const Flux L = wetL ? fLA : ghost_left(nA, mA.inv_l);
-        const Flux R = nB.wet ? fAB : ghost_right(nA, mA.inv_r);
-        node_update(nA, L, R, mA.k2, 0.f, K, e2A, w2A, t2A);
-    }
-    if (nB.wet) {
-        const Flux L = nA.wet ? fAB : ghost_left(nB, mB.inv_l);
-        const Flux R = nR.wet ? fBR : ghost_right(nB, mB.inv_r);
-        node_update(nB, L, R, mB.k2, 0.f, K, e2B, w2B, t2B);
-    }
-    if (__any_sync(FULL, (nA.dir | nB.dir) != 0)) {
-        const float hA = e2A + dA, hB = e2B + dB;
-        const float hL = __shfl_up_sync(FULL, hB, 1), wLn = __shfl_up_sync(FULL, w2B, 1);
-        const float hR = __shfl_down_sync(FULL, hA, 1), wRn = __shfl_down_sync(FULL, w2A, 1);
-        const float w2A0 = w2A, w2B0 = w2B;
-        if (nA.dir < 0) cushion(e2A, w2A, dA, hL, wLn);
-        else if (nA.dir > 0) cushion(e2A, w2A, dA, hB, w2B0);
-        if (nB.dir < 0) cushion(e2B, w2B, dB, hA, w2A0);
-        else if (nB.dir > 0) cushion(e2B, w2B, dB, hR, wRn);
-    }
-    eA = e2A; wA = w2A; tA = t2A;
-    eB = e2B; wB = w2B; tB = t2B;
+// (b) for one node i, dry at the start of the sweep and not a wall, with neighbours L and R
+// (start-of-sweep eta, w, t and wet marks): the wetter neighbour (larger eta) wins, the
+// left one on a tie. Returns the direction of the source (-1, +1) or 0.
+__device__ __forceinline__ int flood1(float& e, float& w, float& t, float d,
+                                      float eL, float wL, float tL, bool oL,
+                                      float eR, float wR, float tR, bool oR, float hmin) {
+    const bool okL = oL && (eL + d > hmin);
+    const bool okR = oR && (eR + d > hmin);
+    if (!(okL || okR)) return 0;
+    const bool useR = okR && (!okL || eR > eL);
+    e = hmin - d;                                              // height h_min
+    w = useR ? wR : wL;
+    t = useR ? tR : tL;
+    return useR ? 1 : -1;
 }
 
-// y-sweep of one column as a march down the rows. Each push takes the sweep input of row k
-// and returns the finished result of row k - 3: (b) runs on row k-1, the interface flux
-// between rows k-2 and k-1 is formed once and shared, (d) runs on row k-2 and (e) on k-3.
-struct YMarch {
-    float e2, w2, t2, d2; bool o2;          // input, row k-2
-    float e1, w1, t1, d1; bool o1;          // input, row k-1
-    Node  b2;                               // after (b), row k-2
-    Flux  f3; bool wet3;                    // flux (k-3 | k-2), wet mark of row k-3 after (b)
-    float de4, dw4, dd4;                    // after (d), row k-4
-    float de3, dw3, dt3, dd3; int dir3;     // after (d), row k-3
+struct XMet2 { float2 inv_l, inv_r, k2; };   // per pair: 1/dx_{j-1}, 1/dx_j, dt^2/(dx_{j-1}+dx_j)
+
+// x-sweep of one row segment held by a warp: lane l has nodes A = window column 2l (.x)
+// and B = 2l + 1 (.y). Neighbours across lanes come by shuffles. On return (E, W, T) hold
+// the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each side
+// lack their 3-node dependency radius). W is the velocity along the row, T across it.
+__device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
+                                        const SweepConst& K, int lane) {
+    const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
+    const unsigned bA = __ballot_sync(FULL, oA), bB = __ballot_sync(FULL, oB);
+    const bool allwet = (bA & bB) == FULL;
+    bool wA = oA, wB = oB;                 // wet after (b)
+    int dirA = 0, dirB = 0;
+    if (!allwet) {
+        if (!oA) { W.x = 0.f; T.x = 0.f; }   // (a): a dry node is at rest
+        if (!oB) { W.y = 0.f; T.y = 0.f; }
+        const bool oL = lane > 0 && ((bB >> (lane - 1)) & 1u);
+        const bool oR = lane < 31 && ((bA >> (lane + 1)) & 1u);
+        const bool cA = !oA && D.x >= K.dwall && (oL || oB);
+        const bool cB = !oB && D.y >= K.dwall && (oA || oR);
+        if (__any_sync(FULL, cA || cB)) {
+            const float eL = __shfl_up_sync(FULL, E.y, 1), eR = __shfl_down_sync(FULL, E.x, 1);
+            const bool qA = cA && ((oL && eL + D.x > K.hmin) || (oB && E.y + D.x > K.hmin));
+            const bool qB = cB && ((oA && E.x + D.y > K.hmin) || (oR && eR + D.y > K.hmin));
+            if (__any_sync(FULL, qA || qB)) {
+                const float wL = __shfl_up_sync(FULL, W.y, 1), tL = __shfl_up_sync(FULL, T.y, 1);
+                const float wR = __shfl_down_sync(FULL, W.x, 1), tR = __shfl_down_sync(FULL, T.x, 1);
+                const float eA0 = E.x, wA0 = W.x, tA0 = T.x;     // A as the source of B
+                if (qA) {
+                    dirA = flood1(E.x, W.x, T.x, D.x, eL, wL, tL, oL, E.y, W.y, T.y, oB, K.hmin);
+                    wA = true;
+                }
+                if (qB) {
+                    dirB = flood1(E.y, W.y, T.y, D.y, eA0, wA0, tA0, oA, eR, wR, tR, oR, K.hmin);
+                    wB = true;
+                }
+            }
+        }
+    }
+    const float2 C = wave_speed2(add2(E, D));
+    // post-(b) state of the right neighbour of B (node A of lane + 1)
+    const float eR = __shfl_down_sync(FULL, E.x, 1), wR = __shfl_down_sync(FULL, W.x, 1);
+    const float tR = __shfl_down_sync(FULL, T.x, 1), dR = __shfl_down_sync(FULL, D.x, 1);
+    const float cR = __shfl_down_sync(FULL, C.x, 1);
+    // right interfaces of A and B: (A|B) and (B|R)
+    Flux2 FR = iface2(E, W, T, D, C, make_float2(E.y, eR), make_float2(W.y, wR),
+                      make_float2(T.y, tR), make_float2(D.y, dR), make_float2(C.y, cR), m.inv_r);
+    // left interfaces: (B_{l-1}|A) from the lane below, and (A|B)
+    Flux2 FL;
+    FL.p = make_float2(__shfl_up_sync(FULL, FR.p.y, 1), FR.p.x);
+    FL.q = make_float2(__shfl_up_sync(FULL, FR.q.y, 1), FR.q.x);
+    FL.t = make_float2(__shfl_up_sync(FULL, FR.t.y, 1), FR.t.x);
+    if (!allwet) {
+        // (c): walls between wet and dry nodes
+        const unsigned w1A = __ballot_sync(FULL, wA), w1B = __ballot_sync(FULL, wB);
+        const bool wetL = lane > 0 && ((w1B >> (lane - 1)) & 1u);
+        const bool wetR = lane < 31 && ((w1A >> (lane + 1)) & 1u);
+        if (!wetL) ghost_left(W.x, C.x, m.inv_l.x, FL.p.x, FL.q.x, FL.t.x);
+        if (!wB) ghost_right(W.x, C.x, m.inv_r.x, FR.p.x, FR.q.x, FR.t.x);
+        if (!wA) ghost_left(W.y, C.y, m.inv_l.y, FL.p.y, FL.q.y, FL.t.y);
+        if (!wetR) ghost_right(W.y, C.y, m.inv_r.y, FR.p.y, FR.q.y, FR.t.y);
+    }
+    float2 E2, W2, T2;
+    node_update2<false>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2);
+    if (!allwet) {
+        if (!wA) { E2.x = E.x; W2.x = W.x; T2.x = T.x; }
+        if (!wB) { E2.y = E.y; W2.y = W.y; T2.y = T.y; }
+        if (__any_sync(FULL, (dirA | dirB) != 0)) {
+            const float hA = E2.x + D.x, hB = E2.y + D.y;
+            const float hL = __shfl_up_sync(FULL, hB, 1), wLn = __shfl_up_sync(FULL, W2.y, 1);
+            const float hR = __shfl_down_sync(FULL, hA, 1), wRn = __shfl_down_sync(FULL, W2.x, 1);
+            const float w2A0 = W2.x, w2B0 = W2.y;
+            if (dirA < 0) cushion(E2.x, W2.x, D.x, hL, wLn);
+            else if (dirA > 0) cushion(E2.x, W2.x, D.x, hB, w2B0);
+            if (dirB < 0) cushion(E2.y, W2.y, D.y, hA, w2A0);
+            else if (dirB > 0) cushion(E2.y, W2.y, D.y, hR, wRn);
+        }
+    }
+    E = E2; W = W2; T = T2;
+}
+
+// One row of a pair of columns in the y-sweep pipeline.
+struct YRow {
+    float2 e, w, t, d, c;     // w: velocity along the column (v), t: across it (u)
+    bool oA, oB;              // wet at the start of the sweep (a)
+    bool wA, wB;              // wet after (b)
+    int dA, dB;               // (b) source direction
+};
+
+// y-sweep of a pair of columns as a march down the rows. Each push takes the sweep input of
+// row k and returns the finished result of row k - 3: (b) runs on row k-1, the interface
+// flux between rows k-2 and k-1 is formed once and shared, (d) runs on row k-2 and (e) on
+// k-3. Rows k-2 and k-1 live in two banks whose roles swap every push (PH), so the
+// pipeline advances without copying them. Row k-2 is held after (b) only: when it was wet
+// at the start of the sweep its values are its start-of-sweep values, which is all step
+// (b) of row k-1 needs from it.
+struct YMarch2 {
+    YRow bank[2];             // [PH]: row k-2 after (b); [1-PH]: row k-1 as input
+    Flux2 fb[2];              // [PH]: flux (k-3 | k-2)
+    bool f3A, f3B;            // row k-3 wet after (b)
+    float2 e3, w3, t3, d3;    // row k-3 after (d)
+    int dir3A, dir3B;
+    float2 h4, w4;            // row k-4 after (d): height, velocity
 
     __device__ __forceinline__ void init() {
-        e2 = w2 = t2 = 0.f; d2 = OUTSIDE_D; o2 = false;
-        e1 = w1 = t1 = 0.f; d1 = OUTSIDE_D; o1 = false;
-        b2 = Node{0.f, 0.f, 0.f, OUTSIDE_D, 0.f, false, 0};
-        f3 = Flux{0.f, 0.f, 0.f}; wet3 = false;
-        de4 = dw4 = 0.f; dd4 = OUTSIDE_D;
-        de3 = dw3 = dt3 = 0.f; dd3 = OUTSIDE_D; dir3 = 0;
+        for (int i = 0; i < 2; ++i) {
+            bank[i].e = bank[i].w = bank[i].t = bank[i].c = v2(0.f);
+            bank[i].d = v2(OUTSIDE_D);
+            bank[i].oA = bank[i].oB = bank[i].wA = bank[i].wB = false;
+            bank[i].dA = bank[i].dB = 0;
+            fb[i].p = fb[i].q = fb[i].t = v2(0.f);
+        }
+        f3A = f3B = false;
+        e3 = w3 = t3 = v2(0.f);
+        d3 = v2(OUTSIDE_D);
+        dir3A = dir3B = 0;
+        h4 = w4 = v2(0.f);
     }
 
-    // m2: metric of row k-2 (inv_l, inv_r, k2, sdt); returns (oe, ow, ot) of row k-3
-    __device__ __forceinline__ void push(float e0, float w0, float t0, float d0, float4 m2,
-                                         const SweepConst& K, float& oe, float& ow, float& ot) {
-        const bool o0 = wet_mark(e0, d0, K);
-        Node b1{e1, w1, t1, d1, 0.f, o1, 0};
-        flood(b1, e2, w2, t2, o2, e0, w0, t0, o0, K);
-        b1.c = sqrtf(GRAV * (b1.eta + b1.d));
-        const Flux f2 = iface(b2, b1, m2.y);
-        float ne = b2.eta, nw = b2.w, nt = b2.t;
-        if (b2.wet) {
-            const Flux L = wet3 ? f3 : ghost_left(b2, m2.x);
-            const Flux R = b1.wet ? f2 : ghost_right(b2, m2.y);
-            node_update(b2, L, R, m2.z, m2.w, K, ne, nw, nt);
+    // m2: metric of row k-2 (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R).
+    // emit(e, w, t, d) receives the finished row k-3; o0A/o0B: the incoming row's wet marks.
+    // careA/careB: whether this lane's columns are emitted; the others may compute anything.
+    template <int PH, bool SRC, class Emit>
+    __device__ __forceinline__ void push(float2 E0, float2 W0, float2 T0, float2 D0, bool o0A, bool o0B,
+                                         float4 m2, const SweepConst& K, bool careA, bool careB,
+                                         Emit&& emit) {
+        YRow& P = bank[PH];
+        YRow& B1 = bank[1 - PH];
+        Flux2& F3 = fb[PH];
+        Flux2& F2 = fb[1 - PH];
+        // rows k-3..k-1 wet in (a) and no newly wetted row k-3: no (b), no walls, no (e)
+        const bool openA = B1.oA && P.wA && f3A && dir3A == 0;
+        const bool openB = B1.oB && P.wB && f3B && dir3B == 0;
+        if (__all_sync(FULL, (!careA || openA) && (!careB || openB))) {
+            B1.wA = B1.wB = true;
+            B1.dA = B1.dB = 0;
+            B1.c = wave_speed2(add2(B1.e, B1.d));
+            F2 = iface2(P.e, P.w, P.t, P.d, P.c, B1.e, B1.w, B1.t, B1.d, B1.c, v2(m2.y));
+            emit(e3, w3, t3, d3);
+            h4 = add2(e3, d3);
+            w4 = w3;
+            node_update2<SRC>(P.e, P.w, P.t, P.d, P.c, F3, F2, v2(m2.z), v2(m2.w), K, e3, w3, t3);
+        } else {
+            // (a)/(b) on row k-1 (input held in B1), neighbours row k-2 (P) and row k (new)
+            B1.wA = B1.oA;
+            B1.wB = B1.oB;
+            B1.dA = B1.dB = 0;
+            if (!B1.oA) {
+                B1.w.x = 0.f; B1.t.x = 0.f;
+                if (B1.d.x >= K.dwall) {
+                    B1.dA = flood1(B1.e.x, B1.w.x, B1.t.x, B1.d.x, P.e.x, P.w.x, P.t.x, P.oA,
+                                   E0.x, W0.x, T0.x, o0A, K.hmin);
+                    B1.wA = B1.dA != 0;
+                }
+            }
+            if (!B1.oB) {
+                B1.w.y = 0.f; B1.t.y = 0.f;
+                if (B1.d.y >= K.dwall) {
+                    B1.dB = flood1(B1.e.y, B1.w.y, B1.t.y, B1.d.y, P.e.y, P.w.y, P.t.y, P.oB,
+                                   E0.y, W0.y, T0.y, o0B, K.hmin);
+                    B1.wB = B1.dB != 0;
+                }
+            }
+            B1.c = wave_speed2(add2(B1.e, B1.d));
+            F2 = iface2(P.e, P.w, P.t, P.d, P.c, B1.e, B1.w, B1.t, B1.d, B1.c, v2(m2.y));
+            // (c): walls, then (d) on row k-2
+            Flux2 L = F3, R = F2;
+            if (P.wA && !f3A) ghost_left(P.w.x, P.c.x, m2.x, L.p.x, L.q.x, L.t.x);
+            if (P.wA && !B1.wA) ghost_right(P.w.x, P.c.x, m2.y, R.p.x, R.q.x, R.t.x);
+            if (P.wB && !f3B) ghost_left(P.w.y, P.c.y, m2.x, L.p.y, L.q.y, L.t.y);
+            if (P.wB && !B1.wB) ghost_right(P.w.y, P.c.y, m2.y, R.p.y, R.q.y, R.t.y);
+            float2 ne, nw, nt;
+            node_update2<SRC>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt);
+            if (!P.wA) { ne.x = P.e.x; nw.x = P.w.x; nt.x = P.t.x; }
+            if (!P.wB) { ne.y = P.e.y; nw.y = P.w.y; nt.y = P.t.y; }
+            // (e) on row k-3, against row k-4 (h4, w4) or row k-2 (ne, nw)
+            float2 oe = e3, ow = w3;
+            if (dir3A != 0) cushion(oe.x, ow.x, d3.x, dir3A < 0 ? h4.x : ne.x + P.d.x, dir3A < 0 ? w4.x : nw.x);
+            if (dir3B != 0) cushion(oe.y, ow.y, d3.y, dir3B < 0 ? h4.y : ne.y + P.d.y, dir3B < 0 ? w4.y : nw.y);
+            emit(oe, ow, t3, d3);
+            h4 = add2(e3, d3);
+            w4 = w3;
+            e3 = ne; w3 = nw; t3 = nt;
         }
-        float fe = de3, fw = dw3;
-        if (dir3 != 0) {
-            const float hj = (dir3 < 0) ? de4 + dd4 : ne + b2.d;
-            const float wj = (dir3 < 0) ? dw4 : nw;
-            cushion(fe, fw, dd3, hj, wj);
-        }
-        oe = fe; ow = fw; ot = dt3;
-        de4 = de3; dw4 = dw3; dd4 = dd3;
-        de3 = ne; dw3 = nw; dt3 = nt; dd3 = b2.d; dir3 = b2.dir;
-        f3 = f2; wet3 = b2.wet;
-        b2 = b1;
-        e2 = e1; w2 = w1; t2 = t1; d2 = d1; o2 = o1;
-        e1 = e0; w1 = w0; t1 = t0; d1 = d0; o1 = o0;
+        d3 = P.d;
+        dir3A = P.dA; dir3B = P.dB;
+        f3A = P.wA; f3B = P.wB;
+        // row k takes the freed bank
+        P.e = E0; P.w = W0; P.t = T0; P.d = D0;
+        P.oA = o0A; P.oB = o0B;
     }
 };
 

@@ -13,7 +13,8 @@ import pytest
 
 import oracle
 import workloads
-from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG, ERR_STATE, ERR_UNSTABLE
+from paper_1410_0753_gb300 import (CliffsError, CliffsGrid, ERR_ARG, ERR_STATE, ERR_TIMEOUT,
+                                   ERR_UNSTABLE, cliffs_inject_wait_expiry)
 from tests import parity as P
 
 pytestmark = pytest.mark.gpu
@@ -373,3 +374,47 @@ def test_error_paths():
     with pytest.raises(CliffsError) as e:
         CliffsGrid(20, 20, 0.1, gauges=[(25, 3)])
     assert e.value.code == ERR_ARG
+
+
+def test_bounded_wait_expiry_reports_timeout_and_recovers():
+    """A ring wait that can never complete (injected: the slots expect bytes no copy
+    delivers) expires after its cycle limit; the step reports CLIFFS_ERR_TIMEOUT, the later
+    launches of the call return at once, and the grid keeps working."""
+    w = workloads.beach_200(120, 90, steps=20)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    cliffs_inject_wait_expiry(g.h, 2_000_000)           # ~1 ms per wait
+    with pytest.raises(CliffsError) as e:
+        g.step(5)
+    assert e.value.code == ERR_TIMEOUT
+    g.set_initial(w.eta0.astype(np.float32))
+    g.step(w.steps)
+    ref = CliffsGrid.from_workload(w)
+    ref.set_bathy(w.x, w.y, w.depth)
+    ref.set_initial(w.eta0.astype(np.float32))
+    ref.step(w.steps)
+    assert np.array_equal(g.state()[0], ref.state()[0])
+    g.close()
+    ref.close()
+
+
+def test_autotuned_tile_shape_gives_identical_results():
+    """The rows-per-warp tile shape changes only how the work is split: every output node is
+    computed by the same arithmetic, so any shape gives the same bits."""
+    w = workloads.spherical_coast(300, 260, steps=80)
+    runs = []
+    for tune in (False, True):
+        g = CliffsGrid.from_workload(w)
+        g.set_bathy(w.x, w.y, w.depth)
+        g.set_initial(w.eta0.astype(np.float32))
+        if tune:
+            table = g.autotune(2)
+            assert len(table) >= 3 and all(t > 0 for t in table.values())
+        g.step(w.steps)
+        runs.append((g.state(), g.gauges(), g.maxwave(), g.boundary(0, 2)))
+        g.close()
+    (s0, g0, m0, b0), (s1, g1, m1, b1) = runs
+    for x, y in zip(s0 + m0, s1 + m1):
+        assert np.array_equal(x, y)
+    assert np.array_equal(g0, g1) and np.array_equal(b0, b1)
