@@ -125,6 +125,21 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
  * (the state is left as computed); ERR_CUDA. */
 int cliffs_step_n(cliffs_grid* g, int64_t n);
 
+/* Advance n time steps like cliffs_step_n, with the same results bit for bit, in ONE kernel
+ * launch (no counterpart in the paper, which runs one scenario at a time): a persistent,
+ * cooperatively launched kernel whose warps take (scenario, tile) work items of the
+ * scenarios still running at each step and meet at a grid-wide barrier between steps.
+ * Scenarios are visited in decreasing order of their cliffs_set_durations limit, so a
+ * batch of uneven durations keeps every SM busy until the longest ends. The launch is
+ * captured once into a CUDA graph (a copy of the step range into a device control block,
+ * then the kernel) and replayed by later calls; it is captured again when a launch argument
+ * changes (tile shape, record buffers, durations). 2D grids only. The grid barrier waits
+ * at most about a second per step before it sets the timeout flag.
+ * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 0); ERR_UNSTABLE as for
+ * cliffs_step_n; ERR_TIMEOUT when a bounded wait gave up; ERR_CUDA (including a device
+ * that cannot launch cooperatively). */
+int cliffs_run_persistent(cliffs_grid* g, int64_t n);
+
 /* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
  * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
  * longer warps). Each candidate S is timed over `trials` launches (after one warm-up) that
@@ -140,8 +155,9 @@ int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32
  * its copies deliver, with waits limited to `cycles` clock cycles. Each wait then expires,
  * the kernel drains its copies (bounded), sets the timeout flag and returns; later launches
  * of the same call return at once; cliffs_step_n returns CLIFFS_ERR_TIMEOUT and the grid
- * stays usable (its state is whatever the interrupted step left). No GPU fault or hang is
- * involved. Errors: ERR_ARG (no grid, cycles <= 0, 1D grid). */
+ * stays usable (its state is whatever the interrupted step left). The injection applies to
+ * the next cliffs_step_n or cliffs_run_persistent call, whichever comes first. No GPU fault
+ * or hang is involved. Errors: ERR_ARG (no grid, cycles <= 0, 1D grid). */
 int cliffs_inject_wait_expiry(cliffs_grid* g, int64_t cycles);
 
 /* Steps completed since set_initial (for a batched grid, by the longest scenario). */

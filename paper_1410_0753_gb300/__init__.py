@@ -26,7 +26,7 @@ __all__ = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
-    "cliffs_inject_wait_expiry", "cliffs_autotune", "EXPORTED",
+    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -38,7 +38,7 @@ EXPORTED = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
-    "cliffs_inject_wait_expiry", "cliffs_autotune",
+    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent",
 ]
 
 
@@ -83,6 +83,7 @@ def lib():
             "cliffs_set_initial": ([vp, C.c_int, vp, vp, vp, C.c_int], C.c_int),
             "cliffs_set_durations": ([vp, vp], C.c_int),
             "cliffs_step_n": ([vp, C.c_int64], C.c_int),
+            "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_steps_done": ([vp, i64p], C.c_int),
             "cliffs_read_gauges": ([vp, C.c_int, vp, i64p], C.c_int),
             "cliffs_read_maxwave": ([vp, C.c_int, vp, vp], C.c_int),
@@ -168,6 +169,10 @@ def cliffs_set_durations(g, steps):
 
 def cliffs_step_n(g, n):
     _check(lib().cliffs_step_n(g, int(n)))
+
+
+def cliffs_run_persistent(g, n):
+    _check(lib().cliffs_run_persistent(g, int(n)))
 
 
 def cliffs_steps_done(g) -> int:
@@ -305,8 +310,13 @@ class CliffsGrid:
     def set_durations(self, steps):
         cliffs_set_durations(self.h, steps)
 
-    def step(self, n):
-        cliffs_step_n(self.h, n)
+    def step(self, n, persistent=False):
+        """Advance n steps: one launch per step, or (persistent=True) all n in one
+        persistent, graph-captured launch with identical results."""
+        if persistent:
+            cliffs_run_persistent(self.h, n)
+        else:
+            cliffs_step_n(self.h, n)
 
     @property
     def steps_done(self):

@@ -257,6 +257,18 @@ struct cliffs_grid {
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
     unsigned* ured = nullptr;
+    // persistent batched run: scenario order and running counts (from the durations), the
+    // device control block with its pinned host image, and the captured graph with the
+    // launch arguments it was captured with
+    int* order_d = nullptr;
+    int* nact_d = nullptr;
+    long long nact_len = 0;
+    long long* ctl_d = nullptr;
+    long long* ctl_h = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    int pblocks = 0;
 };
 
 namespace {
@@ -520,6 +532,10 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->err); cudaFree(g->limit); cudaFree(g->items_d); cudaFree(g->items_dev);
     cudaFree(g->samp_ptr); cudaFree(g->samp); cudaFree(g->grec); cudaFree(g->nrec);
     cudaFree(g->pt_slot); cudaFree(g->pt_w); cudaFree(g->tmp); cudaFree(g->ured);
+    cudaFree(g->order_d); cudaFree(g->nact_d); cudaFree(g->ctl_d);
+    if (g->ctl_h) cudaFreeHost(g->ctl_h);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->cap) cudaStreamDestroy(g->cap);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete g;
 }
@@ -871,6 +887,9 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
 int cliffs_set_durations(cliffs_grid* g, const int64_t* steps) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    cudaFree(g->order_d); cudaFree(g->nact_d);
+    g->order_d = g->nact_d = nullptr;
+    g->nact_len = 0;
     if (!steps) {
         g->limit_h.clear();
         cudaFree(g->limit);
@@ -884,6 +903,20 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps) {
     if (!g->limit) CK(cudaMalloc(&g->limit, sizeof(long long) * g->B));
     CK(cudaMemcpy(g->limit, h.data(), sizeof(long long) * g->B, cudaMemcpyHostToDevice));
     g->limit_h = h;
+    // for the persistent run: scenarios by decreasing duration (ties by index), and for each
+    // step s the number of scenarios still running there (limit >= s)
+    std::vector<int> order(g->B);
+    for (int b = 0; b < g->B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h[p] > h[q]; });
+    const long long L = h[order[0]] + 1;
+    std::vector<int> nact(L, 0);
+    for (int b = 0; b < g->B; ++b) nact[h[b]] += 1;          // scenarios ending at exactly s
+    for (long long t = L - 2; t >= 0; --t) nact[t] += nact[t + 1];
+    CK(cudaMalloc(&g->order_d, sizeof(int) * g->B));
+    CK(cudaMalloc(&g->nact_d, sizeof(int) * L));
+    CK(cudaMemcpy(g->order_d, order.data(), sizeof(int) * g->B, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g->nact_d, nact.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
+    g->nact_len = L;
     return CLIFFS_OK;
 }
 
@@ -933,6 +966,112 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
     int h[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(h, g->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h[0]) {
+        CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
+        if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
+        return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state before step %lld", (long long)g->step);
+    }
+    return CLIFFS_OK;
+}
+
+int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
+    if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
+    if (n == 0) return CLIFFS_OK;
+    const long long last = g->step + n;
+    int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
+    if (rc) return rc;
+    cudaStream_t s = g->stream;
+    if (!g->ctl_d) {
+        CK(cudaMalloc(&g->ctl_d, 4 * sizeof(long long)));
+        CK(cudaMallocHost(&g->ctl_h, 4 * sizeof(long long)));
+        CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        g->pblocks = sms * std::max(1, batch_blocks_per_sm(g->cfg.coords != 1));
+    }
+    // launch arguments; all padding zeroed so that they compare byte for byte
+    struct Key { StepArgs a; BatchArgs b; } k;
+    std::memset(&k, 0, sizeof(k));
+    fill_step_args(g, k.a, 0, 1);
+    k.a.eta_out = k.a.u_out = k.a.v_out = nullptr;
+    k.a.eta_in = k.a.u_in = k.a.v_in = nullptr;
+    k.a.limit = nullptr;
+    if (g->inject_cycles > 0) {
+        // fault injection: every ring slot of this run waits for bytes that never come
+        k.a.wait_cycles = g->inject_cycles;
+        k.a.tx_pad = 16;
+        g->inject_cycles = 0;
+    }
+    BatchArgs& b = k.b;
+    b.ctl = g->ctl_d;
+    b.order = g->order_d;
+    b.nact = g->nact_d;
+    b.nact_len = g->nact_len;
+    b.nall = g->B;
+    for (int i = 0; i < 2; ++i) { b.eta[i] = g->eta[i]; b.u[i] = g->u[i]; b.v[i] = g->v[i]; }
+    b.emax = g->emax; b.smax = g->smax;
+    b.maxout = g->cfg.maxout; b.gout = g->cfg.gout; b.bndout = g->cfg.bndout;
+    b.grec = g->G ? g->grec : nullptr;
+    b.grec_row = (long long)g->G * 3;
+    b.nrec = g->NN ? g->nrec : nullptr;
+    b.nrec_row = (long long)g->NN * 3;
+    if (!b.order) {                               // no durations: every scenario, in index order
+        std::vector<int> id(g->B);
+        for (int i = 0; i < g->B; ++i) id[i] = i;
+        CK(cudaMalloc(&g->order_d, sizeof(int) * g->B));
+        CK(cudaMemcpy(g->order_d, id.data(), sizeof(int) * g->B, cudaMemcpyHostToDevice));
+        b.order = g->order_d;
+    }
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&k);
+    if (!g->gexec || g->gkey.size() != sizeof(k) || std::memcmp(g->gkey.data(), kb, sizeof(k)) != 0) {
+        if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+        // the graph: copy the control block in from its pinned host image, then the
+        // cooperative launch
+        StepMaps2 mm;
+        mm.m[0] = g->maps[0];
+        mm.m[1] = g->maps[1];
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemcpyAsync(g->ctl_d, g->ctl_h, 4 * sizeof(long long), cudaMemcpyHostToDevice, g->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_batch(k.a, mm, b, g->pblocks, g->cap) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(g->cap, &graph);
+        if (e2 != cudaSuccess || e3 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return set_err(CLIFFS_ERR_CUDA, "capturing the persistent run: %s",
+                           cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+        }
+        cudaError_t e4 = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e4 != cudaSuccess) {
+            g->gexec = nullptr;
+            return set_err(CLIFFS_ERR_CUDA, "instantiating the persistent run: %s", cudaGetErrorString(e4));
+        }
+        g->gkey.assign(kb, kb + sizeof(k));
+    }
+    g->ctl_h[0] = g->step;
+    g->ctl_h[1] = last;
+    g->ctl_h[2] = 0;
+    g->ctl_h[3] = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g->timing) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, s));
+    }
+    CK(cudaGraphLaunch(g->gexec, s));
+    if (g->timing) {
+        CK(cudaEventRecord(e1, s));
+        g->ev.emplace_back(e0, e1);
+    }
+    g->step = last;
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, g->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));   // the pinned control block is free again after this
     if (h[0]) {
         CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
         if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");

@@ -100,31 +100,48 @@ __device__ __forceinline__ int runaway(float e, float u, float v) {
     return !(fabsf(e) + fabsf(u) + fabsf(v) < 3e5f);
 }
 
+// What changes from one step to the next: the input state's TMA descriptors, the output
+// planes, and the max-wave fields and record rows when they are due this step (else null).
+struct StepOut {
+    const StepMaps* M;
+    float* eta_out;
+    float* u_out;
+    float* v_out;
+    float* emax;
+    float* smax;
+    float* rec_g;
+    float* rec_n;
+};
+
+__device__ __forceinline__ StepOut step_out(const StepMaps* M, const StepArgs& a) {
+    return StepOut{M, a.eta_out, a.u_out, a.v_out, a.emax, a.smax, a.rec_g, a.rec_n};
+}
+
 // Store a finished pair of nodes of row r. With max-wave due, (em, sm) hold the stored
 // maxima of the pair (loaded beforehand) and are written back where they grow.
-__device__ __forceinline__ void emit_pair(const StepArgs& a, size_t o, bool va, bool vb,
+__device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, size_t o, bool va, bool vb,
                                           float2 E, float2 U, float2 V, float2 D,
-                                          bool withmax, float2 em, float2 sm, int& bad) {
+                                          float2 em, float2 sm, int& bad) {
     if (!va) return;
     if (vb) {
-        *reinterpret_cast<float2*>(a.eta_out + o) = E;
-        *reinterpret_cast<float2*>(a.u_out + o) = U;
-        *reinterpret_cast<float2*>(a.v_out + o) = V;
+        *reinterpret_cast<float2*>(O.eta_out + o) = E;
+        *reinterpret_cast<float2*>(O.u_out + o) = U;
+        *reinterpret_cast<float2*>(O.v_out + o) = V;
         bad |= runaway(E.x, U.x, V.x) | runaway(E.y, U.y, V.y);
     } else {
-        a.eta_out[o] = E.x; a.u_out[o] = U.x; a.v_out[o] = V.x;
+        O.eta_out[o] = E.x; O.u_out[o] = U.x; O.v_out[o] = V.x;
         bad |= runaway(E.x, U.x, V.x);
     }
-    if (withmax) {
+    if (O.emax) {
         bool ch = false;
         max_upd(em.x, sm.x, E.x, U.x, V.x, D.x, a, ch);
         if (vb) max_upd(em.y, sm.y, E.y, U.y, V.y, D.y, a, ch);
         if (ch) {
             if (vb) {
-                *reinterpret_cast<float2*>(a.emax + o) = em;
-                *reinterpret_cast<float2*>(a.smax + o) = sm;
+                *reinterpret_cast<float2*>(O.emax + o) = em;
+                *reinterpret_cast<float2*>(O.smax + o) = sm;
             } else {
-                a.emax[o] = em.x; a.smax[o] = sm.x;
+                O.emax[o] = em.x; O.smax[o] = sm.x;
             }
         }
     }
@@ -143,11 +160,11 @@ struct Samples {
         base = sp;
         mine = (sp + lane < se) ? __ldg(a.samp + sp + lane) : make_int4(0x7fffffff, 0, 0, 0);
     }
-    __device__ __forceinline__ void init(const StepArgs& a, int gw, int lane) {
+    __device__ __forceinline__ void init(const StepArgs& a, const StepOut& O, int gw, int lane) {
         sp = se = base = 0;
         next = 0x7fffffff;
         mine = make_int4(0x7fffffff, 0, 0, 0);
-        if (a.samp_ptr && (a.rec_g || a.rec_n)) {
+        if (a.samp_ptr && (O.rec_g || O.rec_n)) {
             sp = a.samp_ptr[gw];
             se = a.samp_ptr[gw + 1];
             if (sp < se) {
@@ -156,8 +173,8 @@ struct Samples {
             }
         }
     }
-    __device__ __forceinline__ void emit(const StepArgs& a, int b, int r, int c0, int lane,
-                                         float2 E, float2 U, float2 V) {
+    __device__ __forceinline__ void emit(const StepArgs& a, const StepOut& O, int b, int r, int c0,
+                                         int lane, float2 E, float2 U, float2 V) {
         if (r != next) return;
         while (true) {
             const bool mineRow = lane >= sp - base && mine.x == r;
@@ -168,8 +185,8 @@ struct Samples {
             const float vx = __shfl_sync(FULL, V.x, src), vy = __shfl_sync(FULL, V.y, src);
             if (mineRow) {
                 const bool isB = rel & 1;
-                float* out = (mine.z == 0) ? (a.rec_g ? a.rec_g + (long long)b * a.rec_g_bstride : nullptr)
-                                           : a.rec_n;
+                float* out = (mine.z == 0) ? (O.rec_g ? O.rec_g + (long long)b * a.rec_g_bstride : nullptr)
+                                           : O.rec_n;
                 if (out) {
                     out[3 * mine.w + 0] = isB ? ey : ex;
                     out[3 * mine.w + 1] = isB ? uy : ux;
@@ -190,34 +207,50 @@ struct Samples {
 };
 
 // ------------------------------------------------------------------ fused step
-// The work of one warp of k_step_fused: strip `strip`, output rows [r0, r1), walked as
-// row pairs k0 + 2j, k0 + 2j + 1, one pair per ring slot.
+// One warp of the fused step. A work item is a strip and an output row range [r0, r1); the
+// warp walks rows r0-3 .. r1+2 as pairs, one pair per ring slot. The ring's slot and phase
+// follow a running pair count, so a warp may process any number of items in a row.
 template <bool SPH>
 struct FusedWarp {
-    const StepMaps& M;
     const StepArgs& a;
     SweepConst K;
     float* ring;
     uint64_t* bar;
+    unsigned used;             // ring pairs consumed by this warp so far (2^32 is a multiple of 2 * RING)
     int lane, b, c0, cA, r0, r1, k0, npairs;
     size_t orow;               // output offset of row r0 (scenario plane + column)
-    bool withmax, colA, colB, vA, vB, edge;
+    bool colA, colB, vA, vB, edge;
     unsigned tx, nbox;
     XMet2 m0;
     YMarch2 ym;
     Samples smp;
+    StepOut O;
     int bad;
 
-    __device__ __forceinline__ FusedWarp(const StepMaps& M_, const StepArgs& a_) : M(M_), a(a_) {}
+    __device__ __forceinline__ FusedWarp(const StepArgs& a_) : a(a_) {}
 
-    // lanes 0..nbox-1 each start one 64 x 2 box of row pair j into its ring slot
+    __device__ __forceinline__ void setup(unsigned char* smem_raw, int wib) {
+        lane = threadIdx.x & 31;
+        K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+        ring = reinterpret_cast<float*>(smem_raw + wib * WARP_RING_BYTES);
+        bar = reinterpret_cast<uint64_t*>(smem_raw + FUSED_WARPS * WARP_RING_BYTES) + wib * RING;
+        used = 0;
+        bad = 0;
+        if (lane == 0) {
+            for (int s = 0; s < RING; ++s) mbar_init(&bar[s], 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
+
+    // lanes 0..nbox-1 each start one 64 x 2 box of the item's row pair j into its ring slot
     __device__ __forceinline__ void issue(int j) {
-        const int slot = j % RING;
+        const int slot = (int)((used + (unsigned)j) % RING);
         const int row = k0 + SLOT_ROWS * j;
         if (lane == 0) mbar_arrive_tx(&bar[slot], tx);
         if (lane < (int)nbox) {
             fence_proxy_async();
-            tma_row3(ring + slot * SLOT_FLOATS + lane * ARR_FLOATS, &M.e + lane, &bar[slot], c0,
+            tma_row3(ring + slot * SLOT_FLOATS + lane * ARR_FLOATS, &O.M->e + lane, &bar[slot], c0,
                      lane >= 4 ? row - 3 : row, lane == 3 ? 0 : b);
         }
     }
@@ -254,15 +287,70 @@ struct FusedWarp {
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     float2 em = make_float2(0.f, 0.f), sm = em;
-                    if (withmax) {
+                    if (O.emax) {
                         em = reinterpret_cast<const float2*>(s + 4 * ARR_FLOATS)[lane];
                         sm = reinterpret_cast<const float2*>(s + 5 * ARR_FLOATS)[lane];
                     }
-                    emit_pair(a, orow + (size_t)(r - r0) * a.pitch, vA, vB, oe, ot, ow, od,
-                              withmax, em, sm, bad);
-                    smp.emit(a, b, r, c0, lane, oe, ot, ow);
+                    emit_pair(a, O, orow + (size_t)(r - r0) * a.pitch, vA, vB, oe, ot, ow, od, em, sm, bad);
+                    smp.emit(a, O, b, r, c0, lane, oe, ot, ow);
                 }
             });
+    }
+
+    // Process work item `idx` (strip, rows) of scenario b_ for the step described by O_.
+    // Returns false when a wait expired (the warp's copies have landed when it returns).
+    __device__ __forceinline__ bool run_item(int idx, int b_, const StepOut& O_) {
+        O = O_;
+        b = b_;
+        const int4 item = __ldg(a.items + idx);          // (strip, first row, end row)
+        c0 = item.x * XOUT - 4;
+        cA = c0 + 2 * lane;
+        r0 = item.y;
+        r1 = item.z;
+        k0 = r0 - 3;
+        npairs = (r1 + 3 - k0 + 1) / 2;
+        orow = (size_t)b * a.plane + (size_t)r0 * a.pitch + cA;
+        nbox = O.emax ? 6u : 4u;
+        tx = nbox * ARR_FLOATS * 4u + a.tx_pad;
+        colA = cA >= 0 && cA < a.nx;
+        colB = cA + 1 >= 0 && cA + 1 < a.nx;
+        const bool own = lane >= 2 && lane < 30;
+        vA = own && colA;
+        vB = own && colB;
+        edge = c0 < 0 || c0 + XWIN > a.nx;
+        for (int j = 0; j < min(RING, npairs); ++j) issue(j);
+        float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
+        if (colA) { il.x = __ldg(a.xa + cA); ir.x = __ldg(a.xb + cA); k2.x = __ldg(a.xk + cA); }
+        if (colB) { il.y = __ldg(a.xa + cA + 1); ir.y = __ldg(a.xb + cA + 1); k2.y = __ldg(a.xk + cA + 1); }
+        m0 = XMet2{il, ir, k2};
+        smp.init(a, O, idx, lane);
+        ym.init();
+        int j = 0;
+        for (; j < npairs; ++j) {
+            const int slot = (int)((used + (unsigned)j) % RING);
+            const bool ok = mbar_wait(&bar[slot], ((used + (unsigned)j) / RING) & 1u, a.wait_cycles);
+            if (!__all_sync(FULL, ok)) break;
+            const float* s = ring + slot * SLOT_FLOATS;
+            const int k = k0 + SLOT_ROWS * j;
+            row<0>(k, s);
+            row<1>(k + 1, s + XWIN);
+            __syncwarp();
+            if (j + RING < npairs) issue(j + RING);
+        }
+        if (j < npairs) {
+            // a wait expired at pair j: pairs j .. j+RING-1 may still be in flight; let
+            // each land (bounded) before going on
+            for (int i = j; i < min(j + RING, npairs); ++i)
+                mbar_wait(&bar[(used + (unsigned)i) % RING], ((used + (unsigned)i) / RING) & 1u, a.wait_cycles);
+            bad |= 2;
+            return false;
+        }
+        used += (unsigned)npairs;
+        return true;
+    }
+
+    __device__ __forceinline__ void report() {
+        if (bad) atomicOr(a.err, (bad & 2) ? (ERRF_TIMEOUT | ERRF_NONFINITE) : ERRF_NONFINITE);
     }
 };
 
@@ -270,7 +358,6 @@ template <bool SPH>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * FUSED_WARPS + wib;
     const int b = blockIdx.y;
@@ -278,62 +365,86 @@ k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     if (a.limit && a.step > a.limit[b]) return;
     // a wait of an earlier launch expired: do not start new copies
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH> W(M, a);
-    W.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
-    W.ring = reinterpret_cast<float*>(smem_raw + wib * WARP_RING_BYTES);
-    W.bar = reinterpret_cast<uint64_t*>(smem_raw + FUSED_WARPS * WARP_RING_BYTES) + wib * RING;
-    const int4 item = __ldg(a.items + gw);          // (strip, first row, end row)
-    W.lane = lane;
-    W.b = b;
-    W.c0 = item.x * XOUT - 4;
-    W.cA = W.c0 + 2 * lane;
-    W.r0 = item.y;
-    W.r1 = item.z;
-    W.k0 = W.r0 - 3;
-    W.npairs = (W.r1 + 3 - W.k0 + 1) / 2;
-    W.orow = (size_t)b * a.plane + (size_t)W.r0 * a.pitch + W.cA;
-    W.withmax = a.emax != nullptr;
-    W.nbox = W.withmax ? 6u : 4u;
-    W.tx = W.nbox * ARR_FLOATS * 4u + a.tx_pad;
-    W.colA = W.cA >= 0 && W.cA < a.nx;
-    W.colB = W.cA + 1 >= 0 && W.cA + 1 < a.nx;
-    const bool own = lane >= 2 && lane < 30;
-    W.vA = own && W.colA;
-    W.vB = own && W.colB;
-    W.edge = W.c0 < 0 || W.c0 + XWIN > a.nx;
-    W.bad = 0;
-    if (lane == 0) {
-        for (int s = 0; s < RING; ++s) mbar_init(&W.bar[s], 1);
-        fence_mbar_init();
+    FusedWarp<SPH> W(a);
+    W.setup(smem_raw, wib);
+    W.run_item(gw, b, step_out(&M, a));
+    W.report();
+}
+
+// ------------------------------------------------------------------ batched, persistent
+// Grid-wide barrier of a cooperative launch. Thread 0 of every block adds one arrival to the
+// low half of *bar; the last arrival clears the count and advances the generation in the high
+// half, which the others wait on for at most `limit` cycles before setting the timeout flag.
+// Returns false when the run must stop (a wait expired here or anywhere else).
+__device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned nblocks, long long limit, int* err) {
+    __shared__ int go;
+    asm volatile("fence.proxy.async.global;" ::: "memory");    // outputs before the next TMA reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned long long old = atomicAdd(bar, 1ull);
+        const unsigned gen = (unsigned)(old >> 32);
+        if ((unsigned)old == nblocks - 1) {
+            // last arrival: count back to zero and generation + 1, in one atomic
+            atomicAdd(bar, (1ull << 32) - (unsigned long long)nblocks);
+        } else {
+            volatile unsigned* vgen = reinterpret_cast<volatile unsigned*>(bar) + 1;
+            const long long t0 = clock64();
+            while (*vgen == gen) {
+                if (clock64() - t0 > limit) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (!ok) atomicOr(err, ERRF_TIMEOUT);
+        go = ok && !(*reinterpret_cast<volatile int*>(err) & ERRF_TIMEOUT);
     }
-    __syncwarp();
-    for (int j = 0; j < min(RING, W.npairs); ++j) W.issue(j);
-    float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
-    if (W.colA) { il.x = __ldg(a.xa + W.cA); ir.x = __ldg(a.xb + W.cA); k2.x = __ldg(a.xk + W.cA); }
-    if (W.colB) { il.y = __ldg(a.xa + W.cA + 1); ir.y = __ldg(a.xb + W.cA + 1); k2.y = __ldg(a.xk + W.cA + 1); }
-    W.m0 = XMet2{il, ir, k2};
-    W.smp.init(a, gw, lane);
-    W.ym.init();
-    int j = 0;
-    for (; j < W.npairs; ++j) {
-        const int slot = j % RING;
-        const bool ok = mbar_wait(&W.bar[slot], (unsigned)(j / RING) & 1u, a.wait_cycles);
-        if (!__all_sync(FULL, ok)) break;
-        const float* s = W.ring + slot * SLOT_FLOATS;
-        const int k = W.k0 + SLOT_ROWS * j;
-        W.template row<0>(k, s);
-        W.template row<1>(k + 1, s + XWIN);
-        __syncwarp();
-        if (j + RING < W.npairs) W.issue(j + RING);
+    __syncthreads();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return go;
+}
+
+// Steps ctl[0]+1 .. ctl[1] of a batch of scenarios in one launch. Scenarios are taken in
+// decreasing order of duration, so those still running at a step are the first nact[step]
+// of `order`; the step's (scenario, item) pairs are numbered scenario-major and each warp
+// takes the next number from a ticket counter until none are left, then the warps meet at
+// the grid barrier before the next step reads what this one wrote. Two ticket counters
+// (the halves of ctl[3]) alternate by step parity; block 0 clears the one the next step
+// uses while the other is in use. A scenario that has stopped keeps its last state in the
+// buffer of its last step's parity.
+template <bool SPH>
+__global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
+k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs B) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const long long step0 = B.ctl[0], step_end = B.ctl[1];
+    unsigned* tickets = reinterpret_cast<unsigned*>(B.ctl + 3);
+    if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
+    FusedWarp<SPH> W(a);
+    W.setup(smem_raw, wib);
+    for (long long st = step0 + 1; st <= step_end; ++st) {
+        const bool odd = (st & 1) != 0;          // odd steps read buffer 0 and write buffer 1
+        const bool mx = st % B.maxout == 0;
+        StepOut O{odd ? &MM.m[0] : &MM.m[1], odd ? B.eta[1] : B.eta[0], odd ? B.u[1] : B.u[0],
+                  odd ? B.v[1] : B.v[0], mx ? B.emax : nullptr, mx ? B.smax : nullptr,
+                  (B.grec && st % B.gout == 0) ? B.grec + (st / B.gout) * B.grec_row : nullptr,
+                  (B.nrec && st % B.bndout == 0) ? B.nrec + (st / B.bndout) * B.nrec_row : nullptr};
+        const int na = B.nact ? (st < B.nact_len ? __ldg(B.nact + st) : 0) : B.nall;
+        const unsigned total = (unsigned)na * (unsigned)a.nitems;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(tickets + (odd ? 0 : 1), 0u);
+        bool ok = true;
+        while (ok) {
+            unsigned t = 0;
+            if (W.lane == 0) t = atomicAdd(tickets + (odd ? 1 : 0), 1u);
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= total) break;
+            ok = W.run_item((int)(t % (unsigned)a.nitems), __ldg(B.order + t / (unsigned)a.nitems), O);
+        }
+        if (!ok && W.lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
+        if (!grid_sync(reinterpret_cast<unsigned long long*>(B.ctl + 2), gridDim.x, a.wait_cycles, a.err)) break;
     }
-    if (j < W.npairs) {
-        // a wait expired at pair j: pairs j .. j+RING-1 may still be in flight; let each
-        // land (bounded) before the warp leaves
-        for (int i = j; i < min(j + RING, W.npairs); ++i)
-            mbar_wait(&W.bar[i % RING], (unsigned)(i / RING) & 1u, a.wait_cycles);
-        W.bad |= 2;
-    }
-    if (W.bad) atomicOr(a.err, (W.bad & 2) ? (ERRF_TIMEOUT | ERRF_NONFINITE) : ERRF_NONFINITE);
+    W.report();
 }
 
 // x-sweep alone: one warp per (row, strip of 56 columns).
@@ -365,15 +476,15 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     int bad = 0;
     const size_t o = boff + (size_t)r * a.pitch + cA;
     float2 em = make_float2(0.f, 0.f), sm = em;
-    const bool withmax = a.emax != nullptr;
-    if (withmax && va) {
+    const StepOut O = step_out(nullptr, a);
+    if (O.emax && va) {
         em.x = a.emax[o]; sm.x = a.smax[o];
         if (vb) { em.y = a.emax[o + 1]; sm.y = a.smax[o + 1]; }
     }
-    emit_pair(a, o, va, vb, E, U, V, D, withmax, em, sm, bad);
+    emit_pair(a, O, o, va, vb, E, U, V, D, em, sm, bad);
     Samples smp;
-    smp.init(a, gw, lane);
-    smp.emit(a, b, r, c0, lane, E, U, V);
+    smp.init(a, O, gw, lane);
+    smp.emit(a, O, b, r, c0, lane, E, U, V);
     if (bad) atomicOr(a.err, ERRF_NONFINITE);
 }
 
@@ -387,6 +498,7 @@ struct YOnly {
     bool vA, vB, withmax;
     YMarch2 ym;
     Samples smp;
+    StepOut O;
     int bad;
     __device__ __forceinline__ YOnly(const StepArgs& a_) : a(a_) {}
     template <int PH>
@@ -401,12 +513,12 @@ struct YOnly {
                 if (r >= r0 && r < r1) {
                     const size_t o = boff + (size_t)r * a.pitch + cA;
                     float2 em = make_float2(0.f, 0.f), sm = em;
-                    if (withmax && vA) {
+                    if (O.emax && vA) {
                         em.x = a.emax[o]; sm.x = a.smax[o];
                         if (vB) { em.y = a.emax[o + 1]; sm.y = a.smax[o + 1]; }
                     }
-                    emit_pair(a, o, vA, vB, oe, ot, ow, od, withmax, em, sm, bad);
-                    smp.emit(a, b, r, c0, lane, oe, ot, ow);
+                    emit_pair(a, O, o, vA, vB, oe, ot, ow, od, em, sm, bad);
+                    smp.emit(a, O, b, r, c0, lane, oe, ot, ow);
                 }
             });
     }
@@ -433,7 +545,8 @@ __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
     Y.vB = Y.cA + 1 < a.nx;
     Y.withmax = a.emax != nullptr;
     Y.bad = 0;
-    Y.smp.init(a, gw, lane);
+    Y.O = step_out(nullptr, a);
+    Y.smp.init(a, Y.O, gw, lane);
     Y.ym.init();
     int k = Y.r0 - 3;
     for (; k + 1 < Y.r1 + 3; k += 2) {
@@ -452,6 +565,10 @@ static cudaError_t fused_smem_optin() {
         done = cudaFuncSetAttribute(k_step_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
         if (done == cudaSuccess)
             done = cudaFuncSetAttribute(k_step_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
     }
     return done;
 }
@@ -464,6 +581,31 @@ cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, c
     if (a.sph) k_step_fused<true><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
     else k_step_fused<false><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s) {
+    const cudaError_t e = fused_smem_optin();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(FUSED_WARPS * 32);
+    cfg.dynamicSmemBytes = FUSED_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;         // all blocks resident: the grid barrier
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (a.sph) return cudaLaunchKernelEx(&cfg, k_batch<true>, mm, a, b);
+    return cudaLaunchKernelEx(&cfg, k_batch<false>, mm, a, b);
+}
+
+int batch_blocks_per_sm(bool sph) {
+    if (fused_smem_optin() != cudaSuccess) return 1;
+    int nb = 0;
+    if (sph) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true>, FUSED_WARPS * 32, FUSED_SMEM);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false>, FUSED_WARPS * 32, FUSED_SMEM);
+    return nb;
 }
 
 int fused_blocks_per_sm(bool sph) {

@@ -58,7 +58,32 @@ struct StepMaps {
     CUtensorMap e, u, v, d, em, sm;
 };
 
+struct StepMaps2 {
+    StepMaps m[2];                   // [k]: buffer k is the input
+};
+
+// The batched persistent run (k_batch). ctl lives in device memory so that one captured
+// graph serves every call: ctl[0] = steps done before the launch, ctl[1] = steps done after
+// it, ctl[2] = grid barrier (arrival count in the low 32 bits, generation in the high 32),
+// ctl[3] = work-item ticket counters for even (low 32 bits) and odd (high 32) steps.
+struct BatchArgs {
+    long long* ctl;
+    const int* order;                // scenarios by decreasing step limit
+    const int* nact;                 // [nact_len]: scenarios whose limit is >= the step; null: all
+    long long nact_len;
+    int nall;                        // the batch size
+    float* eta[2]; float* u[2]; float* v[2];
+    float* emax; float* smax;
+    int maxout, gout, bndout;
+    float* grec;                     // gauge records, row = step / gout (scenario stride in StepArgs)
+    long long grec_row;              // floats per record row
+    float* nrec;                     // enclosed-grid corner records, row = step / bndout
+    long long nrec_row;
+};
+
 // launchers (cliffs_step.cu)
+cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s);
+int batch_blocks_per_sm(bool sph);
 cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s);
 int fused_blocks_per_sm(bool sph);
 int fused_warps_per_block();
