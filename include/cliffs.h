@@ -140,6 +140,25 @@ int cliffs_step_n(cliffs_grid* g, int64_t n);
  * that cannot launch cooperatively). */
 int cliffs_run_persistent(cliffs_grid* g, int64_t n);
 
+/* Gradient of a gauge misfit with respect to the initial free surface (no counterpart in
+ * the paper, which has no adjoint). Let X_0 be the grid's current state and X_1..X_n the
+ * states of the next n steps; dL_dgauges[r][g] (row-major, r = 0 .. n/gout) is dL/d eta at
+ * gauge g after r*gout of those steps. Writes dL/d eta(X_0) to dL_deta0 ([ny][nx], host or
+ * device). The forward run is recomputed on the device: a state is kept every
+ * checkpoint_every steps, and each segment is run again with all its states stored before
+ * the adjoint steps go back through it. Each adjoint step is the transpose of the Jacobian
+ * of the y-sweep, then of the x-sweep (eqs. (eqQ), (solver2), (stateu), (stateh), (pq3)),
+ * with every branch of the inundation steps (a)-(e), the mirror walls and the friction
+ * clamp taken as in the forward run. The grid's state, records and maxima are unchanged.
+ * dL_dgauges may be NULL (the gradient is then zero). 2D grids with batch == 1 only.
+ * Memory: (checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per node,
+ * kept for later calls.
+ * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, batch > 1, n < 1,
+ * checkpoint_every < 1, NULL output); ERR_UNSTABLE, ERR_TIMEOUT from the forward
+ * recomputation; ERR_CUDA. */
+int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+                     float* dL_deta0);
+
 /* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
  * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
  * longer warps). Each candidate S is timed over `trials` launches (after one warm-up) that

@@ -26,7 +26,8 @@ __all__ = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
-    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "EXPORTED",
+    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
+    "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -38,7 +39,7 @@ EXPORTED = [
     "cliffs_set_durations", "cliffs_step_n", "cliffs_steps_done", "cliffs_read_gauges",
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
-    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent",
+    "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
 ]
 
 
@@ -84,6 +85,7 @@ def lib():
             "cliffs_set_durations": ([vp, vp], C.c_int),
             "cliffs_step_n": ([vp, C.c_int64], C.c_int),
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
+            "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_steps_done": ([vp, i64p], C.c_int),
             "cliffs_read_gauges": ([vp, C.c_int, vp, i64p], C.c_int),
             "cliffs_read_maxwave": ([vp, C.c_int, vp, vp], C.c_int),
@@ -188,6 +190,13 @@ def _out_ptr(out):
         assert out.flags.c_contiguous
         return C.c_void_p(out.ctypes.data)
     return C.c_void_p(out.data_ptr())
+
+
+def cliffs_adjoint_n(g, n, checkpoint_every, dL_dgauges, out):
+    """dL/d eta_0 into ``out`` ([ny][nx] float32, NumPy or torch, host or CUDA) for the
+    gauge-eta adjoint seed ``dL_dgauges`` ([n // gout + 1][G] float32, or None)."""
+    ps, ks = _ptr(dL_dgauges, np.float32)
+    _check(lib().cliffs_adjoint_n(g, int(n), int(checkpoint_every), ps, _out_ptr(out)))
 
 
 def cliffs_read_gauges(g, scenario, out=None) -> int:
@@ -355,3 +364,11 @@ class CliffsGrid:
 
     def autotune(self, trials=3):
         return cliffs_autotune(self.h, trials)
+
+    def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None):
+        """Gradient with respect to the current free surface of a loss whose derivative with
+        respect to the gauge eta records of the next n steps is ``dL_dgauges``."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        cliffs_adjoint_n(self.h, n, checkpoint_every, dL_dgauges, out)
+        return out

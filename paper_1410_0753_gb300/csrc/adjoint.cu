@@ -1,0 +1,522 @@
+// Reverse mode of the split step: the transpose of the Jacobian of one x-sweep followed by
+// one y-sweep (arXiv 1410.0753, section "Numerics", eqs. (eqQ), (solver2), (stateu),
+// (stateh), (pq3) and the inundation steps (a)-(e)), with every branch taken as the forward
+// pass took it: the wet/dry marks of (a), the flooding choice of (b), the mirror walls of
+// (c), the friction clamp and both tests of the cushion (e). Differentiating the step is
+// this library's addition; the paper has no adjoint.
+//
+// One adjoint step k, given the adjoint lambda_{k+1} of the state after step k:
+//   k_adj_xfwd    recompute the x-sweep of the stored state X_k (the same arithmetic as
+//                 the forward kernel, so the same bits) and write it transposed, so that
+//                 the y-sweep's lines (columns) lie along memory;
+//   k_adj_line<1> adjoint of the y-sweep, line by line over the transposed data, written
+//                 back untransposed;
+//   k_adj_line<0> adjoint of the x-sweep over rows, plus the gauge-misfit seed of step k,
+//                 written transposed for the next step's y-sweep adjoint.
+// A warp holds 64 nodes of a line (two per lane); each stage of the sweep needs its line
+// neighbours once, so after the six stages (b), (d), the tests of (e), and the adjoints of
+// (e), (d) and (b), the middle 52 nodes are exact. A block stages its 32 lines x 52 nodes
+// in shared memory and writes them transposed, so every load and store is coalesced.
+//
+// Derivatives are taken on the perturbation form used by the forward kernels (eta kept,
+// c_a - c_b = g (eta_a - eta_b + d_a - d_b)/(c_a + c_b)), which keeps the coefficients
+// free of the cancellation that p = w + 2c would suffer in FP32.
+#include "internal.h"
+#include "sweep.cuh"
+
+namespace cliffs {
+
+constexpr int AHALO = 6;                    // nodes of a window without their full dependency
+constexpr int AOUT = XWIN - 2 * AHALO;      // nodes a window finishes
+constexpr int ALINES = 32;                  // lines per block
+constexpr int AWARPS = 8;                   // warps per block (4 lines each)
+constexpr int TP = ALINES + 1;              // shared tile pitch (no bank conflicts)
+
+struct ANode { float e, w, t, d, c; };      // post-(b) state of a node or of a mirror ghost
+struct ABar { float e, w, t; };             // adjoints of (eta, w, t)
+struct AMet { float il, ir, k2, sdt; };     // 1/ds_left, 1/ds_right, dt^2/(ds_l+ds_r), dt tan/R
+
+// Interface between a left node b and a right node a (times the interval): the fluxes of
+// p, q (eq. (eqQ)) and t (eq. (pq3)) and the differences their derivatives need.
+struct AIface { float dw, dcs, sw, S, dtt, qp, qq, qt; };
+
+__device__ __forceinline__ AIface a_iface(const ANode& b, const ANode& a) {
+    AIface f;
+    const float de = a.e - b.e;
+    f.S = a.c + b.c;
+    f.dcs = GRAV * (de + (a.d - b.d)) / f.S;           // c_a - c_b
+    f.dw = a.w - b.w;
+    f.sw = a.w + b.w;
+    f.dtt = a.t - b.t;
+    const float y = f.sw * f.dcs, z = GRAV * de;
+    f.qp = 0.5f * f.dw * (f.sw + f.S) + z + y;
+    f.qq = 0.5f * f.dw * (f.sw - f.S) + z - y;
+    f.qt = 0.5f * f.sw * f.dtt;
+    return f;
+}
+
+// Friction of eq. (solver2)'s reading: adt = dt g n^2 w sqrt(w^2 + t^2) h^(-4/3), clamped to
+// w when larger in magnitude (mode 2), else mode 1; mode 0 without friction.
+struct AFric { float adt, s, hm; int mode; };
+
+__device__ __forceinline__ AFric a_friction(const ANode& C, const SweepConst& K) {
+    AFric F{0.f, 0.f, 0.f, 0};
+    if (K.dt_gn2 > 0.f) {
+        const float s2 = fmaf(C.w, C.w, C.t * C.t);
+        F.s = s2 * rsqrt_approx(fmaxf(s2, 1e-30f));
+        F.hm = pow_m43(C.e + C.d);
+        F.adt = K.dt_gn2 * C.w * F.s * F.hm;
+        F.mode = 1;
+        if (fabsf(F.adt) > fabsf(C.w)) { F.adt = C.w; F.mode = 2; }
+    }
+    return F;
+}
+
+// (d) at a wet node C with neighbours L and R (mirror ghosts already substituted): the
+// new eta and w, which the tests of (e) compare.
+template <bool SRC>
+__device__ __forceinline__ void a_dstage(const ANode& L, const ANode& C, const ANode& R, const AMet& m,
+                                         const SweepConst& K, float& e2, float& w2) {
+    const AIface fl = a_iface(L, C), fr = a_iface(C, R);
+    const float QpL = fl.qp * m.il, QpR = fr.qp * m.ir, QqL = fl.qq * m.il, QqR = fr.qq * m.ir;
+    const float hdt = K.half_dt;
+    float dp = -hdt * (QpL + QpR) + (C.w + C.c) * m.k2 * (QpR - QpL);
+    float dq = -hdt * (QqL + QqR) + (C.w - C.c) * m.k2 * (QqR - QqL);
+    const AFric F = a_friction(C, K);
+    dp -= F.adt;
+    dq -= F.adt;
+    if (SRC) {
+        const float s = m.sdt * C.c * C.w;
+        dp += s;
+        dq -= s;
+    }
+    const float dc = 0.25f * (dp - dq);
+    w2 = C.w + 0.5f * (dp + dq);
+    e2 = C.e + dc * (2.f * C.c + dc) * INV_GRAV;
+}
+
+// Adjoint of (d) at a wet node: given the adjoints (ge, gw, gt) of its new (eta, w, t), add
+// the adjoints of the post-(b) states of L, C and R (c folded into eta by dc/deta = g/2c).
+template <bool SRC>
+__device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, const ANode& R, const AMet& m,
+                                             const SweepConst& K, float ge, float gw, float gt,
+                                             ABar& bL, ABar& bC, ABar& bR) {
+    const AIface fl = a_iface(L, C), fr = a_iface(C, R);
+    const float QpL = fl.qp * m.il, QpR = fr.qp * m.ir, QqL = fl.qq * m.il, QqR = fr.qq * m.ir;
+    const float QtL = fl.qt * m.il, QtR = fr.qt * m.ir;
+    const float hdt = K.half_dt;
+    const float lp = C.w + C.c, lq = C.w - C.c;
+    float dp = -hdt * (QpL + QpR) + lp * m.k2 * (QpR - QpL);
+    float dq = -hdt * (QqL + QqR) + lq * m.k2 * (QqR - QqL);
+    const AFric F = a_friction(C, K);
+    dp -= F.adt;
+    dq -= F.adt;
+    if (SRC) {
+        const float s = m.sdt * C.c * C.w;
+        dp += s;
+        dq -= s;
+    }
+    const float dcn = 0.25f * (dp - dq);
+    // eta2 = eta + dcn (2c + dcn)/g, w2 = w + (dp + dq)/2, dcn = (dp - dq)/4
+    float eC = ge, wC = gw, tC = gt, cC = ge * 2.f * dcn * INV_GRAV, cL = 0.f, cR = 0.f;
+    const float gdcn = ge * 2.f * (C.c + dcn) * INV_GRAV;
+    const float gdp = 0.5f * gw + 0.25f * gdcn, gdq = 0.5f * gw - 0.25f * gdcn;
+    // t2 = t - dt/2 (QtL + QtR) + w k2 (QtR - QtL)   (eq. (pq3))
+    float gQtL = 0.f, gQtR = 0.f;
+    if (K.transverse) {
+        gQtL = gt * (-hdt - C.w * m.k2);
+        gQtR = gt * (-hdt + C.w * m.k2);
+        wC += gt * m.k2 * (QtR - QtL);
+    }
+    // dp = -dt/2 (QpL + QpR) + (w + c) k2 (QpR - QpL) - adt + sdt c w, dq alike with w - c
+    const float gQpL = gdp * (-hdt - lp * m.k2), gQpR = gdp * (-hdt + lp * m.k2);
+    const float gQqL = gdq * (-hdt - lq * m.k2), gQqR = gdq * (-hdt + lq * m.k2);
+    const float glp = gdp * m.k2 * (QpR - QpL), glq = gdq * m.k2 * (QqR - QqL);
+    wC += glp + glq;
+    cC += glp - glq;
+    const float gadt = -(gdp + gdq);
+    if (F.mode == 2) {
+        wC += gadt;
+    } else if (F.mode == 1 && F.s > 0.f) {
+        const float G = gadt * K.dt_gn2 * F.hm;
+        wC += G * (F.s + C.w * C.w / F.s);
+        tC += G * C.w * C.t / F.s;
+        eC += G * C.w * F.s * (-4.f / 3.f) / (C.e + C.d);
+    }
+    if (SRC) {
+        const float gs = (gdp - gdq) * m.sdt;
+        cC += gs * C.w;
+        wC += gs * C.c;
+    }
+    // Q(a, b) ds = 1/2 (lam_a + lam_b)(r_a - r_b) - g (d_a - d_b): partials with respect to
+    // w and c of both sides, for p (lam = w + c, r = w + 2c) and q (lam = w - c, r = w - 2c)
+    {   // left interface: b = L, a = C
+        const float A = gQpL * m.il, B = gQqL * m.il, T = gQtL * m.il;
+        const float hp = 0.5f * fl.dw + fl.dcs, hq = 0.5f * fl.dw - fl.dcs;
+        const float sp = fl.sw + fl.S, sq = fl.sw - fl.S;
+        wC += A * (hp + 0.5f * sp) + B * (hq + 0.5f * sq) + T * 0.5f * fl.dtt;
+        bL.w += A * (hp - 0.5f * sp) + B * (hq - 0.5f * sq) + T * 0.5f * fl.dtt;
+        cC += A * (hp + sp) - B * (hq + sq);
+        cL += A * (hp - sp) - B * (hq - sq);
+        tC += T * 0.5f * fl.sw;
+        bL.t -= T * 0.5f * fl.sw;
+    }
+    {   // right interface: b = C, a = R
+        const float A = gQpR * m.ir, B = gQqR * m.ir, T = gQtR * m.ir;
+        const float hp = 0.5f * fr.dw + fr.dcs, hq = 0.5f * fr.dw - fr.dcs;
+        const float sp = fr.sw + fr.S, sq = fr.sw - fr.S;
+        bR.w += A * (hp + 0.5f * sp) + B * (hq + 0.5f * sq) + T * 0.5f * fr.dtt;
+        wC += A * (hp - 0.5f * sp) + B * (hq - 0.5f * sq) + T * 0.5f * fr.dtt;
+        cR += A * (hp + sp) - B * (hq + sq);
+        cC += A * (hp - sp) - B * (hq - sq);
+        bR.t += T * 0.5f * fr.sw;
+        tC -= T * 0.5f * fr.sw;
+    }
+    bC.e += eC + cC * 0.5f * GRAV / C.c;
+    bC.w += wC;
+    bC.t += tC;
+    bL.e += cL * 0.5f * GRAV / L.c;
+    bR.e += cR * 0.5f * GRAV / R.c;
+}
+
+// neighbours across the window: node 0 of a lane is window node 2*lane, node 1 is 2*lane+1
+__device__ __forceinline__ void nbr(const float (&x)[2], float (&l)[2], float (&r)[2]) {
+    l[0] = __shfl_up_sync(FULL, x[1], 1);
+    l[1] = x[0];
+    r[0] = x[1];
+    r[1] = __shfl_down_sync(FULL, x[0], 1);
+}
+__device__ __forceinline__ void nbr(const int (&x)[2], int (&l)[2], int (&r)[2]) {
+    l[0] = __shfl_up_sync(FULL, x[1], 1);
+    l[1] = x[0];
+    r[0] = x[1];
+    r[1] = __shfl_down_sync(FULL, x[0], 1);
+}
+
+// Adjoint of one sweep of a 64-node line window. In: the sweep's input (e, w, t, d) and the
+// adjoint (ge, gw, gt) of its output. Out: the adjoint of its input, exact at window
+// nodes 6..57.
+template <bool SRC>
+__device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&w)[2], const float (&t)[2],
+                                             const float (&d)[2], const float (&ge)[2], const float (&gw)[2],
+                                             const float (&gt)[2], const AMet (&m)[2], const SweepConst& K,
+                                             float (&oe)[2], float (&ow)[2], float (&ot)[2]) {
+    // (a) wet marks at the start of the sweep
+    int o[2], fl[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        fl[i] = d[i] >= K.dwall;
+        o[i] = fl[i] && (e[i] + d[i] >= K.hmin);
+    }
+    // (b) flooding from the wetter neighbour (left on a tie), start-of-sweep values
+    float eL[2], eR[2], wL[2], wR[2], tL[2], tR[2];
+    int oL[2], oR[2];
+    nbr(e, eL, eR); nbr(w, wL, wR); nbr(t, tL, tR); nbr(o, oL, oR);
+    float e1[2], w1[2], t1[2];
+    int dir[2], wt[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        e1[i] = e[i]; w1[i] = w[i]; t1[i] = t[i]; dir[i] = 0; wt[i] = o[i];
+        if (!o[i]) {
+            w1[i] = 0.f;
+            t1[i] = 0.f;
+            if (fl[i]) {
+                const bool okL = oL[i] && (eL[i] + d[i] > K.hmin);
+                const bool okR = oR[i] && (eR[i] + d[i] > K.hmin);
+                if (okL || okR) {
+                    const bool useR = okR && (!okL || eR[i] > eL[i]);
+                    e1[i] = K.hmin - d[i];
+                    w1[i] = useR ? wR[i] : wL[i];
+                    t1[i] = useR ? tR[i] : tL[i];
+                    dir[i] = useR ? 1 : -1;
+                    wt[i] = 1;
+                }
+            }
+        }
+    }
+    // (c)+(d): the stencil of each wet node, mirror ghosts for dry neighbours
+    float c1[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) c1[i] = wt[i] ? wave_speed(e1[i] + d[i]) : 1.f;
+    float e1L[2], e1R[2], w1L[2], w1R[2], t1L[2], t1R[2], dL[2], dR[2], cL[2], cR[2];
+    int wtL[2], wtR[2];
+    nbr(e1, e1L, e1R); nbr(w1, w1L, w1R); nbr(t1, t1L, t1R); nbr(d, dL, dR); nbr(c1, cL, cR);
+    nbr(wt, wtL, wtR);
+    ANode Cn[2], Ln[2], Rn[2];
+    float h2[2], w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        Cn[i] = ANode{e1[i], w1[i], t1[i], d[i], c1[i]};
+        const ANode G{e1[i], -w1[i], t1[i], d[i], c1[i]};
+        Ln[i] = wtL[i] ? ANode{e1L[i], w1L[i], t1L[i], dL[i], cL[i]} : G;
+        Rn[i] = wtR[i] ? ANode{e1R[i], w1R[i], t1R[i], dR[i], cR[i]} : G;
+        if (wt[i]) {
+            float ee, ww;
+            a_dstage<SRC>(Ln[i], Cn[i], Rn[i], m[i], K, ee, ww);
+            h2[i] = ee + d[i];
+            w2[i] = ww;
+        } else {
+            h2[i] = e1[i] + d[i];
+            w2[i] = w1[i];
+        }
+    }
+    // (e) tests of each newly wetted node against its source after (d)
+    float h2L[2], h2R[2], w2L[2], w2R[2];
+    nbr(h2, h2L, h2R); nbr(w2, w2L, w2R);
+    int ce[2], cw[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        ce[i] = cw[i] = 0;
+        if (dir[i]) {
+            const float hs = dir[i] < 0 ? h2L[i] : h2R[i];
+            const float ws = dir[i] < 0 ? w2L[i] : w2R[i];
+            ce[i] = h2[i] > 0.5f * hs;
+            cw[i] = fabsf(w2[i]) > fabsf(ws);
+        }
+    }
+    // adjoint of (e): a limited value came from the source's
+    float geL[2], geR[2], gwL[2], gwR[2];
+    int dirL[2], dirR[2], ceL[2], ceR[2], cwL[2], cwR[2];
+    nbr(ge, geL, geR); nbr(gw, gwL, gwR);
+    nbr(dir, dirL, dirR); nbr(ce, ceL, ceR); nbr(cw, cwL, cwR);
+    ABar bL[2], bC[2], bR[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float De = (ce[i] ? 0.f : ge[i]) + ((dirL[i] == 1 && ceL[i]) ? 0.5f * geL[i] : 0.f) +
+                         ((dirR[i] == -1 && ceR[i]) ? 0.5f * geR[i] : 0.f);
+        const float Dw = (cw[i] ? 0.f : gw[i]) + ((dirL[i] == 1 && cwL[i]) ? gwL[i] : 0.f) +
+                         ((dirR[i] == -1 && cwR[i]) ? gwR[i] : 0.f);
+        // adjoint of (c)+(d); a dry node passes its values through
+        bL[i] = bR[i] = ABar{0.f, 0.f, 0.f};
+        if (wt[i]) {
+            bC[i] = ABar{0.f, 0.f, 0.f};
+            a_dstage_adj<SRC>(Ln[i], Cn[i], Rn[i], m[i], K, De, Dw, gt[i], bL[i], bC[i], bR[i]);
+            if (!wtL[i]) {                       // the ghost mirrors C: (eta, -w, t)
+                bC[i].e += bL[i].e; bC[i].w -= bL[i].w; bC[i].t += bL[i].t;
+                bL[i] = ABar{0.f, 0.f, 0.f};
+            }
+            if (!wtR[i]) {
+                bC[i].e += bR[i].e; bC[i].w -= bR[i].w; bC[i].t += bR[i].t;
+                bR[i] = ABar{0.f, 0.f, 0.f};
+            }
+        } else {
+            bC[i] = ABar{De, Dw, gt[i]};
+        }
+    }
+    // every node gathers its own part and its neighbours' parts
+    float Be[2], Bw[2], Bt[2];
+    Be[0] = bC[0].e + bL[1].e + __shfl_up_sync(FULL, bR[1].e, 1);
+    Bw[0] = bC[0].w + bL[1].w + __shfl_up_sync(FULL, bR[1].w, 1);
+    Bt[0] = bC[0].t + bL[1].t + __shfl_up_sync(FULL, bR[1].t, 1);
+    Be[1] = bC[1].e + bR[0].e + __shfl_down_sync(FULL, bL[0].e, 1);
+    Bw[1] = bC[1].w + bR[0].w + __shfl_down_sync(FULL, bL[0].w, 1);
+    Bt[1] = bC[1].t + bR[0].t + __shfl_down_sync(FULL, bL[0].t, 1);
+    // adjoint of (b) and (a): a flooded node took its source's velocities; its height
+    // h_min is a constant; a dry node keeps its eta and has no velocity
+    float BwL[2], BwR[2], BtL[2], BtR[2];
+    nbr(Bw, BwL, BwR); nbr(Bt, BtL, BtR);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (o[i]) {
+            oe[i] = Be[i];
+            ow[i] = Bw[i] + (dirL[i] == 1 ? BwL[i] : 0.f) + (dirR[i] == -1 ? BwR[i] : 0.f);
+            ot[i] = Bt[i] + (dirL[i] == 1 ? BtL[i] : 0.f) + (dirR[i] == -1 ? BtR[i] : 0.f);
+        } else {
+            oe[i] = dir[i] == 0 ? Be[i] : 0.f;
+            ow[i] = 0.f;
+            ot[i] = 0.f;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ void load2(const float* p, long long o, int pos, int n, float& a, float& b, float fill) {
+    a = b = fill;
+    if (pos >= 0 && pos + 1 < n) {
+        const float2 v = *reinterpret_cast<const float2*>(p + o + pos);
+        a = v.x; b = v.y;
+    } else {
+        if (pos >= 0 && pos < n) a = p[o + pos];
+        if (pos + 1 >= 0 && pos + 1 < n) b = p[o + pos + 1];
+    }
+}
+
+// Adjoint of the sweeps along one direction. DIR 0: lines are rows of row-major data and
+// the output is written transposed; DIR 1: lines are rows of transposed data (columns of
+// the grid) and the output is written row-major.
+template <int DIR, bool SPH>
+__global__ void __launch_bounds__(AWARPS * 32) k_adj_line(const AdjLineArgs A) {
+    __shared__ float tile[3][AOUT][TP];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int strip = blockIdx.x, l0 = blockIdx.y * ALINES;
+    const int p0 = strip * AOUT - AHALO;
+    const int pA = p0 + 2 * lane;
+    const SweepConst K{A.hmin, A.dwall, A.half_dt, A.dt_gn2, A.transverse};
+    AMet mb[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int p = pA + i;
+        mb[i] = AMet{0.f, 0.f, 0.f, 0.f};
+        if (DIR == 0) {
+            if (p >= 0 && p < A.npos) mb[i] = AMet{A.xa[p], A.xb[p], A.xk[p], 0.f};
+        } else {
+            const float4 q = A.ymet[min(max(p, -MET_PAD), A.npos - 1 + MET_PAD)];
+            mb[i] = AMet{q.x, q.y, q.z, q.w};
+        }
+    }
+    for (int j = 0; j < ALINES / AWARPS; ++j) {
+        const int ln = wi * (ALINES / AWARPS) + j;
+        const int line = l0 + ln;
+        if (line >= A.nlines) break;                 // warp-uniform
+        const long long o = (long long)line * A.ipitch;
+        float e[2], w[2], t[2], d[2], ge[2], gw[2], gt[2];
+        load2(A.pe, o, pA, A.npos, e[0], e[1], 0.f);
+        load2(A.pw, o, pA, A.npos, w[0], w[1], 0.f);
+        load2(A.pt, o, pA, A.npos, t[0], t[1], 0.f);
+        load2(A.pd, o, pA, A.npos, d[0], d[1], OUTSIDE_D);
+        load2(A.ge, o, pA, A.npos, ge[0], ge[1], 0.f);
+        load2(A.gw, o, pA, A.npos, gw[0], gw[1], 0.f);
+        load2(A.gt, o, pA, A.npos, gt[0], gt[1], 0.f);
+        AMet m[2] = {mb[0], mb[1]};
+        if (DIR == 0 && SPH) {
+            const float f = A.xrow[line];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) { m[i].il *= f; m[i].ir *= f; m[i].k2 *= f; }
+        }
+        float oe[2], ow[2], ot[2];
+        line_adjoint<DIR == 1 && SPH>(e, w, t, d, ge, gw, gt, m, K, oe, ow, ot);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = 2 * lane + i - AHALO;
+            if (q >= 0 && q < AOUT) {
+                tile[0][q][ln] = oe[i];
+                tile[1][q][ln] = ow[i];
+                tile[2][q][ln] = ot[i];
+            }
+        }
+    }
+    __syncthreads();
+    if (DIR == 0 && A.seed) {
+        // gauge-misfit seed of this step: dL/d eta at each gauge node
+        for (int k = threadIdx.x; k < A.G; k += blockDim.x) {
+            const int q = A.gxy[2 * k] - strip * AOUT, ln = A.gxy[2 * k + 1] - l0;
+            if (q >= 0 && q < AOUT && ln >= 0 && ln < ALINES) atomicAdd(&tile[0][q][ln], A.seed[k]);
+        }
+        __syncthreads();
+    }
+    float* out[3] = {A.oe, A.ow, A.ot};
+    for (int idx = threadIdx.x; idx < 3 * AOUT * ALINES; idx += blockDim.x) {
+        const int f = idx / (AOUT * ALINES), q = (idx / ALINES) % AOUT, ln = idx % ALINES;
+        const int p = strip * AOUT + q, line = l0 + ln;
+        if (p < A.npos && line < A.nlines) out[f][(long long)p * A.opitch + line] = tile[f][q][ln];
+    }
+}
+
+// The forward x-sweep of a stored state, written transposed ([nx][tpitch]): the same
+// window loads, edge treatment and sweep as the fused step kernel.
+template <bool SPH>
+__global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, const float* __restrict__ pe,
+                                                          const float* __restrict__ pu,
+                                                          const float* __restrict__ pv, float* te, float* tu,
+                                                          float* tv, int tpitch) {
+    __shared__ float tile[3][XOUT][TP];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int strip = blockIdx.x, r0 = blockIdx.y * ALINES;
+    const int c0 = strip * XOUT - 4, cA = c0 + 2 * lane;
+    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    const bool colA = cA >= 0 && cA < a.nx, colB = cA + 1 >= 0 && cA + 1 < a.nx;
+    float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
+    if (colA) { il.x = a.xa[cA]; ir.x = a.xb[cA]; k2.x = a.xk[cA]; }
+    if (colB) { il.y = a.xa[cA + 1]; ir.y = a.xb[cA + 1]; k2.y = a.xk[cA + 1]; }
+    for (int j = 0; j < ALINES / AWARPS; ++j) {
+        const int ln = wi * (ALINES / AWARPS) + j;
+        const int r = r0 + ln;
+        if (r >= a.ny) break;                       // warp-uniform
+        const long long o = (long long)r * a.pitch;
+        float2 E, U, V, D;
+        load2(pe, o, cA, a.nx, E.x, E.y, 0.f);
+        load2(pu, o, cA, a.nx, U.x, U.y, 0.f);
+        load2(pv, o, cA, a.nx, V.x, V.y, 0.f);
+        load2(a.d, o, cA, a.nx, D.x, D.y, OUTSIDE_D);
+        XMet2 m{il, ir, k2};
+        if (SPH) {
+            const float2 f = v2(a.xrow[r]);
+            m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
+        }
+        xsweep2(E, U, V, D, m, K, lane);
+        const float vals[3][2] = {{E.x, E.y}, {U.x, U.y}, {V.x, V.y}};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = 2 * lane + i - 4;
+            if (q >= 0 && q < XOUT) {
+                tile[0][q][ln] = vals[0][i];
+                tile[1][q][ln] = vals[1][i];
+                tile[2][q][ln] = vals[2][i];
+            }
+        }
+    }
+    __syncthreads();
+    float* out[3] = {te, tu, tv};
+    for (int idx = threadIdx.x; idx < 3 * XOUT * ALINES; idx += blockDim.x) {
+        const int f = idx / (XOUT * ALINES), q = (idx / ALINES) % XOUT, ln = idx % ALINES;
+        const int c = strip * XOUT + q, r = r0 + ln;
+        if (c < a.nx && r < a.ny) out[f][(long long)c * tpitch + r] = tile[f][q][ln];
+    }
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols (32 x 32 tiles through shared memory)
+__global__ void __launch_bounds__(256) k_transpose(const float* __restrict__ in, int ipitch, float* out,
+                                                   int opitch, int rows, int cols) {
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.x; k < 1024; k += 256) {
+        const int r = r0 + k / 32, c = c0 + k % 32;
+        if (r < rows && c < cols) t[k / 32][k % 32] = in[(long long)r * ipitch + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 1024; k += 256) {
+        const int c = c0 + k / 32, r = r0 + k % 32;
+        if (r < rows && c < cols) out[(long long)c * opitch + r] = t[k % 32][k / 32];
+    }
+}
+
+// lambda.eta[gauge] += seed[gauge] on transposed data
+__global__ void k_adj_seed(float* te, int tpitch, const int* gxy, int G, const float* seed) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < G) atomicAdd(te + (long long)gxy[2 * k] * tpitch + gxy[2 * k + 1], seed[k]);
+}
+
+cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s) {
+    const dim3 grid((A.npos + AOUT - 1) / AOUT, (A.nlines + ALINES - 1) / ALINES);
+    if (dir == 0) {
+        if (sph) k_adj_line<0, true><<<grid, AWARPS * 32, 0, s>>>(A);
+        else k_adj_line<0, false><<<grid, AWARPS * 32, 0, s>>>(A);
+    } else {
+        if (sph) k_adj_line<1, true><<<grid, AWARPS * 32, 0, s>>>(A);
+        else k_adj_line<1, false><<<grid, AWARPS * 32, 0, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
+                            float* tu, float* tv, int tpitch, cudaStream_t s) {
+    const dim3 grid((a.nx + XOUT - 1) / XOUT, (a.ny + ALINES - 1) / ALINES);
+    if (a.sph) k_adj_xfwd<true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+    else k_adj_xfwd<false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,
+                             cudaStream_t s) {
+    const dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    k_transpose<<<grid, 256, 0, s>>>(in, ipitch, out, opitch, rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seed(float* te, int tpitch, const int* gxy, int G, const float* seed, cudaStream_t s) {
+    if (G <= 0) return cudaSuccess;
+    k_adj_seed<<<(G + 127) / 128, 128, 0, s>>>(te, tpitch, gxy, G, seed);
+    return cudaGetLastError();
+}
+
+}  // namespace cliffs

@@ -269,6 +269,19 @@ struct cliffs_grid {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int pblocks = 0;
+    // adjoint work space: K recomputed states and the checkpoints (row-major, 3 planes
+    // each), the transposed x-swept state, adjoint and depth (7 planes of [nx][tpitch]),
+    // the row-major intermediate adjoint (3 planes), gauge nodes and seeds
+    int adj_K = 0;
+    long long adj_ncap = 0;
+    float* adj_slots = nullptr;
+    float* adj_ckpt = nullptr;
+    float* adj_t = nullptr;
+    float* adj_lb = nullptr;
+    std::vector<StepMaps> adj_maps;
+    int* adj_gxy = nullptr;
+    float* adj_seed = nullptr;
+    long long adj_seed_cap = 0;
 };
 
 namespace {
@@ -535,6 +548,8 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->order_d); cudaFree(g->nact_d); cudaFree(g->ctl_d);
     if (g->ctl_h) cudaFreeHost(g->ctl_h);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
+    cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
     if (g->cap) cudaStreamDestroy(g->cap);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete g;
@@ -1076,6 +1091,156 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
         CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
         if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
         return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state before step %lld", (long long)g->step);
+    }
+    return CLIFFS_OK;
+}
+
+int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+                     float* dL_deta0) {
+    g_err[0] = 0;
+    if (!g || !dL_deta0) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
+    if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
+    if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
+    cudaStream_t s = g->stream;
+    const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);
+    const long long P = g->plane;                          // row-major plane, floats
+    const int tp = (ny + 31) / 32 * 32;                     // transposed pitch
+    const long long TPL = (long long)tp * nx;               // transposed plane, floats
+    const long long nseg = (n + K - 1) / K;
+    const long long nrec = n / g->cfg.gout + 1;
+    const int G = g->G;
+    // work space (kept for later calls)
+    if (g->adj_K < K || !g->adj_slots) {
+        cudaFree(g->adj_slots);
+        g->adj_slots = nullptr;
+        g->adj_maps.clear();
+        CK(cudaMalloc(&g->adj_slots, sizeof(float) * 3 * P * (size_t)std::max(K, 2)));
+        g->adj_K = std::max(K, 2);
+        g->adj_maps.resize(g->adj_K);
+        for (int j = 0; j < g->adj_K; ++j) {
+            StepMaps& M = g->adj_maps[j];
+            M = g->maps[0];
+            float* b = g->adj_slots + 3 * P * j;
+            int rc = make_map(&M.e, b, 3, g->pitch, ny, 1);
+            if (!rc) rc = make_map(&M.u, b + P, 3, g->pitch, ny, 1);
+            if (!rc) rc = make_map(&M.v, b + 2 * P, 3, g->pitch, ny, 1);
+            if (rc) return rc;
+        }
+    }
+    if (g->adj_ncap < nseg || !g->adj_ckpt) {
+        cudaFree(g->adj_ckpt);
+        g->adj_ckpt = nullptr;
+        CK(cudaMalloc(&g->adj_ckpt, sizeof(float) * 3 * P * nseg));
+        g->adj_ncap = nseg;
+    }
+    if (!g->adj_t) {
+        CK(cudaMalloc(&g->adj_t, sizeof(float) * 7 * TPL));
+        CK(cudaMalloc(&g->adj_lb, sizeof(float) * 3 * P));
+        CK(cudaMemsetAsync(g->adj_t, 0, sizeof(float) * 7 * TPL, s));
+        CK(cudaMemsetAsync(g->adj_lb, 0, sizeof(float) * 3 * P, s));
+        if (G > 0) {
+            CK(cudaMalloc(&g->adj_gxy, sizeof(int) * 2 * G));
+            CK(cudaMemcpyAsync(g->adj_gxy, g->gauges.data(), sizeof(int) * 2 * G, cudaMemcpyHostToDevice, s));
+        }
+    }
+    if (G > 0 && dL_dgauges && g->adj_seed_cap < nrec) {
+        cudaFree(g->adj_seed);
+        g->adj_seed = nullptr;
+        CK(cudaMalloc(&g->adj_seed, sizeof(float) * G * nrec));
+        g->adj_seed_cap = nrec;
+    }
+    const bool seeded = G > 0 && dL_dgauges;
+    if (seeded)
+        CK(cudaMemcpyAsync(g->adj_seed, dL_dgauges, sizeof(float) * G * nrec, cudaMemcpyDefault, s));
+    float* XT = g->adj_t;                                   // eta', u', v' transposed
+    float* LT = g->adj_t + 3 * TPL;                         // adjoint (eta, u, v) transposed
+    float* DT = g->adj_t + 6 * TPL;                         // depth transposed
+    float* LB = g->adj_lb;                                  // adjoint (eta, u, v) row-major
+    auto slot = [&](int j) { return g->adj_slots + 3 * P * j; };
+    StepArgs a;
+    fill_step_args(g, a, 0, 1);
+    a.limit = nullptr;
+    a.step = 1;
+    auto fwd = [&](int from, int to) -> int {
+        a.eta_in = slot(from); a.u_in = slot(from) + P; a.v_in = slot(from) + 2 * P;
+        a.eta_out = slot(to); a.u_out = slot(to) + P; a.v_out = slot(to) + 2 * P;
+        const cudaError_t le = launch_step_fused(a, g->adj_maps[from], 1, s);
+        if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
+        return CLIFFS_OK;
+    };
+    // X_0: the grid's current state
+    const int cb = (int)cur_buf(g, 0);
+    CK(cudaMemcpyAsync(slot(0), g->eta[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(slot(0) + P, g->u[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+    // checkpoint pass: X_{sK} for every segment s
+    for (long long j = 0; j <= (nseg - 1) * K; ++j) {
+        const int cur = (int)(j & 1);
+        if (j % K == 0)
+            CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K), slot(cur), sizeof(float) * 3 * P,
+                               cudaMemcpyDeviceToDevice, s));
+        if (j < (nseg - 1) * K) {
+            int rc = fwd(cur, 1 - cur);
+            if (rc) return rc;
+        }
+    }
+    cudaError_t le = launch_transpose(g->d32, g->pitch, DT, tp, ny, nx, s);
+    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "transpose: %s", cudaGetErrorString(le));
+    // lambda_n: the seed of the last record
+    CK(cudaMemsetAsync(LT, 0, sizeof(float) * 3 * TPL, s));
+    if (seeded && n % g->cfg.gout == 0) {
+        le = launch_adj_seed(LT, tp, g->adj_gxy, G, g->adj_seed + (n / g->cfg.gout) * G, s);
+        if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "seed: %s", cudaGetErrorString(le));
+    }
+    AdjLineArgs Y{};                                        // y-sweep adjoint: lines are columns
+    Y.pe = XT; Y.pw = XT + 2 * TPL; Y.pt = XT + TPL; Y.pd = DT;
+    Y.ge = LT; Y.gw = LT + 2 * TPL; Y.gt = LT + TPL;
+    Y.oe = LB; Y.ow = LB + 2 * P; Y.ot = LB + P;
+    Y.nlines = nx; Y.npos = ny; Y.ipitch = tp; Y.opitch = g->pitch;
+    Y.ymet = a.ymet;
+    AdjLineArgs X{};                                        // x-sweep adjoint: lines are rows
+    X.pd = g->d32;
+    X.ge = LB; X.gw = LB + P; X.gt = LB + 2 * P;
+    X.oe = LT; X.ow = LT + TPL; X.ot = LT + 2 * TPL;
+    X.nlines = ny; X.npos = nx; X.ipitch = g->pitch; X.opitch = tp;
+    X.xa = a.xa; X.xb = a.xb; X.xk = a.xk; X.xrow = a.xrow;
+    X.gxy = g->adj_gxy; X.G = G;
+    for (AdjLineArgs* A : {&X, &Y}) {
+        A->hmin = a.hmin; A->dwall = a.dwall; A->half_dt = a.half_dt; A->dt_gn2 = a.dt_gn2;
+        A->transverse = a.transverse;
+    }
+    for (long long sg = nseg - 1; sg >= 0; --sg) {
+        const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
+        CK(cudaMemcpyAsync(slot(0), g->adj_ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+        for (long long j = j0; j + 1 < j1; ++j) {
+            int rc = fwd((int)(j - j0), (int)(j - j0 + 1));
+            if (rc) return rc;
+        }
+        for (long long j = j1 - 1; j >= j0; --j) {
+            const float* st = slot((int)(j - j0));
+            le = launch_adj_xfwd(a, st, st + P, st + 2 * P, XT, XT + TPL, XT + 2 * TPL, tp, s);
+            if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
+            X.pe = st; X.pw = st + P; X.pt = st + 2 * P;
+            X.seed = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * G : nullptr;
+            if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
+            if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+        }
+    }
+    // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]
+    int rc = ensure_tmp(g, sizeof(float) * (size_t)nx * ny);
+    if (rc) return rc;
+    le = launch_transpose(LT, tp, (float*)g->tmp, nx, nx, ny, s);
+    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "transpose: %s", cudaGetErrorString(le));
+    CK(cudaMemcpyAsync(dL_deta0, g->tmp, sizeof(float) * (size_t)nx * ny, cudaMemcpyDefault, s));
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, g->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h[0]) {
+        CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
+        if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
+        return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state in the forward recomputation");
     }
     return CLIFFS_OK;
 }

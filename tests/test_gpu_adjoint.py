@@ -1,0 +1,145 @@
+"""The hand-written adjoint (cliffs_adjoint_n) on the GPU.
+
+Pinned three ways: (1) the dot-product identity against the FP64 oracle's tangent-linear
+model, <dL/d eta0, delta> = sum_r,g seed[r,g] * (TLM delta)[r,g], with branches frozen on the
+primal on both sides; (2) central finite differences of the GPU forward on unit-source
+coefficients through torch.autograd; (3) checkpoint spacing changes nothing (bit for bit).
+
+Tolerances. The adjoint runs in FP32 against an FP64 tangent model over runs of 60-160
+steps; each step's Jacobian coefficients carry FP32 relative errors of a few 1e-7, and the
+coefficients are formed in the perturbation form, so no p = w + 2c cancellation enters.
+Measured: at most 8e-6 of the largest term of the dot product (shoreline and spherical runs
+included). The bound is 1e-4, which a dropped term, a wrong sign or a transposed stencil
+exceeds by orders of magnitude. Central differences of the FP32 forward with h = 1e-3 carry
+~1e-5 relative rounding noise and O(h^2) truncation; measured 4e-5, bound 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+DOT_RTOL = 1e-4
+FD_RTOL = 1e-3
+
+
+def _start(w, **kw):
+    g = CliffsGrid.from_workload(w, **kw)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    return g
+
+
+def _cases():
+    return {
+        "inversion_slope": lambda: workloads.inversion_1024(nx=128, ny=112, steps=160),
+        "beach_runup": lambda: workloads.beach_200(120, 90, steps=120),
+        "spherical_coast": lambda: workloads.spherical_coast(160, 150, steps=60),
+    }
+
+
+@pytest.mark.parametrize("case", sorted(_cases()))
+def test_adjoint_dot_product_against_oracle_tlm(case):
+    w = _cases()[case]()
+    n = w.steps
+    g = _start(w)
+    nrec = n // w.gout + 1
+    G = len(w.gauges)
+    rng = np.random.default_rng(17)
+    seed = rng.standard_normal((nrec, G)).astype(np.float32)
+    grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
+    assert np.isfinite(grad).all()
+    d64 = P.f32(P.oracle_depth(w))
+    p = oracle.params_from(w)
+    yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
+    worst = 0.0
+    for k in range(3):
+        cx, cy = rng.uniform(0.3, 0.7) * w.nx, rng.uniform(0.3, 0.7) * w.ny
+        sig = rng.uniform(0.05, 0.12) * min(w.nx, w.ny)
+        delta = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig ** 2))
+        if k == 2:
+            delta = delta + 0.1 * rng.standard_normal(delta.shape)
+        _, gtan, _, _ = oracle.run_tlm(p, w.x, w.y, d64, w.eta0, delta, nsteps=n, gout=w.gout,
+                                       gauges=w.gauges)
+        terms = seed.astype(np.float64) * gtan
+        want = terms.sum()
+        got = float((grad * delta).sum())
+        scale = max(np.abs(terms).max(), 1e-12)
+        err = abs(got - want) / scale
+        worst = max(worst, err)
+        assert err <= DOT_RTOL, (case, k, got, want, scale)
+    P.report("adjoint_dot_" + case, rel_err=worst)
+    g.close()
+
+
+def test_adjoint_gradient_matches_finite_differences_through_autograd():
+    import torch
+    from paper_1410_0753_gb300.autograd import gauge_run
+    w = workloads.inversion_1024(nx=128, ny=112, steps=120)
+    n = w.steps
+    basis = torch.tensor(w.extra["basis"], device="cuda")
+    truth = torch.tensor(w.extra["theta_true"], device="cuda")
+    g = _start(w)
+    with torch.no_grad():
+        obs = gauge_run(torch.einsum("k,kyx->yx", truth, basis), g, n)
+
+    def loss(theta):
+        eta0 = torch.einsum("k,kyx->yx", theta, basis)
+        return 0.5 * ((gauge_run(eta0, g, n, 25) - obs) ** 2).sum(dtype=torch.float64)
+
+    theta = torch.tensor(w.extra["theta0"], device="cuda", requires_grad=True)
+    L = loss(theta)
+    L.backward()
+    grad = theta.grad.detach().cpu().numpy().astype(np.float64)
+    assert np.isfinite(grad).all() and np.abs(grad).max() > 0
+    h = 1e-3
+    worst = 0.0
+    with torch.no_grad():
+        for k in np.argsort(-np.abs(grad))[:6]:
+            e = torch.zeros_like(theta)
+            e[k] = h
+            fd = (loss(theta + e).item() - loss(theta - e).item()) / (2 * h)
+            err = abs(fd - grad[k]) / np.abs(grad).max()
+            worst = max(worst, err)
+            assert err <= FD_RTOL, (k, fd, grad[k])
+    P.report("adjoint_fd_inversion", rel_err=worst)
+    g.close()
+
+
+def test_adjoint_checkpoint_spacing_and_state_untouched():
+    """Any checkpoint spacing gives the same gradient bit for bit (the forward is recomputed
+    by the same kernel), and the grid's own state is left as it was."""
+    w = workloads.beach_200(96, 80, steps=70)
+    g = _start(w)
+    g.step(5)
+    before = g.state()
+    n = 40
+    seed = np.random.default_rng(3).standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    ref = g.adjoint(n, seed, checkpoint_every=n)
+    for K in (1, 7, 16):
+        assert np.array_equal(g.adjoint(n, seed, checkpoint_every=K), ref)
+    for x, y in zip(before, g.state()):
+        assert np.array_equal(x, y)
+    assert np.count_nonzero(ref) > 0
+    assert not np.any(g.adjoint(n, None))
+    g.close()
+
+
+def test_adjoint_argument_errors():
+    w = workloads.ensemble_512(batch=2, nx=64, ny=48, dmin=5, dmax=9)
+    g = _start(w)
+    with pytest.raises(CliffsError) as e:
+        g.adjoint(4, None)
+    assert e.value.code == ERR_ARG
+    g.close()
+    w = workloads.beach_200(64, 48, steps=10)
+    g = _start(w)
+    for n, k in ((0, 5), (5, 0)):
+        with pytest.raises(CliffsError) as e:
+            g.adjoint(n, None, checkpoint_every=k)
+        assert e.value.code == ERR_ARG
+    g.close()
