@@ -14,6 +14,11 @@ is timed with CUDA events on the grid's stream; the K steps are bracketed by a b
 device synchronisation; the maximum over ranks is reported. With N > 1 each rank advances
 its own replica of the grid (the path does not shard: replicas only).
 
+With one GPU the line also carries ``forms``: the batched ensemble (256 scenarios of uneven
+duration on a shared 512 x 512 bathymetry in one persistent, graph-captured launch) and the
+adjoint (gradient of a 32-gauge misfit over 2000 steps of a 1024 x 1024 grid), each next to
+the plain single-scenario forward on the same GPU.
+
 ``--impl reference`` times the FP64 CPU oracle on the same workload on the host cores.
 """
 import argparse
@@ -179,6 +184,85 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _event_ms(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_forms(torch, stream):
+    """The batched ensemble (256 scenarios of uneven duration on one 512 x 512 bathymetry, one
+    persistent graph-captured launch) and the adjoint (1024 x 1024, 2000 steps, checkpoint
+    every 100), each reported against the plain single-scenario forward on this GPU."""
+    import workloads
+    from paper_1410_0753_gb300 import CliffsGrid
+    out = {}
+    s = stream.cuda_stream
+    # batched
+    w = workloads.ensemble_512()
+    g = CliffsGrid.from_workload(w, stream=s)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    eta0 = w.eta0.astype(np.float32)
+    g.set_initial(eta0)
+    g.set_durations(w.durations)
+    tune = g.autotune(2)
+    g.step(10, persistent=True)                     # capture the graph, warm up
+    g.set_initial(eta0)
+    T = int(w.durations.max())
+    ms_b = _event_ms(torch, stream, lambda: g.step(T, persistent=True))
+    useful = float(w.durations.sum()) * w.cells
+    g.close()
+    g1 = CliffsGrid.from_workload(w, batch=1, stream=s)
+    g1.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    g1.set_initial(eta0[0])
+    g1.step(20)
+    n1 = 1000
+    ms_1 = _event_ms(torch, stream, lambda: g1.step(n1))
+    g1.close()
+    v_b = useful / (ms_b / 1e3) / 1e9
+    v_1 = w.cells * n1 / (ms_1 / 1e3) / 1e9
+    out["batched"] = {
+        "workload": w.name, "scenarios": int(w.batch), "durations": [int(w.durations.min()), int(w.durations.max())],
+        "value": v_b, "unit": UNIT, "ms": ms_b, "launches": 1,
+        "rows_per_warp": min(tune, key=tune.get) if tune else None,
+        "single_scenario_forward": {"value": v_1, "unit": UNIT, "steps": n1,
+                                    "note": "one scenario, one launch per step, same grid"},
+        "vs_single_scenario_forward": v_b / v_1,
+        "note": "useful cell-updates (each scenario up to its own duration) / time of one "
+                "persistent, cooperative, graph-captured launch"}
+    # adjoint
+    w = workloads.inversion_1024()
+    g = CliffsGrid.from_workload(w, stream=s)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    e0 = w.eta0.astype(np.float32)
+    g.set_initial(e0)
+    g.autotune(2)
+    n = w.steps
+    seed = np.random.default_rng(1).standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    grad = torch.empty((w.ny, w.nx), dtype=torch.float32, device="cuda")
+    g.adjoint(50, seed[:51], 100, grad)             # allocate work space, warm up
+    g.set_initial(e0)
+    g.step(10)
+    g.set_initial(e0)
+    ms_f = _event_ms(torch, stream, lambda: g.step(n))
+    g.set_initial(e0)
+    ms_a = _event_ms(torch, stream, lambda: g.adjoint(n, seed, 100, grad))
+    g.close()
+    out["adjoint"] = {
+        "workload": w.name, "steps": n, "checkpoint_every": 100, "gauges": len(w.gauges),
+        "gradient_ms": ms_a, "forward_ms": ms_f, "gradient_over_forward": ms_a / ms_f,
+        "value": w.cells * n / (ms_a / 1e3) / 1e9, "unit": UNIT,
+        "forward_value": w.cells * n / (ms_f / 1e3) / 1e9,
+        "note": "gradient = checkpoint pass + segment recomputation + adjoint steps, one call "
+                "of cliffs_adjoint_n; forward = cliffs_step_n over the same steps"}
+    return out
+
+
 def run_cuda(args, world, rank, local):
     import torch
     import workloads
@@ -292,6 +376,10 @@ def run_cuda(args, world, rank, local):
                         "eta_scale": float(np.abs(e64).max())}
         gv.close()
 
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = measure_forms(torch, stream)
+
     if rank == 0:
         line = {
             "metric": baseline_metric(), "value": value, "unit": UNIT, "n_gpus": world,
@@ -310,6 +398,7 @@ def run_cuda(args, world, rank, local):
                          "peak_kind": peak_kind},
             "cpu_baseline": cpu,
             "oracle_error": oracle_error,
+            "forms": forms,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "wall_ms": 1e3 * wall,
@@ -332,6 +421,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
