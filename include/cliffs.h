@@ -161,9 +161,10 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
 
 /* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
  * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
- * longer warps). Each candidate S is timed over `trials` launches (after one warm-up) that
- * read the current state and write scratch planes, with max-wave and records off; the
- * fastest is kept for later steps. The grid's state, maxima and records are unchanged.
+ * longer warps, and the count of warps against the resident slots decides the tail). Each
+ * candidate S is timed over `trials` launches (after one warm-up) that read the current
+ * state and write scratch planes, with max-wave and records off, each after a 192 MiB write
+ * that evicts the inputs from L2; the fastest is kept for later steps. The grid's state, maxima and records are unchanged.
  * Optional outputs: cand[] and us[] (capacity 16) receive the candidates and their best
  * times in microseconds, *ncand their count (0 for 1D grids, which have no tile shape).
  * Errors: ERR_STATE before set_initial; ERR_NOMEM; ERR_CUDA; ERR_TIMEOUT. */

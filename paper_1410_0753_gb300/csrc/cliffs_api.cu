@@ -389,6 +389,31 @@ int set_rows_per_warp(cliffs_grid* g, int S, int S_hard) {
 
 int hard_rows(int S) { return std::max(8, (S * 3 / 4) & ~1); }
 
+// warps of one fused launch with S rows per warp, and the warps resident at once
+long long fused_warps(const cliffs_grid* g, int S) {
+    int nhard = 0;
+    for (int st = 0; st < g->nstrips; ++st) nhard += g->hard.empty() ? 0 : g->hard[st];
+    const int Sh = hard_rows(S);
+    return ((long long)(g->nstrips - nhard) * ((g->ny + S - 1) / S) +
+            (long long)nhard * ((g->ny + Sh - 1) / Sh)) * g->B;
+}
+
+long long resident_warps(const cliffs_grid* g) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return (long long)std::max(1, nsm) * std::max(1, fused_blocks_per_sm(g->cfg.coords != 1)) *
+           fused_warps_per_block();
+}
+
+// the smallest even S whose launch fits in `waves` waves of resident warps (0 if none does)
+int wave_rows(const cliffs_grid* g, int waves) {
+    const long long cap = resident_warps(g) * waves;
+    for (int S = 8; S <= std::max(8, g->ny); S += 2)
+        if (fused_warps(g, S) <= cap) return S;
+    return 0;
+}
+
 int choose_geometry(cliffs_grid* g) {
     if (g->ny == 1) {
         g->kind = 1;
@@ -404,24 +429,14 @@ int choose_geometry(cliffs_grid* g) {
         g->kind = 0;
         g->nstrips = (g->nx + XOUT - 1) / XOUT;
         // rows per warp S: each warp walks S + 6 rows (3-row halo above and below), so the
-        // cost of one wave of warps is ~ S + 6; pick S minimising waves * (S + 6) with the
-        // resident warps the occupancy calculator reports (ties go to the larger S)
-        int dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long resident = (long long)std::max(1, nsm) *
-                                   std::max(1, fused_blocks_per_sm(g->cfg.coords != 1)) *
-                                   fused_warps_per_block();
-        int nhard = 0;
-        for (int st = 0; st < g->nstrips; ++st) nhard += g->hard[st];
-        const int cand[] = {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+        // cost of one wave of warps is ~ S + 6; pick the even S minimising waves * (S + 6)
+        // with the resident warps the occupancy calculator reports (ties go to the larger S)
+        const long long resident = resident_warps(g);
         double best = 1e300;
         int bestS = 32;
-        for (int S : cand) {
-            if (S > 2 * g->ny && S != 16) break;
-            const int Sh = hard_rows(S);
-            const long long warps = ((long long)(g->nstrips - nhard) * ((g->ny + S - 1) / S) +
-                                     (long long)nhard * ((g->ny + Sh - 1) / Sh)) * g->B;
+        for (int S = 8; S <= 1024; S += (S < 128 ? 2 : 32)) {
+            if (S > 2 * g->ny && S != 8) break;
+            const long long warps = fused_warps(g, S);
             const double cost = (double)((warps + resident - 1) / resident) * (S + 6);
             if (cost <= best) { best = cost; bestS = S; }
         }
@@ -1256,10 +1271,13 @@ int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32
     if (trials < 1) trials = 3;
     cudaStream_t s = g->stream;
     // scratch output planes: the trial steps read the current state and write elsewhere,
-    // with max-wave and records off, so the grid's state and outputs are untouched
+    // with max-wave and records off, so the grid's state and outputs are untouched; before
+    // each trial a write larger than L2 evicts the inputs, as in a long run
     const size_t pb = sizeof(float) * (size_t)g->B * g->plane;
+    const size_t flush_bytes = (size_t)192 << 20;
     float* scratch = nullptr;
-    CK(cudaMalloc(&scratch, 3 * pb));
+    CK(cudaMalloc(&scratch, 3 * pb + flush_bytes));
+    unsigned char* flush = reinterpret_cast<unsigned char*>(scratch + 3 * (pb / sizeof(float)));
     const int cur = (int)(g->step & 1);
     StepArgs a;
     fill_step_args(g, a, cur, 1 - cur);
@@ -1267,7 +1285,16 @@ int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32
     a.u_out = scratch + (size_t)g->B * g->plane;
     a.v_out = scratch + 2 * (size_t)g->B * g->plane;
     a.step = g->step + 1;
-    const int list[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
+    // fixed shapes, and those that just fit one, two or three waves of resident warps
+    std::vector<int> list = {16, 24, 32, 48, 64, 96, 128};
+    for (int wv = 1; wv <= 3; ++wv) {
+        const int S1 = wave_rows(g, wv);
+        if (S1 > 0)
+            for (int d : {0, 2, 4}) list.push_back(S1 + d);
+    }
+    std::sort(list.begin(), list.end());
+    list.erase(std::unique(list.begin(), list.end()), list.end());
+    if (list.size() > 16) list.resize(16);
     const int oldS = g->S;
     int bestS = oldS, n = 0;
     double best = 1e300;
@@ -1283,6 +1310,7 @@ int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32
         a.items = g->items_dev; a.nitems = (int)g->items.size();
         float tbest = 1e30f;
         for (int t = 0; t <= trials; ++t) {             // the first launch warms up
+            cudaMemsetAsync(flush, t & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
             cudaError_t le = launch_step_fused(a, g->maps[cur], g->B, s);
             cudaEventRecord(e1, s);
