@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_line(const AdjLineArgs A) {
 
 // The forward x-sweep of a stored state, written transposed ([nx][tpitch]): the same
 // window loads, edge treatment and sweep as the fused step kernel.
-template <bool SPH>
+template <bool SPH, bool FRIC>
 __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, const float* __restrict__ pe,
                                                           const float* __restrict__ pu,
                                                           const float* __restrict__ pv, float* te, float* tu,
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
             const float2 f = v2(a.xrow[r]);
             m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
         }
-        xsweep2(E, U, V, D, m, K, lane);
+        xsweep2<FRIC>(E, U, V, D, m, K, lane);
         const float vals[3][2] = {{E.x, E.y}, {U.x, U.y}, {V.x, V.y}};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -501,8 +501,14 @@ cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_
 cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
                             float* tu, float* tv, int tpitch, cudaStream_t s) {
     const dim3 grid((a.nx + XOUT - 1) / XOUT, (a.ny + ALINES - 1) / ALINES);
-    if (a.sph) k_adj_xfwd<true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
-    else k_adj_xfwd<false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+    const bool f = a.dt_gn2 > 0.f;
+    if (a.sph) {
+        if (f) k_adj_xfwd<true, true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+        else k_adj_xfwd<true, false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+    } else {
+        if (f) k_adj_xfwd<false, true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+        else k_adj_xfwd<false, false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
+    }
     return cudaGetLastError();
 }
 

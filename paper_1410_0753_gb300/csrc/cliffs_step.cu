@@ -210,7 +210,7 @@ struct Samples {
 // One warp of the fused step. A work item is a strip and an output row range [r0, r1); the
 // warp walks rows r0-3 .. r1+2 as pairs, one pair per ring slot. The ring's slot and phase
 // follow a running pair count, so a warp may process any number of items in a row.
-template <bool SPH>
+template <bool SPH, bool FRIC>
 struct FusedWarp {
     const StepArgs& a;
     SweepConst K;
@@ -255,27 +255,30 @@ struct FusedWarp {
         }
     }
 
-    // one row k held at `s` (row h of its slot)
-    template <int PH>
-    __device__ __forceinline__ void row(int k, const float* s) {
-        float2 E = reinterpret_cast<const float2*>(s + 0 * ARR_FLOATS)[lane];
-        float2 U = reinterpret_cast<const float2*>(s + 1 * ARR_FLOATS)[lane];
-        float2 V = reinterpret_cast<const float2*>(s + 2 * ARR_FLOATS)[lane];
-        float2 D = reinterpret_cast<const float2*>(s + 3 * ARR_FLOATS)[lane];
-        const float4 m2 = __ldg(a.ymet + k - 2);
+    // row k held at `s`: its values (zero state, dry depth outside the domain) and x metric
+    __device__ __forceinline__ bool load_row(int k, const float* s, float2& E, float2& U, float2& V, float2& D,
+                                             XMet2& m) {
+        E = reinterpret_cast<const float2*>(s + 0 * ARR_FLOATS)[lane];
+        U = reinterpret_cast<const float2*>(s + 1 * ARR_FLOATS)[lane];
+        V = reinterpret_cast<const float2*>(s + 2 * ARR_FLOATS)[lane];
+        D = reinterpret_cast<const float2*>(s + 3 * ARR_FLOATS)[lane];
         const bool rowin = k >= 0 && k < a.ny;
         if (edge || !rowin) {
             if (!(rowin && colA)) { E.x = U.x = V.x = 0.f; D.x = OUTSIDE_D; }
             if (!(rowin && colB)) { E.y = U.y = V.y = 0.f; D.y = OUTSIDE_D; }
         }
-        if (rowin) {
-            XMet2 m = m0;
-            if (SPH) {
-                const float2 f = v2(__ldg(a.xrow + k));
-                m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
-            }
-            xsweep2(E, U, V, D, m, K, lane);
+        m = m0;
+        if (SPH && rowin) {
+            const float2 f = v2(__ldg(a.xrow + k));
+            m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
         }
+        return rowin;
+    }
+
+    // the x-swept row k into the y-sweep pipeline; the finished row k - 3 goes out
+    template <int PH>
+    __device__ __forceinline__ void push_row(int k, const float* s, float2 E, float2 U, float2 V, float2 D) {
+        const float4 m2 = __ldg(a.ymet + k - 2);
         // y-sweep input of row k: eta, w = v, t = u
         const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
         // a non-finite x-sweep result reads as a dry node in the y-sweep and would be
@@ -283,7 +286,7 @@ struct FusedWarp {
         if (vA && !oA) bad |= !(fabsf(E.x) < 1e5f);
         if (vB && !oB) bad |= !(fabsf(E.y) < 1e5f);
         const int r = k - 3;
-        ym.template push<PH, SPH>(E, V, U, D, oA, oB, m2, K, vA, vB,
+        ym.template push<PH, SPH, FRIC>(E, V, U, D, oA, oB, m2, K, vA, vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     float2 em = make_float2(0.f, 0.f), sm = em;
@@ -295,6 +298,15 @@ struct FusedWarp {
                     smp.emit(a, O, b, r, c0, lane, oe, ot, ow);
                 }
             });
+    }
+
+    // row k of a ring slot: x-sweep, then into the y-sweep pipeline
+    template <int PH>
+    __device__ __forceinline__ void row(int k, const float* s) {
+        float2 E, U, V, D;
+        XMet2 m;
+        if (load_row(k, s, E, U, V, D, m)) xsweep2<FRIC>(E, U, V, D, m, K, lane);
+        push_row<PH>(k, s, E, U, V, D);
     }
 
     // Process work item `idx` (strip, rows) of scenario b_ for the step described by O_.
@@ -354,7 +366,7 @@ struct FusedWarp {
     }
 };
 
-template <bool SPH>
+template <bool SPH, bool FRIC>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -365,7 +377,7 @@ k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     if (a.limit && a.step > a.limit[b]) return;
     // a wait of an earlier launch expired: do not start new copies
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH> W(a);
+    FusedWarp<SPH, FRIC> W(a);
     W.setup(smem_raw, wib);
     W.run_item(gw, b, step_out(&M, a));
     W.report();
@@ -413,7 +425,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned nblo
 // (the halves of ctl[3]) alternate by step parity; block 0 clears the one the next step
 // uses while the other is in use. A scenario that has stopped keeps its last state in the
 // buffer of its last step's parity.
-template <bool SPH>
+template <bool SPH, bool FRIC>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -421,7 +433,7 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
     const long long step0 = B.ctl[0], step_end = B.ctl[1];
     unsigned* tickets = reinterpret_cast<unsigned*>(B.ctl + 3);
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH> W(a);
+    FusedWarp<SPH, FRIC> W(a);
     W.setup(smem_raw, wib);
     for (long long st = step0 + 1; st <= step_end; ++st) {
         const bool odd = (st & 1) != 0;          // odd steps read buffer 0 and write buffer 1
@@ -448,7 +460,7 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
 }
 
 // x-sweep alone: one warp per (row, strip of 56 columns).
-template <bool SPH>
+template <bool SPH, bool FRIC>
 __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     }
     float2 E, U, V, D;
     load_pair(a, boff, r, cA, E, U, V, D);
-    xsweep2(E, U, V, D, m, K, lane);
+    xsweep2<FRIC>(E, U, V, D, m, K, lane);
     const bool own = lane >= 2 && lane < 30;
     const bool va = own && cA < a.nx, vb = own && cA + 1 < a.nx;
     int bad = 0;
@@ -489,7 +501,7 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
 }
 
 // y-sweep alone: one warp per (strip of 64 columns, S rows).
-template <bool SPH>
+template <bool SPH, bool FRIC>
 struct YOnly {
     const StepArgs& a;
     SweepConst K;
@@ -508,7 +520,7 @@ struct YOnly {
         const float4 m2 = __ldg(a.ymet + k - 2);
         const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
         const int r = k - 3;
-        ym.template push<PH, SPH>(E, V, U, D, oA, oB, m2, K, vA, vB,
+        ym.template push<PH, SPH, FRIC>(E, V, U, D, oA, oB, m2, K, vA, vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     const size_t o = boff + (size_t)r * a.pitch + cA;
@@ -524,14 +536,14 @@ struct YOnly {
     }
 };
 
-template <bool SPH>
+template <bool SPH, bool FRIC>
 __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int b = blockIdx.y;
     if (gw >= a.nstrips * a.nseg) return;
     if (a.limit && a.step > a.limit[b]) return;
-    YOnly<SPH> Y(a);
+    YOnly<SPH, FRIC> Y(a);
     Y.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
     const int strip = gw % a.nstrips, seg = gw / a.nstrips;
     Y.lane = lane;
@@ -559,16 +571,21 @@ __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
 
 // ------------------------------------------------------------------ launchers
 // the ring needs more than the default 48 KB of dynamic shared memory per block
+// the kernel variant for the grid's metric (spherical or not) and friction (on or off)
+#define CLIFFS_VARIANT(K, sph, fric) \
+    ((sph) ? ((fric) ? K<true, true> : K<true, false>) : ((fric) ? K<false, true> : K<false, false>))
+
 static cudaError_t fused_smem_optin() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
-        done = cudaFuncSetAttribute(k_step_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(k_step_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        done = cudaSuccess;
+        for (int v = 0; v < 4 && done == cudaSuccess; ++v) {
+            done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_step_fused, v & 1, v & 2),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+            if (done == cudaSuccess)
+                done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_batch, v & 1, v & 2),
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        }
     }
     return done;
 }
@@ -578,8 +595,7 @@ cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, c
     if (e != cudaSuccess) return e;
     const int nw = a.nitems;
     const dim3 grid((nw + FUSED_WARPS - 1) / FUSED_WARPS, batch);
-    if (a.sph) k_step_fused<true><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
-    else k_step_fused<false><<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
+    CLIFFS_VARIANT(k_step_fused, a.sph, a.dt_gn2 > 0.f)<<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
     return cudaGetLastError();
 }
 
@@ -596,23 +612,22 @@ cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (a.sph) return cudaLaunchKernelEx(&cfg, k_batch<true>, mm, a, b);
-    return cudaLaunchKernelEx(&cfg, k_batch<false>, mm, a, b);
+    return cudaLaunchKernelEx(&cfg, CLIFFS_VARIANT(k_batch, a.sph, a.dt_gn2 > 0.f), mm, a, b);
 }
 
 int batch_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    if (sph) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true>, FUSED_WARPS * 32, FUSED_SMEM);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false>, FUSED_WARPS * 32, FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT(k_batch, sph, true), FUSED_WARPS * 32,
+                                                  FUSED_SMEM);
     return nb;
 }
 
 int fused_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    if (sph) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<true>, FUSED_WARPS * 32, FUSED_SMEM);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<false>, FUSED_WARPS * 32, FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT(k_step_fused, sph, true), FUSED_WARPS * 32,
+                                                  FUSED_SMEM);
     return nb;
 }
 
@@ -621,16 +636,14 @@ int fused_warps_per_block() { return FUSED_WARPS; }
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s) {
     const int nw = a.nstrips * a.ny;
     const dim3 grid((nw + 3) / 4, batch);
-    if (a.sph) k_xsweep<true><<<grid, 128, 0, s>>>(a);
-    else k_xsweep<false><<<grid, 128, 0, s>>>(a);
+    CLIFFS_VARIANT(k_xsweep, a.sph, a.dt_gn2 > 0.f)<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ysweep(const StepArgs& a, int batch, cudaStream_t s) {
     const int nw = a.nstrips * a.nseg;
     const dim3 grid((nw + 3) / 4, batch);
-    if (a.sph) k_ysweep<true><<<grid, 128, 0, s>>>(a);
-    else k_ysweep<false><<<grid, 128, 0, s>>>(a);
+    CLIFFS_VARIANT(k_ysweep, a.sph, a.dt_gn2 > 0.f)<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,7 @@ __device__ __forceinline__ void ghost_right(float w, float c, float inv, float& 
 //   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep (SRC).
 // Friction: alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3) at time level n on both p and q,
 // clamped so that |alpha dt| <= |w|.
-template <bool SRC>
+template <bool SRC, bool FRIC>
 __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float2 d, float2 c,
                                              const Flux2& L, const Flux2& R, float2 k2, float2 sdt,
                                              const SweepConst& K,
@@ -132,7 +132,7 @@ __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float
     const float2 nh = v2(-K.half_dt);
     float2 dp = fma2(mul2(lp, k2), sub2(R.p, L.p), mul2(nh, add2(L.p, R.p)));
     float2 dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(nh, add2(L.q, R.q)));
-    if (K.dt_gn2 > 0.f) {
+    if (FRIC) {
         const float2 h = add2(e, d);
         const float2 s2 = fma2(w, w, mul2(t, t));
         const float2 s = mul2(s2, make_float2(rsqrt_approx(fmaxf(s2.x, 1e-30f)),
@@ -152,10 +152,8 @@ __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float
     const float2 dc = mul2(v2(0.25f), sub2(dp, dq));
     w2 = add2(w, du);
     e2 = fma2(mul2(dc, fma2(v2(2.f), c, dc)), v2(INV_GRAV), e);
-    if (K.transverse)
-        t2 = fma2(mul2(w, k2), sub2(R.t, L.t), fma2(nh, add2(L.t, R.t), t));
-    else
-        t2 = t;
+    const float2 tn = fma2(mul2(w, k2), sub2(R.t, L.t), fma2(nh, add2(L.t, R.t), t));
+    t2 = K.transverse ? tn : t;
 }
 
 // (e): a node wetted in (b) against its source neighbour's state after (d).
@@ -187,6 +185,7 @@ struct XMet2 { float2 inv_l, inv_r, k2; };   // per pair: 1/dx_{j-1}, 1/dx_j, dt
 // and B = 2l + 1 (.y). Neighbours across lanes come by shuffles. On return (E, W, T) hold
 // the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each side
 // lack their 3-node dependency radius). W is the velocity along the row, T across it.
+template <bool FRIC>
 __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
                                         const SweepConst& K, int lane) {
     const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
@@ -244,7 +243,7 @@ __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 
         if (!wetR) ghost_right(W.y, C.y, m.inv_r.y, FR.p.y, FR.q.y, FR.t.y);
     }
     float2 E2, W2, T2;
-    node_update2<false>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2);
+    node_update2<false, FRIC>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2);
     if (!allwet) {
         if (!wA) { E2.x = E.x; W2.x = W.x; T2.x = T.x; }
         if (!wB) { E2.y = E.y; W2.y = W.y; T2.y = T.y; }
@@ -303,7 +302,7 @@ struct YMarch2 {
     // m2: metric of row k-2 (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R).
     // emit(e, w, t, d) receives the finished row k-3; o0A/o0B: the incoming row's wet marks.
     // careA/careB: whether this lane's columns are emitted; the others may compute anything.
-    template <int PH, bool SRC, class Emit>
+    template <int PH, bool SRC, bool FRIC, class Emit>
     __device__ __forceinline__ void push(float2 E0, float2 W0, float2 T0, float2 D0, bool o0A, bool o0B,
                                          float4 m2, const SweepConst& K, bool careA, bool careB,
                                          Emit&& emit) {
@@ -322,7 +321,7 @@ struct YMarch2 {
             emit(e3, w3, t3, d3);
             h4 = add2(e3, d3);
             w4 = w3;
-            node_update2<SRC>(P.e, P.w, P.t, P.d, P.c, F3, F2, v2(m2.z), v2(m2.w), K, e3, w3, t3);
+            node_update2<SRC, FRIC>(P.e, P.w, P.t, P.d, P.c, F3, F2, v2(m2.z), v2(m2.w), K, e3, w3, t3);
         } else {
             // (a)/(b) on row k-1 (input held in B1), neighbours row k-2 (P) and row k (new)
             B1.wA = B1.oA;
@@ -353,7 +352,7 @@ struct YMarch2 {
             if (P.wB && !f3B) ghost_left(P.w.y, P.c.y, m2.x, L.p.y, L.q.y, L.t.y);
             if (P.wB && !B1.wB) ghost_right(P.w.y, P.c.y, m2.y, R.p.y, R.q.y, R.t.y);
             float2 ne, nw, nt;
-            node_update2<SRC>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt);
+            node_update2<SRC, FRIC>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt);
             if (!P.wA) { ne.x = P.e.x; nw.x = P.w.x; nt.x = P.t.x; }
             if (!P.wB) { ne.y = P.e.y; nw.y = P.w.y; nt.y = P.t.y; }
             // (e) on row k-3, against row k-4 (h4, w4) or row k-2 (ne, nw)
