@@ -208,6 +208,29 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         fl[i] = d[i] >= K.dwall;
         o[i] = fl[i] && (e[i] + d[i] >= K.hmin);
     }
+    if (__all_sync(FULL, o[0] && o[1])) {
+        // every node of the window wet: no (b), no walls, no (e); only the stencil of (d)
+        float c[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) c[i] = wave_speed(e[i] + d[i]);
+        float eL[2], eR[2], wL[2], wR[2], tL[2], tR[2], dL[2], dR[2], cL[2], cR[2];
+        nbr(e, eL, eR); nbr(w, wL, wR); nbr(t, tL, tR); nbr(d, dL, dR); nbr(c, cL, cR);
+        ABar bL[2], bC[2], bR[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            bL[i] = bC[i] = bR[i] = ABar{0.f, 0.f, 0.f};
+            a_dstage_adj<SRC>(ANode{eL[i], wL[i], tL[i], dL[i], cL[i]}, ANode{e[i], w[i], t[i], d[i], c[i]},
+                              ANode{eR[i], wR[i], tR[i], dR[i], cR[i]}, m[i], K, ge[i], gw[i], gt[i],
+                              bL[i], bC[i], bR[i]);
+        }
+        oe[0] = bC[0].e + bL[1].e + __shfl_up_sync(FULL, bR[1].e, 1);
+        ow[0] = bC[0].w + bL[1].w + __shfl_up_sync(FULL, bR[1].w, 1);
+        ot[0] = bC[0].t + bL[1].t + __shfl_up_sync(FULL, bR[1].t, 1);
+        oe[1] = bC[1].e + bR[0].e + __shfl_down_sync(FULL, bL[0].e, 1);
+        ow[1] = bC[1].w + bR[0].w + __shfl_down_sync(FULL, bL[0].w, 1);
+        ot[1] = bC[1].t + bR[0].t + __shfl_down_sync(FULL, bL[0].t, 1);
+        return;
+    }
     // (b) flooding from the wetter neighbour (left on a tie), start-of-sweep values
     float eL[2], eR[2], wL[2], wR[2], tL[2], tR[2];
     int oL[2], oR[2];
@@ -345,7 +368,7 @@ __device__ __forceinline__ void load2(const float* p, long long o, int pos, int 
 // the output is written transposed; DIR 1: lines are rows of transposed data (columns of
 // the grid) and the output is written row-major.
 template <int DIR, bool SPH>
-__global__ void __launch_bounds__(AWARPS * 32) k_adj_line(const AdjLineArgs A) {
+__global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const AdjLineArgs A) {
     __shared__ float tile[3][AOUT][TP];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int strip = blockIdx.x, l0 = blockIdx.y * ALINES;
