@@ -15,9 +15,10 @@ device synchronisation; the maximum over ranks is reported. With N > 1 each rank
 its own replica of the grid (the path does not shard: replicas only).
 
 With one GPU the line also carries ``forms``: the batched ensemble (256 scenarios of uneven
-duration on a shared 512 x 512 bathymetry in one persistent, graph-captured launch) and the
-adjoint (gradient of a 32-gauge misfit over 2000 steps of a 1024 x 1024 grid), each next to
-the plain single-scenario forward on the same GPU.
+duration on a shared 512 x 512 bathymetry in one persistent, graph-captured launch), the
+8192 x 8192 shelf-and-islands stress grid (pure step and max-wave every step) and the
+adjoint (gradient of a 32-gauge misfit over 2000 steps of a 1024 x 1024 grid), the batched
+and adjoint forms next to the plain single-scenario forward on the same GPU.
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload on the host cores.
 """
@@ -235,6 +236,25 @@ def measure_forms(torch, stream):
         "vs_single_scenario_forward": v_b / v_1,
         "note": "useful cell-updates (each scenario up to its own duration) / time of one "
                 "persistent, cooperative, graph-captured launch"}
+    # the HBM stress grid (8192 x 8192, shorelines around 10 islands), as a pure step and with
+    # max-wave every step; its 1.9 GB working set is far larger than L2
+    w = workloads.shelf_islands()
+    peaks, _ = measured_peaks()
+    out["stress"] = {"workload": w.name, "cells": w.cells}
+    for tag, maxout, bpc in (("pure_step", 10 ** 9, 28), ("maxwave_every_step", 1, 36)):
+        g = CliffsGrid.from_workload(w, stream=s, maxout=maxout, gauges=[], nests=[])
+        g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+        g.set_initial(w.eta0.astype(np.float32))
+        tune = g.autotune(2)
+        g.step(5)
+        n = 60
+        ms = _event_ms(torch, stream, lambda: g.step(n))
+        v = w.cells * n / (ms / 1e3) / 1e9
+        out["stress"][tag] = {"value": v, "unit": UNIT, "steps": n, "ms_per_step": ms / n,
+                              "bytes_per_cell": bpc, "achieved_gbs": v * bpc,
+                              "frac": v * bpc / peaks["hbm_gbs"],
+                              "rows_per_warp": min(tune, key=tune.get) if tune else None}
+        g.close()
     # adjoint
     w = workloads.inversion_1024()
     g = CliffsGrid.from_workload(w, stream=s)

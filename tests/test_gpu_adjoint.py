@@ -98,16 +98,59 @@ def test_adjoint_gradient_matches_finite_differences_through_autograd():
     assert np.isfinite(grad).all() and np.abs(grad).max() > 0
     h = 1e-3
     worst = 0.0
+    rng = np.random.default_rng(5)
+    dirs = []
+    for k in np.argsort(-np.abs(grad))[:8]:             # 8 coordinates
+        e = np.zeros(64)
+        e[k] = 1.0
+        dirs.append(e)
+    for _ in range(4):                                  # and 4 random directions
+        v = rng.standard_normal(64)
+        dirs.append(v / np.linalg.norm(v))
     with torch.no_grad():
-        for k in np.argsort(-np.abs(grad))[:6]:
-            e = torch.zeros_like(theta)
-            e[k] = h
+        for v in dirs:
+            e = torch.tensor(h * v, dtype=theta.dtype, device="cuda")
             fd = (loss(theta + e).item() - loss(theta - e).item()) / (2 * h)
-            err = abs(fd - grad[k]) / np.abs(grad).max()
+            want = float(grad @ v)
+            err = abs(fd - want) / np.abs(grad).max()
             worst = max(worst, err)
-            assert err <= FD_RTOL, (k, fd, grad[k])
+            assert err <= FD_RTOL, (fd, want)
     P.report("adjoint_fd_inversion", rel_err=worst)
     g.close()
+
+
+def test_adjoint_unit_source_gradient_against_oracle():
+    """The gradient of L = sum (eta_g - obs)^2 with respect to all 64 unit-source
+    coefficients, obs from the FP64 oracle at the true coefficients: GPU forward + adjoint
+    against the oracle's own forward and tangent-linear runs, within 1e-3 relative L2 over
+    the 64-vector."""
+    w = workloads.inversion_1024(nx=128, ny=112, steps=100)
+    n = w.steps
+    basis = w.extra["basis"].astype(np.float64)
+    d64 = P.f32(P.oracle_depth(w))
+    p = oracle.params_from(w)
+    eta_true = P.f32(np.tensordot(w.extra["theta_true"].astype(np.float64), basis, axes=1))
+    obs = oracle.run(p, w.x, w.y, d64, eta_true, nsteps=n, gout=w.gout, gauges=w.gauges)["gauges"][:, :, 0]
+    # GPU: forward at theta0, seed 2 (eta - obs), adjoint, projected on the basis
+    g = _start(w)
+    g.step(n)
+    seed32 = (2.0 * (g.gauges()[:, :, 0].astype(np.float64) - obs)).astype(np.float32)
+    g.set_initial(w.eta0.astype(np.float32))
+    grad_eta = g.adjoint(n, seed32, checkpoint_every=30).astype(np.float64)
+    gpu = basis.reshape(64, -1) @ grad_eta.ravel()
+    g.close()
+    # oracle: its own forward residual and one tangent-linear run per coefficient
+    r64 = oracle.run(p, w.x, w.y, d64, w.eta0, nsteps=n, gout=w.gout, gauges=w.gauges)["gauges"][:, :, 0]
+    seed64 = 2.0 * (r64 - obs)
+    ref = np.empty(64)
+    for k in range(64):
+        _, gtan, _, _ = oracle.run_tlm(p, w.x, w.y, d64, w.eta0, basis[k], nsteps=n, gout=w.gout,
+                                       gauges=w.gauges)
+        ref[k] = float((seed64 * gtan).sum())
+    rel = np.linalg.norm(gpu - ref) / np.linalg.norm(ref)
+    P.report("adjoint_theta64_vs_oracle", rel_l2=rel)
+    assert np.linalg.norm(ref) > 0
+    assert rel <= 1e-3, rel
 
 
 def test_adjoint_checkpoint_spacing_and_state_untouched():
