@@ -68,7 +68,10 @@ typedef struct cliffs_config {
     double  dt;                 /* time step, s; the CFL number |lambda| dt/dx must be <= 1 */
     int32_t transverse;         /* 1: advect the transverse velocity, eq. (pq3) */
     int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) */
-    int32_t alternate;          /* 0: x then y every step; 1: y first on odd steps */
+    int32_t alternate;          /* 0: x then y every step; 1: y first on the odd steps
+                                   (counted from 0 at set_initial), the alternating reading of
+                                   section "Numerics"; cliffs_step_n only (the persistent run
+                                   and the adjoint reject it) */
     int32_t maxout;             /* steps between max-wave updates (> 0) */
     int32_t gout;               /* steps between gauge records (> 0) */
     int32_t bndout;             /* steps between boundary-series records (> 0) */

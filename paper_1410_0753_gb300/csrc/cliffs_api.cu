@@ -550,6 +550,7 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.sph = g->cfg.coords != 1;
     a.wait_cycles = 2000000000LL;            // about a second at the GB300's clocks
     a.tx_pad = 0;
+    a.yfirst = 0;
 }
 
 void free_grid(cliffs_grid* g) {
@@ -611,7 +612,7 @@ int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
         return set_err(CLIFFS_ERR_ARG, "maxout, gout and bndout must be >= 1");
     if (!(cfg->solver == 0 || cfg->solver == 2))
         return set_err(CLIFFS_ERR_ARG, "solver %d is not available (use 2)", cfg->solver);
-    if (cfg->alternate != 0) return set_err(CLIFFS_ERR_ARG, "alternate sweep order is not available");
+    if (cfg->alternate != 0 && cfg->alternate != 1) return set_err(CLIFFS_ERR_ARG, "alternate must be 0 or 1");
     if (cfg->n_gauges < 0 || (cfg->n_gauges > 0 && !cfg->gauge_ixiy))
         return set_err(CLIFFS_ERR_ARG, "bad gauge list");
     for (int k = 0; k < cfg->n_gauges; ++k) {
@@ -966,6 +967,7 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
         const int in = (int)(g->step & 1), out = 1 - in;
         fill_step_args(g, a, in, out);
         a.step = st;
+        a.yfirst = g->cfg.alternate && ((st - 1) & 1);       // odd steps sweep y first
         if (st % g->cfg.maxout == 0) { a.emax = g->emax; a.smax = g->smax; }
         if (g->G && st % g->cfg.gout == 0) a.rec_g = g->grec + (st / g->cfg.gout) * g->G * 3;
         if (g->NN && st % g->cfg.bndout == 0) a.rec_n = g->nrec + (st / g->cfg.bndout) * g->NN * 3;
@@ -1010,6 +1012,7 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
+    if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the persistent run sweeps x then y every step");
     if (n == 0) return CLIFFS_OK;
     const long long last = g->step + n;
     int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
@@ -1117,6 +1120,7 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
+    if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes the x-then-y order only");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);

@@ -209,8 +209,10 @@ struct Samples {
 // ------------------------------------------------------------------ fused step
 // One warp of the fused step. A work item is a strip and an output row range [r0, r1); the
 // warp walks rows r0-3 .. r1+2 as pairs, one pair per ring slot. The ring's slot and phase
-// follow a running pair count, so a warp may process any number of items in a row.
-template <bool SPH, bool FRIC>
+// follow a running pair count, so a warp may process any number of items in a row. With YF
+// (a y-first step of the alternating order) rows enter the y-sweep pipeline unswept and each
+// finished row is x-swept across the warp on its way out; the tile geometry is the same.
+template <bool SPH, bool FRIC, bool YF = false>
 struct FusedWarp {
     const StepArgs& a;
     SweepConst K;
@@ -289,6 +291,15 @@ struct FusedWarp {
         ym.template push<PH, SPH, FRIC>(E, V, U, D, oA, oB, m2, K, vA, vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
+                    if (YF) {
+                        // x-sweep of the y-swept row r: along-row velocity u (ot), across v (ow)
+                        XMet2 mr = m0;
+                        if (SPH) {
+                            const float2 f = v2(__ldg(a.xrow + r));
+                            mr.inv_l = mul2(mr.inv_l, f); mr.inv_r = mul2(mr.inv_r, f); mr.k2 = mul2(mr.k2, f);
+                        }
+                        xsweep2<FRIC>(oe, ot, ow, od, mr, K, lane);
+                    }
                     float2 em = make_float2(0.f, 0.f), sm = em;
                     if (O.emax) {
                         em = reinterpret_cast<const float2*>(s + 4 * ARR_FLOATS)[lane];
@@ -305,7 +316,7 @@ struct FusedWarp {
     __device__ __forceinline__ void row(int k, const float* s) {
         float2 E, U, V, D;
         XMet2 m;
-        if (load_row(k, s, E, U, V, D, m)) xsweep2<FRIC>(E, U, V, D, m, K, lane);
+        if (load_row(k, s, E, U, V, D, m) && !YF) xsweep2<FRIC>(E, U, V, D, m, K, lane);
         push_row<PH>(k, s, E, U, V, D);
     }
 
@@ -366,7 +377,7 @@ struct FusedWarp {
     }
 };
 
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool YF>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -377,7 +388,7 @@ k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     if (a.limit && a.step > a.limit[b]) return;
     // a wait of an earlier launch expired: do not start new copies
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH, FRIC> W(a);
+    FusedWarp<SPH, FRIC, YF> W(a);
     W.setup(smem_raw, wib);
     W.run_item(gw, b, step_out(&M, a));
     W.report();
@@ -574,17 +585,21 @@ __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
 // the kernel variant for the grid's metric (spherical or not) and friction (on or off)
 #define CLIFFS_VARIANT(K, sph, fric) \
     ((sph) ? ((fric) ? K<true, true> : K<true, false>) : ((fric) ? K<false, true> : K<false, false>))
+#define CLIFFS_VARIANT3(K, sph, fric, yf) \
+    ((yf) ? CLIFFS_VARIANT2(K, sph, fric, true) : CLIFFS_VARIANT2(K, sph, fric, false))
+#define CLIFFS_VARIANT2(K, sph, fric, yf) \
+    ((sph) ? ((fric) ? K<true, true, yf> : K<true, false, yf>) : ((fric) ? K<false, true, yf> : K<false, false, yf>))
 
 static cudaError_t fused_smem_optin() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
         done = cudaSuccess;
-        for (int v = 0; v < 4 && done == cudaSuccess; ++v) {
-            done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_step_fused, v & 1, v & 2),
+        for (int v = 0; v < 8 && done == cudaSuccess; ++v)
+            done = cudaFuncSetAttribute(CLIFFS_VARIANT3(k_step_fused, v & 1, v & 2, v & 4),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-            if (done == cudaSuccess)
-                done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_batch, v & 1, v & 2),
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
+        for (int v = 0; v < 4 && done == cudaSuccess; ++v) {
+            done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_batch, v & 1, v & 2),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
         }
     }
     return done;
@@ -595,7 +610,7 @@ cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, c
     if (e != cudaSuccess) return e;
     const int nw = a.nitems;
     const dim3 grid((nw + FUSED_WARPS - 1) / FUSED_WARPS, batch);
-    CLIFFS_VARIANT(k_step_fused, a.sph, a.dt_gn2 > 0.f)<<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
+    CLIFFS_VARIANT3(k_step_fused, a.sph, a.dt_gn2 > 0.f, a.yfirst != 0)<<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
     return cudaGetLastError();
 }
 
@@ -626,8 +641,8 @@ int batch_blocks_per_sm(bool sph) {
 int fused_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT(k_step_fused, sph, true), FUSED_WARPS * 32,
-                                                  FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT3(k_step_fused, sph, true, false),
+                                                  FUSED_WARPS * 32, FUSED_SMEM);
     return nb;
 }
 

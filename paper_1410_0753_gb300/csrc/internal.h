@@ -40,6 +40,7 @@ struct StepArgs {
     float hmin, dwall, half_dt, dt_gn2;
     int transverse;
     int sph;                         // geographic grid: x metric scaled per row
+    int yfirst;                      // this step sweeps y, then x (alternating order)
     long long wait_cycles;           // limit of every mbarrier wait (clock cycles)
     unsigned tx_pad;                 // extra bytes each ring slot expects (fault injection; 0)
 };
