@@ -551,6 +551,7 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.wait_cycles = 2000000000LL;            // about a second at the GB300's clocks
     a.tx_pad = 0;
     a.yfirst = 0;
+    a.inv_dt2_s1 = g->cfg.solver == 1 ? (float)(1.0 / (g->cfg.dt * g->cfg.dt)) : 0.f;
 }
 
 void free_grid(cliffs_grid* g) {
@@ -610,8 +611,8 @@ int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
     if (cfg->manning_n2 < 0.0) return set_err(CLIFFS_ERR_ARG, "manning_n2 must be >= 0");
     if (cfg->maxout < 1 || cfg->gout < 1 || cfg->bndout < 1)
         return set_err(CLIFFS_ERR_ARG, "maxout, gout and bndout must be >= 1");
-    if (!(cfg->solver == 0 || cfg->solver == 2))
-        return set_err(CLIFFS_ERR_ARG, "solver %d is not available (use 2)", cfg->solver);
+    if (!(cfg->solver == 0 || cfg->solver == 1 || cfg->solver == 2))
+        return set_err(CLIFFS_ERR_ARG, "solver must be 1 or 2 (0 means 2)");
     if (cfg->alternate != 0 && cfg->alternate != 1) return set_err(CLIFFS_ERR_ARG, "alternate must be 0 or 1");
     if (cfg->n_gauges < 0 || (cfg->n_gauges > 0 && !cfg->gauge_ixiy))
         return set_err(CLIFFS_ERR_ARG, "bad gauge list");
@@ -1121,6 +1122,7 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
     if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes the x-then-y order only");
+    if (g->cfg.solver == 1) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes eq. (solver2) only");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);

@@ -212,7 +212,7 @@ struct Samples {
 // follow a running pair count, so a warp may process any number of items in a row. With YF
 // (a y-first step of the alternating order) rows enter the y-sweep pipeline unswept and each
 // finished row is x-swept across the warp on its way out; the tile geometry is the same.
-template <bool SPH, bool FRIC, bool YF = false>
+template <bool SPH, bool FRIC, bool YF = false, bool S1 = false>
 struct FusedWarp {
     const StepArgs& a;
     SweepConst K;
@@ -233,7 +233,7 @@ struct FusedWarp {
 
     __device__ __forceinline__ void setup(unsigned char* smem_raw, int wib) {
         lane = threadIdx.x & 31;
-        K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+        K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse, a.inv_dt2_s1};
         ring = reinterpret_cast<float*>(smem_raw + wib * WARP_RING_BYTES);
         bar = reinterpret_cast<uint64_t*>(smem_raw + FUSED_WARPS * WARP_RING_BYTES) + wib * RING;
         used = 0;
@@ -288,7 +288,7 @@ struct FusedWarp {
         if (vA && !oA) bad |= !(fabsf(E.x) < 1e5f);
         if (vB && !oB) bad |= !(fabsf(E.y) < 1e5f);
         const int r = k - 3;
-        ym.template push<PH, SPH, FRIC>(E, V, U, D, oA, oB, m2, K, vA, vB,
+        ym.template push<PH, SPH, FRIC, S1>(E, V, U, D, oA, oB, m2, K, vA, vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     if (YF) {
@@ -298,7 +298,7 @@ struct FusedWarp {
                             const float2 f = v2(__ldg(a.xrow + r));
                             mr.inv_l = mul2(mr.inv_l, f); mr.inv_r = mul2(mr.inv_r, f); mr.k2 = mul2(mr.k2, f);
                         }
-                        xsweep2<FRIC>(oe, ot, ow, od, mr, K, lane);
+                        xsweep2<FRIC, S1>(oe, ot, ow, od, mr, K, lane);
                     }
                     float2 em = make_float2(0.f, 0.f), sm = em;
                     if (O.emax) {
@@ -316,7 +316,7 @@ struct FusedWarp {
     __device__ __forceinline__ void row(int k, const float* s) {
         float2 E, U, V, D;
         XMet2 m;
-        if (load_row(k, s, E, U, V, D, m) && !YF) xsweep2<FRIC>(E, U, V, D, m, K, lane);
+        if (load_row(k, s, E, U, V, D, m) && !YF) xsweep2<FRIC, S1>(E, U, V, D, m, K, lane);
         push_row<PH>(k, s, E, U, V, D);
     }
 
@@ -377,7 +377,7 @@ struct FusedWarp {
     }
 };
 
-template <bool SPH, bool FRIC, bool YF>
+template <bool SPH, bool FRIC, bool YF, bool S1>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -388,7 +388,7 @@ k_step_fused(const __grid_constant__ StepMaps M, const StepArgs a) {
     if (a.limit && a.step > a.limit[b]) return;
     // a wait of an earlier launch expired: do not start new copies
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH, FRIC, YF> W(a);
+    FusedWarp<SPH, FRIC, YF, S1> W(a);
     W.setup(smem_raw, wib);
     W.run_item(gw, b, step_out(&M, a));
     W.report();
@@ -436,7 +436,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned nblo
 // (the halves of ctl[3]) alternate by step parity; block 0 clears the one the next step
 // uses while the other is in use. A scenario that has stopped keeps its last state in the
 // buffer of its last step's parity.
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool S1>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -444,7 +444,7 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
     const long long step0 = B.ctl[0], step_end = B.ctl[1];
     unsigned* tickets = reinterpret_cast<unsigned*>(B.ctl + 3);
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
-    FusedWarp<SPH, FRIC> W(a);
+    FusedWarp<SPH, FRIC, false, S1> W(a);
     W.setup(smem_raw, wib);
     for (long long st = step0 + 1; st <= step_end; ++st) {
         const bool odd = (st & 1) != 0;          // odd steps read buffer 0 and write buffer 1
@@ -471,7 +471,7 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
 }
 
 // x-sweep alone: one warp per (row, strip of 56 columns).
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool S1>
 __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     const int c0 = strip * XOUT - 4;
     const int cA = c0 + 2 * lane;
     const size_t boff = (size_t)b * a.plane;
-    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse, a.inv_dt2_s1};
     float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
     if (cA >= 0 && cA < a.nx) { il.x = a.xa[cA]; ir.x = a.xb[cA]; k2.x = a.xk[cA]; }
     if (cA + 1 >= 0 && cA + 1 < a.nx) { il.y = a.xa[cA + 1]; ir.y = a.xb[cA + 1]; k2.y = a.xk[cA + 1]; }
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
     }
     float2 E, U, V, D;
     load_pair(a, boff, r, cA, E, U, V, D);
-    xsweep2<FRIC>(E, U, V, D, m, K, lane);
+    xsweep2<FRIC, S1>(E, U, V, D, m, K, lane);
     const bool own = lane >= 2 && lane < 30;
     const bool va = own && cA < a.nx, vb = own && cA + 1 < a.nx;
     int bad = 0;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128) k_xsweep(const StepArgs a) {
 }
 
 // y-sweep alone: one warp per (strip of 64 columns, S rows).
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool S1>
 struct YOnly {
     const StepArgs& a;
     SweepConst K;
@@ -531,7 +531,7 @@ struct YOnly {
         const float4 m2 = __ldg(a.ymet + k - 2);
         const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
         const int r = k - 3;
-        ym.template push<PH, SPH, FRIC>(E, V, U, D, oA, oB, m2, K, vA, vB,
+        ym.template push<PH, SPH, FRIC, S1>(E, V, U, D, oA, oB, m2, K, vA, vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     const size_t o = boff + (size_t)r * a.pitch + cA;
@@ -547,15 +547,15 @@ struct YOnly {
     }
 };
 
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool S1>
 __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int b = blockIdx.y;
     if (gw >= a.nstrips * a.nseg) return;
     if (a.limit && a.step > a.limit[b]) return;
-    YOnly<SPH, FRIC> Y(a);
-    Y.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    YOnly<SPH, FRIC, S1> Y(a);
+    Y.K = SweepConst{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse, a.inv_dt2_s1};
     const int strip = gw % a.nstrips, seg = gw / a.nstrips;
     Y.lane = lane;
     Y.b = b;
@@ -582,25 +582,42 @@ __global__ void __launch_bounds__(128) k_ysweep(const StepArgs a) {
 
 // ------------------------------------------------------------------ launchers
 // the ring needs more than the default 48 KB of dynamic shared memory per block
-// the kernel variant for the grid's metric (spherical or not) and friction (on or off)
-#define CLIFFS_VARIANT(K, sph, fric) \
-    ((sph) ? ((fric) ? K<true, true> : K<true, false>) : ((fric) ? K<false, true> : K<false, false>))
-#define CLIFFS_VARIANT3(K, sph, fric, yf) \
-    ((yf) ? CLIFFS_VARIANT2(K, sph, fric, true) : CLIFFS_VARIANT2(K, sph, fric, false))
-#define CLIFFS_VARIANT2(K, sph, fric, yf) \
-    ((sph) ? ((fric) ? K<true, true, yf> : K<true, false, yf>) : ((fric) ? K<false, true, yf> : K<false, false, yf>))
+// Kernel variants, indexed by the grid's metric (spherical: +1), friction (on: +2), sweep
+// order of the step (y first: +4) and solver (eq. (solver1): +8 for the fused step, +4 for
+// the others).
+#define CLIFFS_V2(K, ...) (const void*)K<false, false, __VA_ARGS__>, (const void*)K<true, false, __VA_ARGS__>, \
+                          (const void*)K<false, true, __VA_ARGS__>, (const void*)K<true, true, __VA_ARGS__>
+
+static const void* fused_kernel(bool sph, bool fric, bool yf, bool s1) {
+    static const void* const t[16] = {CLIFFS_V2(k_step_fused, false, false), CLIFFS_V2(k_step_fused, true, false),
+                                      CLIFFS_V2(k_step_fused, false, true), CLIFFS_V2(k_step_fused, true, true)};
+    return t[(sph ? 1 : 0) + (fric ? 2 : 0) + (yf ? 4 : 0) + (s1 ? 8 : 0)];
+}
+static const void* batch_kernel(bool sph, bool fric, bool s1) {
+    static const void* const t[8] = {CLIFFS_V2(k_batch, false), CLIFFS_V2(k_batch, true)};
+    return t[(sph ? 1 : 0) + (fric ? 2 : 0) + (s1 ? 4 : 0)];
+}
+static const void* xsweep_kernel(bool sph, bool fric, bool s1) {
+    static const void* const t[8] = {CLIFFS_V2(k_xsweep, false), CLIFFS_V2(k_xsweep, true)};
+    return t[(sph ? 1 : 0) + (fric ? 2 : 0) + (s1 ? 4 : 0)];
+}
+static const void* ysweep_kernel(bool sph, bool fric, bool s1) {
+    static const void* const t[8] = {CLIFFS_V2(k_ysweep, false), CLIFFS_V2(k_ysweep, true)};
+    return t[(sph ? 1 : 0) + (fric ? 2 : 0) + (s1 ? 4 : 0)];
+}
+
+static bool solver1(const StepArgs& a) { return a.inv_dt2_s1 > 0.f; }
 
 static cudaError_t fused_smem_optin() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
         done = cudaSuccess;
+        for (int v = 0; v < 16 && done == cudaSuccess; ++v)
+            done = cudaFuncSetAttribute(fused_kernel(v & 1, v & 2, v & 4, v & 8),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
         for (int v = 0; v < 8 && done == cudaSuccess; ++v)
-            done = cudaFuncSetAttribute(CLIFFS_VARIANT3(k_step_fused, v & 1, v & 2, v & 4),
+            done = cudaFuncSetAttribute(batch_kernel(v & 1, v & 2, v & 4),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        for (int v = 0; v < 4 && done == cudaSuccess; ++v) {
-            done = cudaFuncSetAttribute(CLIFFS_VARIANT(k_batch, v & 1, v & 2),
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        }
     }
     return done;
 }
@@ -608,10 +625,12 @@ static cudaError_t fused_smem_optin() {
 cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s) {
     const cudaError_t e = fused_smem_optin();
     if (e != cudaSuccess) return e;
-    const int nw = a.nitems;
-    const dim3 grid((nw + FUSED_WARPS - 1) / FUSED_WARPS, batch);
-    CLIFFS_VARIANT3(k_step_fused, a.sph, a.dt_gn2 > 0.f, a.yfirst != 0)<<<grid, FUSED_WARPS * 32, FUSED_SMEM, s>>>(m, a);
-    return cudaGetLastError();
+    const dim3 grid((a.nitems + FUSED_WARPS - 1) / FUSED_WARPS, batch);
+    StepMaps mm = m;
+    StepArgs aa = a;
+    void* args[] = {&mm, &aa};
+    return cudaLaunchKernel(fused_kernel(a.sph, a.dt_gn2 > 0.f, a.yfirst != 0, solver1(a)), grid,
+                            dim3(FUSED_WARPS * 32), args, FUSED_SMEM, s);
 }
 
 cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s) {
@@ -627,39 +646,43 @@ cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, CLIFFS_VARIANT(k_batch, a.sph, a.dt_gn2 > 0.f), mm, a, b);
+    StepMaps2 m2 = mm;
+    StepArgs aa = a;
+    BatchArgs bb = b;
+    void* args[] = {&m2, &aa, &bb};
+    return cudaLaunchKernelExC(&cfg, batch_kernel(a.sph, a.dt_gn2 > 0.f, solver1(a)), args);
 }
 
 int batch_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT(k_batch, sph, true), FUSED_WARPS * 32,
-                                                  FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(sph, true, false), FUSED_WARPS * 32, FUSED_SMEM);
     return nb;
 }
 
 int fused_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, CLIFFS_VARIANT3(k_step_fused, sph, true, false),
-                                                  FUSED_WARPS * 32, FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_kernel(sph, true, false, false), FUSED_WARPS * 32,
+                                                  FUSED_SMEM);
     return nb;
 }
 
 int fused_warps_per_block() { return FUSED_WARPS; }
 
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s) {
-    const int nw = a.nstrips * a.ny;
-    const dim3 grid((nw + 3) / 4, batch);
-    CLIFFS_VARIANT(k_xsweep, a.sph, a.dt_gn2 > 0.f)<<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    const dim3 grid((a.nstrips * a.ny + 3) / 4, batch);
+    StepArgs aa = a;
+    void* args[] = {&aa};
+    return cudaLaunchKernel(xsweep_kernel(a.sph, a.dt_gn2 > 0.f, solver1(a)), grid, dim3(128), args, 0, s);
 }
 
 cudaError_t launch_ysweep(const StepArgs& a, int batch, cudaStream_t s) {
     const int nw = a.nstrips * a.nseg;
     const dim3 grid((nw + 3) / 4, batch);
-    CLIFFS_VARIANT(k_ysweep, a.sph, a.dt_gn2 > 0.f)<<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    StepArgs aa = a;
+    void* args[] = {&aa};
+    return cudaLaunchKernel(ysweep_kernel(a.sph, a.dt_gn2 > 0.f, solver1(a)), grid, dim3(128), args, 0, s);
 }
 
 }  // namespace cliffs

@@ -41,6 +41,7 @@ struct StepArgs {
     int transverse;
     int sph;                         // geographic grid: x metric scaled per row
     int yfirst;                      // this step sweeps y, then x (alternating order)
+    float inv_dt2_s1;                // 1/dt^2 with eq. (solver1), 0 with eq. (solver2)
     long long wait_cycles;           // limit of every mbarrier wait (clock cycles)
     unsigned tx_pad;                 // extra bytes each ring slot expects (fault injection; 0)
 };

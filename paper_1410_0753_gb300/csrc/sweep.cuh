@@ -43,6 +43,7 @@ struct SweepConst {
     float half_dt;    // dt / 2
     float dt_gn2;     // dt * g * Manning n^2 (0 disables friction)
     int   transverse; // eq. (pq3) on/off
+    float inv_dt2;    // 1 / dt^2 (eq. (solver1): 1/(dx_{j-1}+dx_j) = k2 / dt^2)
 };
 
 // ------------------------------------------------------------------ packed FP32x2
@@ -122,16 +123,25 @@ __device__ __forceinline__ void ghost_right(float w, float c, float inv, float& 
 //   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep (SRC).
 // Friction: alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3) at time level n on both p and q,
 // clamped so that |alpha dt| <= |w|.
-template <bool SRC, bool FRIC>
+// With S1, eq. (solver1): the first-order term is dt Q(j+1, j-1) over dx_{j-1} + dx_j, given
+// as the flux F1 between the two neighbours (per unit length) instead of the mean of L and R.
+template <bool SRC, bool FRIC, bool S1 = false>
 __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float2 d, float2 c,
                                              const Flux2& L, const Flux2& R, float2 k2, float2 sdt,
                                              const SweepConst& K,
-                                             float2& e2, float2& w2, float2& t2) {
+                                             float2& e2, float2& w2, float2& t2, const Flux2* F1 = nullptr) {
     const float2 lp = add2(w, c);
     const float2 lq = sub2(w, c);
     const float2 nh = v2(-K.half_dt);
-    float2 dp = fma2(mul2(lp, k2), sub2(R.p, L.p), mul2(nh, add2(L.p, R.p)));
-    float2 dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(nh, add2(L.q, R.q)));
+    const float2 ndt = v2(-2.f * K.half_dt);
+    float2 dp, dq;
+    if (S1) {
+        dp = fma2(mul2(lp, k2), sub2(R.p, L.p), mul2(ndt, F1->p));
+        dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(ndt, F1->q));
+    } else {
+        dp = fma2(mul2(lp, k2), sub2(R.p, L.p), mul2(nh, add2(L.p, R.p)));
+        dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(nh, add2(L.q, R.q)));
+    }
     if (FRIC) {
         const float2 h = add2(e, d);
         const float2 s2 = fma2(w, w, mul2(t, t));
@@ -152,7 +162,8 @@ __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float
     const float2 dc = mul2(v2(0.25f), sub2(dp, dq));
     w2 = add2(w, du);
     e2 = fma2(mul2(dc, fma2(v2(2.f), c, dc)), v2(INV_GRAV), e);
-    const float2 tn = fma2(mul2(w, k2), sub2(R.t, L.t), fma2(nh, add2(L.t, R.t), t));
+    const float2 tn = S1 ? fma2(mul2(w, k2), sub2(R.t, L.t), fma2(ndt, F1->t, t))
+                         : fma2(mul2(w, k2), sub2(R.t, L.t), fma2(nh, add2(L.t, R.t), t));
     t2 = K.transverse ? tn : t;
 }
 
@@ -185,7 +196,7 @@ struct XMet2 { float2 inv_l, inv_r, k2; };   // per pair: 1/dx_{j-1}, 1/dx_j, dt
 // and B = 2l + 1 (.y). Neighbours across lanes come by shuffles. On return (E, W, T) hold
 // the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each side
 // lack their 3-node dependency radius). W is the velocity along the row, T across it.
-template <bool FRIC>
+template <bool FRIC, bool S1 = false>
 __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
                                         const SweepConst& K, int lane) {
     const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
@@ -232,18 +243,35 @@ __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 
     FL.p = make_float2(__shfl_up_sync(FULL, FR.p.y, 1), FR.p.x);
     FL.q = make_float2(__shfl_up_sync(FULL, FR.q.y, 1), FR.q.x);
     FL.t = make_float2(__shfl_up_sync(FULL, FR.t.y, 1), FR.t.x);
+    bool wetL = true, wetR = true;
     if (!allwet) {
         // (c): walls between wet and dry nodes
         const unsigned w1A = __ballot_sync(FULL, wA), w1B = __ballot_sync(FULL, wB);
-        const bool wetL = lane > 0 && ((w1B >> (lane - 1)) & 1u);
-        const bool wetR = lane < 31 && ((w1A >> (lane + 1)) & 1u);
+        wetL = lane > 0 && ((w1B >> (lane - 1)) & 1u);
+        wetR = lane < 31 && ((w1A >> (lane + 1)) & 1u);
         if (!wetL) ghost_left(W.x, C.x, m.inv_l.x, FL.p.x, FL.q.x, FL.t.x);
         if (!wB) ghost_right(W.x, C.x, m.inv_r.x, FR.p.x, FR.q.x, FR.t.x);
         if (!wA) ghost_left(W.y, C.y, m.inv_l.y, FL.p.y, FL.q.y, FL.t.y);
         if (!wetR) ghost_right(W.y, C.y, m.inv_r.y, FR.p.y, FR.q.y, FR.t.y);
     }
+    Flux2 F1;
+    if (S1) {
+        // eq. (solver1): flux between the two neighbours of each node, mirror ghosts for dry ones
+        float2 le = make_float2(__shfl_up_sync(FULL, E.y, 1), E.x), lw = make_float2(__shfl_up_sync(FULL, W.y, 1), W.x);
+        float2 lt = make_float2(__shfl_up_sync(FULL, T.y, 1), T.x), ld = make_float2(__shfl_up_sync(FULL, D.y, 1), D.x);
+        float2 lc = make_float2(__shfl_up_sync(FULL, C.y, 1), C.x);
+        float2 re = make_float2(E.y, eR), rw = make_float2(W.y, wR), rt = make_float2(T.y, tR);
+        float2 rd = make_float2(D.y, dR), rc = make_float2(C.y, cR);
+        if (!allwet) {
+            if (!wetL) { le.x = E.x; lw.x = -W.x; lt.x = T.x; ld.x = D.x; lc.x = C.x; }
+            if (!wB) { re.x = E.x; rw.x = -W.x; rt.x = T.x; rd.x = D.x; rc.x = C.x; }
+            if (!wA) { le.y = E.y; lw.y = -W.y; lt.y = T.y; ld.y = D.y; lc.y = C.y; }
+            if (!wetR) { re.y = E.y; rw.y = -W.y; rt.y = T.y; rd.y = D.y; rc.y = C.y; }
+        }
+        F1 = iface2(le, lw, lt, ld, lc, re, rw, rt, rd, rc, mul2(m.k2, v2(K.inv_dt2)));
+    }
     float2 E2, W2, T2;
-    node_update2<false, FRIC>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2);
+    node_update2<false, FRIC, S1>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2, &F1);
     if (!allwet) {
         if (!wA) { E2.x = E.x; W2.x = W.x; T2.x = T.x; }
         if (!wB) { E2.y = E.y; W2.y = W.y; T2.y = T.y; }
@@ -283,6 +311,7 @@ struct YMarch2 {
     float2 e3, w3, t3, d3;    // row k-3 after (d)
     int dir3A, dir3B;
     float2 h4, w4;            // row k-4 after (d): height, velocity
+    float2 pe, pw, pt, pd, pc;   // row k-3 after (b) (eq. (solver1) only)
 
     __device__ __forceinline__ void init() {
         for (int i = 0; i < 2; ++i) {
@@ -297,12 +326,29 @@ struct YMarch2 {
         d3 = v2(OUTSIDE_D);
         dir3A = dir3B = 0;
         h4 = w4 = v2(0.f);
+        pe = pw = pt = pc = v2(0.f);
+        pd = v2(OUTSIDE_D);
+    }
+
+    // eq. (solver1): flux between rows k-3 and k-1 around row k-2 (P), with mirror ghosts
+    // of P for a neighbour row that is dry after (b)
+    __device__ __forceinline__ Flux2 f1(const YRow& P, const YRow& B1, bool open, float k2,
+                                        const SweepConst& K) const {
+        float2 le = pe, lw = pw, lt = pt, ld = pd, lc = pc;
+        float2 re = B1.e, rw = B1.w, rt = B1.t, rd = B1.d, rc = B1.c;
+        if (!open) {
+            if (!f3A) { le.x = P.e.x; lw.x = -P.w.x; lt.x = P.t.x; ld.x = P.d.x; lc.x = P.c.x; }
+            if (!f3B) { le.y = P.e.y; lw.y = -P.w.y; lt.y = P.t.y; ld.y = P.d.y; lc.y = P.c.y; }
+            if (!B1.wA) { re.x = P.e.x; rw.x = -P.w.x; rt.x = P.t.x; rd.x = P.d.x; rc.x = P.c.x; }
+            if (!B1.wB) { re.y = P.e.y; rw.y = -P.w.y; rt.y = P.t.y; rd.y = P.d.y; rc.y = P.c.y; }
+        }
+        return iface2(le, lw, lt, ld, lc, re, rw, rt, rd, rc, v2(k2 * K.inv_dt2));
     }
 
     // m2: metric of row k-2 (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R).
     // emit(e, w, t, d) receives the finished row k-3; o0A/o0B: the incoming row's wet marks.
     // careA/careB: whether this lane's columns are emitted; the others may compute anything.
-    template <int PH, bool SRC, bool FRIC, class Emit>
+    template <int PH, bool SRC, bool FRIC, bool S1, class Emit>
     __device__ __forceinline__ void push(float2 E0, float2 W0, float2 T0, float2 D0, bool o0A, bool o0B,
                                          float4 m2, const SweepConst& K, bool careA, bool careB,
                                          Emit&& emit) {
@@ -321,7 +367,9 @@ struct YMarch2 {
             emit(e3, w3, t3, d3);
             h4 = add2(e3, d3);
             w4 = w3;
-            node_update2<SRC, FRIC>(P.e, P.w, P.t, P.d, P.c, F3, F2, v2(m2.z), v2(m2.w), K, e3, w3, t3);
+            Flux2 F1;
+            if (S1) F1 = f1(P, B1, true, m2.z, K);
+            node_update2<SRC, FRIC, S1>(P.e, P.w, P.t, P.d, P.c, F3, F2, v2(m2.z), v2(m2.w), K, e3, w3, t3, &F1);
         } else {
             // (a)/(b) on row k-1 (input held in B1), neighbours row k-2 (P) and row k (new)
             B1.wA = B1.oA;
@@ -352,7 +400,9 @@ struct YMarch2 {
             if (P.wB && !f3B) ghost_left(P.w.y, P.c.y, m2.x, L.p.y, L.q.y, L.t.y);
             if (P.wB && !B1.wB) ghost_right(P.w.y, P.c.y, m2.y, R.p.y, R.q.y, R.t.y);
             float2 ne, nw, nt;
-            node_update2<SRC, FRIC>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt);
+            Flux2 F1;
+            if (S1) F1 = f1(P, B1, false, m2.z, K);
+            node_update2<SRC, FRIC, S1>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt, &F1);
             if (!P.wA) { ne.x = P.e.x; nw.x = P.w.x; nt.x = P.t.x; }
             if (!P.wB) { ne.y = P.e.y; nw.y = P.w.y; nt.y = P.t.y; }
             // (e) on row k-3, against row k-4 (h4, w4) or row k-2 (ne, nw)
@@ -364,6 +414,7 @@ struct YMarch2 {
             w4 = w3;
             e3 = ne; w3 = nw; t3 = nt;
         }
+        if (S1) { pe = P.e; pw = P.w; pt = P.t; pd = P.d; pc = P.c; }
         d3 = P.d;
         dir3A = P.dA; dir3B = P.dB;
         f3A = P.wA; f3B = P.wB;

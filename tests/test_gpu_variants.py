@@ -78,3 +78,57 @@ def test_alternating_order_keeps_1d_equal_2d():
     assert e.value.code == ERR_ARG
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("case", ["beach", "spherical_alternate", "line_x", "line_y"])
+def test_solver1_against_oracle(case):
+    """eq. (solver1) (the original VTCS-2 first-order term over the double interval) on wet/dry
+    and spherical grids, with the alternating order, and on 1D lines along x and along y."""
+    alt = 0
+    if case == "beach":
+        w = workloads.beach_200(120, 96, steps=240)
+    elif case == "spherical_alternate":
+        w = workloads.spherical_coast(220, 190, steps=160)
+        w.nests = []
+        alt = 1
+    else:
+        b = workloads.beach_200(200, 3, steps=300)
+        w = b
+        row = 1
+        w.depth = b.depth[row:row + 1]
+        w.eta0 = b.eta0[row:row + 1]
+        w.y = b.y[row:row + 1]
+        w.ny = 1
+        w.gauges = np.array([(ix, 0) for ix in (40, 100, 150, 180)], dtype=np.int32)
+        if case == "line_y":
+            w.depth, w.eta0 = w.depth.T.copy(), w.eta0.T.copy()
+            w.x, w.y = w.y, b.x
+            w.nx, w.ny = 1, 200
+            w.gauges = w.gauges[:, ::-1].copy()
+    n = w.steps
+    g, o, d64 = _run_both(w, n, solver=1, alternate=alt)
+    _assert_gauges("solver1_" + case, g["gauges"], o["gauges"])
+    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], g["depth"], d64, w.h_min)
+    assert np.array_equal(wet32 & ~near, wet64 & ~near)
+    amp = np.abs(w.eta0).max()
+    assert np.abs(g["eta"] - o["eta"])[wet64].max() <= 1e-4 * amp
+    g0 = P.gpu_run(w, n, alternate=alt)                 # solver2 gives a different answer
+    assert not np.array_equal(g0["eta"], g["eta"])
+    g["grid"].close()
+    g0["grid"].close()
+
+
+def test_solver1_persistent_equals_per_step():
+    w = workloads.ensemble_512(batch=4, nx=120, ny=100, dmin=20, dmax=60)
+    runs = []
+    for pers in (False, True):
+        g = CliffsGrid.from_workload(w, solver=1)
+        g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+        g.set_initial(w.eta0.astype(np.float32))
+        g.set_durations(w.durations)
+        g.step(int(w.durations.max()), persistent=pers)
+        runs.append([g.state(b) for b in range(w.batch)] + [g.gauges(b) for b in range(w.batch)])
+        g.close()
+    for x, y in zip(runs[0], runs[1]):
+        for p, q in zip(x if isinstance(x, tuple) else (x,), y if isinstance(y, tuple) else (y,)):
+            assert np.array_equal(p, q)
