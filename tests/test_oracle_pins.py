@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import workloads
 
 G = 9.81
 
@@ -553,3 +554,20 @@ def test_maxwave_ignores_dry_cells():
     fmax = np.finfo(np.float32).max
     assert np.all(r["eta_max"][d < -1] == -fmax) and np.all(r["speed_max"][d < -1] == 0)
     assert np.all(r["eta_max"][d > 0] >= eta0[d > 0])
+
+
+# ----------------------------------------------------------------------------------------
+# Run-up of a non-breaking solitary wave on a plane beach (section "Examples", "Runup on a
+# sloping beach"; the Synolakis 1987 experiment): the run-up law R/d = 2.831 sqrt(cot beta)
+# (H/d)^(5/4) holds to about 10 % for H/d = 0.0185 on the 1:19.85 slope. This exercises the
+# inundation algorithm (a)-(e) over a whole run-up and run-down.
+
+def test_runup_of_a_solitary_wave_follows_the_runup_law():
+    w = workloads.runup_1d()
+    p = oracle.params_from(w)
+    r = oracle.run(p, w.x, w.y, w.depth.astype(np.float64), w.eta0, w.u0, None, nsteps=w.steps, maxout=1)
+    land = w.depth[0] < 0
+    em = r["eta_max"][0][land]
+    R = em[em > -1e30].max()
+    law = w.extra["runup_law"]
+    assert abs(R / law - 1.0) <= 0.10, (R, law)

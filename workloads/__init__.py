@@ -333,10 +333,56 @@ def inversion_1024(nx=1024, ny=1024, steps=2000, seed_offset=5):
     return w
 
 
+# --------------------------------------------------------------------------- run-up (E1)
+
+def runup_1d(H_over_d=0.0185, d=1.0, slope=19.85, dt=0.03, steps=2000):
+    """Solitary-wave run-up on a plane beach (section "Examples", "Runup on a sloping beach"),
+    reconstructed: the paper's grid and initial-condition files are not available. A 1D
+    Cartesian line from deep water at depth d to dry land, slope 1:slope from the toe up
+    through the still shoreline; node spacing d in the deep part, narrowing linearly to
+    0.1 d twenty depths before the toe and 0.1 d from there over the beach. Initial wave
+    eta = H sech^2(gamma (x - X1)), gamma = sqrt(3H/(4 d^3)), centred half a wavelength
+    (arccosh(sqrt 20)/gamma) seaward of the toe, moving shoreward with u = eta sqrt(g/d).
+    Parameters of the paper's table: h_min 0.003 m, no friction, inundation on, dt 0.03 s,
+    2000 steps; max-wave every step. The wave travels toward +x; the still shoreline is at
+    x = 0. The beach is used unfiltered: it has no depth jumps, and raising depths below
+    min_depth would flatten the swash zone."""
+    H = H_over_d * d
+    gamma = math.sqrt(3.0 * H / (4.0 * d ** 3))
+    half = math.acosh(math.sqrt(20.0)) / gamma
+    x_toe = -slope * d
+    x1 = x_toe - half
+    x_deep = x1 - 2.0 * half
+    x_fine = x_toe - 20.0 * d
+    x_land = 3.0 * d
+    xs = [x_deep]
+    while xs[-1] < x_land:
+        xc = xs[-1]
+        if xc < x_fine:
+            f = min(1.0, (x_fine - xc) / (x_fine - x_deep))
+            dx = d * (0.1 + 0.9 * f)
+        else:
+            dx = 0.1 * d
+        xs.append(xc + dx)
+    x = np.array(xs)
+    depth = np.where(x <= x_toe, d, -x / slope)
+    eta0 = H / np.cosh(gamma * (x - x1)) ** 2
+    eta0 = np.where(depth > 0.0, eta0, 0.0)
+    u0 = eta0 * math.sqrt(G / d)
+    n = len(x)
+    w = Workload("runup_1d_%.4f" % H_over_d, n, 1, 1, f32(x), f32(np.zeros(1)), f32(depth[None, :]),
+                 f32(eta0[None, :]), dt, steps, u0=f32(u0[None, :]), h_min=0.003, manning_n2=0.0,
+                 maxout=1, gout=steps + 1, bndout=steps + 1)
+    w.extra.update(dict(H=H, d=d, slope=slope,
+                        runup_law=2.831 * math.sqrt(slope) * H_over_d ** 1.25 * d))
+    return w
+
+
 WORKLOADS = {
     "beach_200": beach_200,
     "spherical_coast": spherical_coast,
     "shelf_islands": shelf_islands,
     "ensemble_512": ensemble_512,
     "inversion_1024": inversion_1024,
+    "runup_1d": runup_1d,
 }
