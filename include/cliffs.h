@@ -120,6 +120,28 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
  * (its state, max-wave and records then stay as they were). Default: unlimited. */
 int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
 
+/* Boundary input (section "Running Options", "The input to the computations": one series
+ * per edge, vals(tim, uvq, pnt) of (u, v, eta) at times time(tim); parameter-file fields 5
+ * and 13). edge: 0 W, 1 E, 2 S, 3 N; times[nt] in seconds, increasing; vals[nt][3][np] with
+ * np = ny for W and E, nx for S and N (host or device arrays, copied). A 1D grid along x
+ * takes W and E (one node each), along y S and N. The paper does not say how the input enters
+ * the scheme; the reading taken here: before each step the edge nodes take the input's
+ * values at the current model time, linearly interpolated between records (the first or last
+ * record outside their span), edges in the order W, E, S, N (S and N own the corners); an
+ * edge without input stays a reflecting wall. nt = 0 removes the edge's input. batch == 1
+ * only; a grid with input runs through cliffs_step_n (not the persistent run or the
+ * adjoint). Errors: ERR_ARG (edge, sizes, times not increasing, batch > 1). */
+int cliffs_set_boundary_input(cliffs_grid* g, int edge, const double* times, int64_t nt, const double* vals);
+
+/* Model clock under boundary input (parameter-file fields 5, cuke, and 13). The run starts at
+ * t_start: the first record time at which |eta| exceeds cuke anywhere on an input edge, or,
+ * with cuke <= 0 (or no such record), the earliest record time. The state after k steps since
+ * set_initial is at t_start + k dt, and the input for the step from it is taken at that time.
+ * With stop_at_end != 0, cliffs_step_n ends early (returning CLIFFS_OK) before a step whose
+ * result would lie past the end of the shortest record; cliffs_steps_done tells how far it
+ * went. Writes t_start when the pointer is not NULL. Errors: ERR_STATE without input. */
+int cliffs_set_boundary_clock(cliffs_grid* g, double cuke, int stop_at_end, double* t_start);
+
 /* Advance n time steps. One step is an x-sweep over every row then a y-sweep over every
  * column (order alternates when cfg.alternate), each with the inundation steps (a)-(e) and
  * eq. (solver2); then max-wave (every maxout steps), gauges (every gout) and boundary

@@ -11,6 +11,7 @@ through ctypes:
 * ``sweep_line``    - one 1D sweep of one line with the record of steps (a)-(e)
 * ``run``           - time steps with max-wave, gauges and enclosed-grid boundary series
 * ``run_tlm``       - the tangent-linear model of ``run`` (branches frozen on the primal)
+* ``run_forced``    - ``run`` under boundary input on the domain edges
 
 Parity status of each part (what pins it) is listed in the tests under ``tests/test_oracle_*``.
 The spherical metric (reading 7) is pinned only by its Cartesian limit and by propagation
@@ -86,6 +87,9 @@ def _bind(L):
                                  C.c_long, C.c_long, C.c_int,
                                  C.c_int, C.c_int, ip, dp, dp, C.c_long, lp]
     L.oracle_run_tlm.restype = C.c_int
+    L.oracle_run_forced.argtypes = [P(OracleParams), dp, dp, dp, dp, dp, dp, C.c_long, C.c_long, C.c_double,
+                                    P(dp), lp, P(dp), C.c_int, C.c_int, ip, dp, C.c_long, lp]
+    L.oracle_run_forced.restype = C.c_int
     return L
 
 
@@ -217,6 +221,46 @@ def run(p: OracleParams, x, y, depth, eta, u=None, v=None, nsteps=0, step0=0,
             series.append(edges)
         out["boundary"] = series
     return out
+
+
+def run_forced(p: OracleParams, x, y, depth, eta, boundary, u=None, v=None, nsteps=0, step0=0,
+               t0=0.0, gout=1, gauges=None):
+    """A run under boundary input: ``boundary`` maps an edge (0 W, 1 E, 2 S, 3 N) to
+    (times[nt], vals[nt][3][np]) with vals ordered (u, v, eta); before each step the edge
+    nodes take the input at model time t0 + (k - step0) dt. Returns the final state and the
+    gauge records [nrec][G][3]."""
+    L = lib()
+    ny, nx = depth.shape
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    depth = np.ascontiguousarray(depth, np.float64)
+    eta = np.array(eta, np.float64).reshape(ny, nx)
+    u = np.zeros_like(eta) if u is None else np.array(u, np.float64).reshape(ny, nx)
+    v = np.zeros_like(eta) if v is None else np.array(v, np.float64).reshape(ny, nx)
+    keep = []
+    tp = (C.POINTER(C.c_double) * 4)()
+    vp = (C.POINTER(C.c_double) * 4)()
+    nt = (C.c_long * 4)()
+    for e in range(4):
+        if e in boundary:
+            t, vals = boundary[e]
+            t = np.ascontiguousarray(t, np.float64)
+            vals = np.ascontiguousarray(vals, np.float64)
+            npnt = ny if e < 2 else nx
+            assert vals.shape == (len(t), 3, npnt), (e, vals.shape)
+            keep += [t, vals]
+            tp[e], vp[e], nt[e] = _d(t), _d(vals), len(t)
+    G = 0 if gauges is None else len(gauges)
+    gix = np.ascontiguousarray(np.asarray(gauges, np.int32).reshape(-1)) if G else None
+    cap = nsteps + 1
+    grec = np.zeros((cap, max(G, 1), 3))
+    ng = C.c_long(0)
+    rc = L.oracle_run_forced(C.byref(p), _d(x), _d(y), _d(depth), _d(eta), _d(u), _d(v), int(step0),
+                             int(nsteps), float(t0), tp, nt, vp, int(gout), G, _i(gix), _d(grec), cap,
+                             C.byref(ng))
+    if rc != 0:
+        raise ValueError("oracle_run_forced failed (%d)" % rc)
+    return dict(eta=eta, u=u, v=v, gauges=grec[: ng.value, :G] if G else None)
 
 
 def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv=None,

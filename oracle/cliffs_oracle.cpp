@@ -580,6 +580,62 @@ int oracle_run(const oracle_params* p, const double* x, const double* y, const d
     return 0;
 }
 
+// Boundary input (section "Running Options", "The input to the computations"): time series
+// of (u, v, eta) at the nodes of the W, E, S and N edges, vals[nt][3][np] at times[nt]. The
+// paper does not say how the input enters the scheme; the reading taken here: before each
+// step, the edge nodes take the input's values at the current model time, linearly
+// interpolated between records (the first or last record outside their span); the edges
+// are set in the order W, E, S, N, so S and N own the corners. An edge with no series is
+// left to the scheme (a reflecting wall).
+static void impose_edge(const Params& P, double* eta, double* u, double* v, int edge,
+                        const double* times, long nt, const double* vals, double t) {
+    const int np = (edge < 2) ? P.ny : P.nx;
+    long k = 0;
+    double w = 0.0;
+    if (t <= times[0] || nt == 1) { k = 0; w = 0.0; }
+    else if (t >= times[nt - 1]) { k = nt - 1; w = 0.0; }
+    else {
+        while (k + 1 < nt - 1 && times[k + 1] <= t) ++k;
+        w = (t - times[k]) / (times[k + 1] - times[k]);
+    }
+    for (int q = 0; q < np; ++q) {
+        const int ix = (edge == 0) ? 0 : (edge == 1) ? P.nx - 1 : q;
+        const int iy = (edge == 2) ? 0 : (edge == 3) ? P.ny - 1 : q;
+        const size_t c = (size_t)iy * P.nx + ix;
+        double val[3];
+        for (int f = 0; f < 3; ++f) {
+            const double a = vals[(k * 3 + f) * np + q];
+            const double b = (w > 0.0) ? vals[((k + 1) * 3 + f) * np + q] : a;
+            val[f] = (1.0 - w) * a + w * b;
+        }
+        u[c] = val[0]; v[c] = val[1]; eta[c] = val[2];
+    }
+}
+
+// A run under boundary input from model time t0: before step k the edges are set at time
+// t0 + (k - step0) dt. Gauges (eta, u, v) are recorded as in oracle_run.
+int oracle_run_forced(const oracle_params* p, const double* x, const double* y, const double* d,
+                      double* eta, double* u, double* v, long step0, long nsteps, double t0,
+                      const double* const* times, const long* nt, const double* const* vals,
+                      int gout, int n_gauges, const int* gauge_ixiy, double* gauge_rec, long gauge_cap,
+                      long* n_gauge_rec) {
+    Params P = to_params(p);
+    if ((P.nx > 1 && P.nx < 3) || (P.ny > 1 && P.ny < 3)) return -1;
+    Grid Gd{P, x, y, d};
+    long zero1 = 0, zero2 = 0;
+    Outputs O{0, nullptr, nullptr, gout, n_gauges, gauge_ixiy, gauge_rec, gauge_cap,
+              n_gauge_rec ? n_gauge_rec : &zero1, 0, 0, nullptr, nullptr, 0, &zero2, {}, {}, {}, {}};
+    record<double>(Gd, step0, eta, u, v, &O);
+    for (long k = step0; k < step0 + nsteps; ++k) {
+        const double t = t0 + (double)(k - step0) * P.dt;
+        for (int e = 0; e < 4; ++e)
+            if (times[e] && nt[e] > 0) impose_edge(P, eta, u, v, e, times[e], nt[e], vals[e], t);
+        step<double>(Gd, k, eta, u, v);
+        record<double>(Gd, k + 1, eta, u, v, &O);
+    }
+    return 0;
+}
+
 // Tangent-linear run: the primal (eta,u,v) and a tangent (deta,du,dv) advance together;
 // every branch is decided on the primal. Gauge tangents of eta are written to
 // gauge_tan[nrec][G] at the steps where gauges are recorded.

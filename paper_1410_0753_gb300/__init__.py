@@ -27,7 +27,7 @@ __all__ = [
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
-    "EXPORTED",
+    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -40,6 +40,7 @@ EXPORTED = [
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
+    "cliffs_set_boundary_input", "cliffs_set_boundary_clock",
 ]
 
 
@@ -86,6 +87,8 @@ def lib():
             "cliffs_step_n": ([vp, C.c_int64], C.c_int),
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
+            "cliffs_set_boundary_input": ([vp, C.c_int, vp, C.c_int64, vp], C.c_int),
+            "cliffs_set_boundary_clock": ([vp, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
             "cliffs_steps_done": ([vp, i64p], C.c_int),
             "cliffs_read_gauges": ([vp, C.c_int, vp, i64p], C.c_int),
             "cliffs_read_maxwave": ([vp, C.c_int, vp, vp], C.c_int),
@@ -197,6 +200,23 @@ def cliffs_adjoint_n(g, n, checkpoint_every, dL_dgauges, out):
     gauge-eta adjoint seed ``dL_dgauges`` ([n // gout + 1][G] float32, or None)."""
     ps, ks = _ptr(dL_dgauges, np.float32)
     _check(lib().cliffs_adjoint_n(g, int(n), int(checkpoint_every), ps, _out_ptr(out)))
+
+
+def cliffs_set_boundary_input(g, edge, times, vals):
+    """Boundary input of one edge (0 W, 1 E, 2 S, 3 N): times[nt], vals[nt][3][np] (u, v, eta);
+    times=None removes it."""
+    if times is None:
+        _check(lib().cliffs_set_boundary_input(g, int(edge), None, 0, None))
+        return
+    pt, kt = _ptr(times, np.float64)
+    pv, kv = _ptr(vals, np.float64)
+    _check(lib().cliffs_set_boundary_input(g, int(edge), pt, len(times), pv))
+
+
+def cliffs_set_boundary_clock(g, cuke=0.0, stop_at_end=0) -> float:
+    t = C.c_double()
+    _check(lib().cliffs_set_boundary_clock(g, float(cuke), int(stop_at_end), C.byref(t)))
+    return t.value
 
 
 def cliffs_read_gauges(g, scenario, out=None) -> int:
@@ -364,6 +384,12 @@ class CliffsGrid:
 
     def autotune(self, trials=3):
         return cliffs_autotune(self.h, trials)
+
+    def set_boundary_input(self, edge, times, vals):
+        cliffs_set_boundary_input(self.h, edge, times, vals)
+
+    def set_boundary_clock(self, cuke=0.0, stop_at_end=False):
+        return cliffs_set_boundary_clock(self.h, cuke, int(stop_at_end))
 
     def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None):
         """Gradient with respect to the current free surface of a loss whose derivative with

@@ -193,6 +193,37 @@ __global__ void k_boundary(const float* nrec, int nnodes, const int* slot, const
 
 inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+// Boundary input for one step: per edge the series and the two records (k, k+1) to mix
+// with weight w.
+struct BndStep {
+    const double* vals[4];
+    int np[4];
+    long long k[4];
+    double w[4];
+};
+
+// Edge nodes take the input (u, v, eta); S and N own the corners when they have input.
+__global__ void k_bnd(float* eta, float* u, float* v, int pitch, int nx, int ny, BndStep b) {
+    const int e = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!b.vals[e] || q >= b.np[e]) return;
+    if (e < 2 && ((q == 0 && b.vals[2]) || (q == ny - 1 && b.vals[3])) && nx > 1 && ny > 1) return;
+    const int ix = (e == 0) ? 0 : (e == 1) ? nx - 1 : q;
+    const int iy = (e == 2) ? 0 : (e == 3) ? ny - 1 : q;
+    const int np = b.np[e];
+    const double* r0 = b.vals[e] + b.k[e] * 3 * np;
+    const double w = b.w[e];
+    double val[3];
+    for (int f = 0; f < 3; ++f) {
+        const double a = r0[f * np + q];
+        val[f] = (w > 0.0) ? (1.0 - w) * a + w * r0[(3 + f) * np + q] : a;
+    }
+    const size_t o = (size_t)iy * pitch + ix;
+    u[o] = (float)val[0];
+    v[o] = (float)val[1];
+    eta[o] = (float)val[2];
+}
+
 }  // namespace
 
 void cliffs::set_last_error(const char* msg) {
@@ -282,6 +313,13 @@ struct cliffs_grid {
     int* adj_gxy = nullptr;
     float* adj_seed = nullptr;
     long long adj_seed_cap = 0;
+    // boundary input: per edge (W, E, S, N) the record times (host) and (u, v, eta) series
+    // (device), the model clock and whether a run stops at the end of the records
+    std::vector<double> bnd_t[4];
+    double* bnd_v[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool bnd_any = false;
+    double t_start = 0.0;
+    bool bnd_stop = false;
 };
 
 namespace {
@@ -567,6 +605,7 @@ void free_grid(cliffs_grid* g) {
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
     cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
+    for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
     if (g->cap) cudaStreamDestroy(g->cap);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete g;
@@ -952,6 +991,56 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps) {
     return CLIFFS_OK;
 }
 
+int cliffs_set_boundary_input(cliffs_grid* g, int edge, const double* times, int64_t nt, const double* vals) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (edge < 0 || edge > 3) return set_err(CLIFFS_ERR_ARG, "edge %d out of range (0 W, 1 E, 2 S, 3 N)", edge);
+    if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "boundary input needs batch == 1");
+    if ((g->ny == 1 && edge >= 2) || (g->nx == 1 && edge < 2))
+        return set_err(CLIFFS_ERR_ARG, "edge %d runs along the 1D grid", edge);
+    if (nt < 0 || (nt > 0 && (!times || !vals))) return set_err(CLIFFS_ERR_ARG, "bad series");
+    cudaFree(g->bnd_v[edge]);
+    g->bnd_v[edge] = nullptr;
+    g->bnd_t[edge].clear();
+    if (nt > 0) {
+        std::vector<double> t(nt);
+        CK(cudaMemcpy(t.data(), times, sizeof(double) * nt, cudaMemcpyDefault));
+        for (int64_t i = 0; i + 1 < nt; ++i)
+            if (!(t[i + 1] > t[i])) return set_err(CLIFFS_ERR_ARG, "record times must increase");
+        const int np = edge < 2 ? g->ny : g->nx;
+        CK(cudaMalloc(&g->bnd_v[edge], sizeof(double) * 3 * np * nt));
+        CK(cudaMemcpy(g->bnd_v[edge], vals, sizeof(double) * 3 * np * nt, cudaMemcpyDefault));
+        g->bnd_t[edge] = t;
+    }
+    g->bnd_any = false;
+    for (int e = 0; e < 4; ++e) g->bnd_any |= !g->bnd_t[e].empty();
+    return CLIFFS_OK;
+}
+
+int cliffs_set_boundary_clock(cliffs_grid* g, double cuke, int stop_at_end, double* t_start) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->bnd_any) return set_err(CLIFFS_ERR_STATE, "no boundary input");
+    double t0 = 1e300, tc = 1e300;
+    for (int e = 0; e < 4; ++e) {
+        const std::vector<double>& T = g->bnd_t[e];
+        if (T.empty()) continue;
+        t0 = std::min(t0, T.front());
+        if (cuke > 0.0) {
+            const int np = e < 2 ? g->ny : g->nx;
+            std::vector<double> h((size_t)3 * np * T.size());
+            CK(cudaMemcpy(h.data(), g->bnd_v[e], sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+            for (size_t r = 0; r < T.size() && T[r] < tc; ++r)
+                for (int q = 0; q < np; ++q)
+                    if (std::fabs(h[(r * 3 + 2) * np + q]) > cuke) { tc = T[r]; break; }
+        }
+    }
+    g->t_start = (cuke > 0.0 && tc < 1e300) ? tc : t0;
+    g->bnd_stop = stop_at_end != 0;
+    if (t_start) *t_start = g->t_start;
+    return CLIFFS_OK;
+}
+
 int cliffs_step_n(cliffs_grid* g, int64_t n) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
@@ -963,9 +1052,39 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
     if (rc) return rc;
     cudaStream_t s = g->stream;
     StepArgs a;
+    double t_end = 1e300;
+    if (g->bnd_any)
+        for (int e = 0; e < 4; ++e)
+            if (!g->bnd_t[e].empty()) t_end = std::min(t_end, g->bnd_t[e].back());
     for (long long k = 0; k < n; ++k) {
         const long long st = g->step + 1;
         const int in = (int)(g->step & 1), out = 1 - in;
+        if (g->bnd_any) {
+            const double t = g->t_start + (double)g->step * g->cfg.dt;
+            if (g->bnd_stop && t + g->cfg.dt > t_end * (1.0 + 1e-12) + 1e-9 * g->cfg.dt) break;
+            BndStep b{};
+            int npmax = 0;
+            for (int e = 0; e < 4; ++e) {
+                const std::vector<double>& T = g->bnd_t[e];
+                if (T.empty()) continue;
+                long long i = 0;
+                double w = 0.0;
+                if (t <= T.front() || T.size() == 1) i = 0;
+                else if (t >= T.back()) i = (long long)T.size() - 1;
+                else {
+                    i = (long long)(std::upper_bound(T.begin(), T.end(), t) - T.begin()) - 1;
+                    w = (t - T[i]) / (T[i + 1] - T[i]);
+                }
+                b.vals[e] = g->bnd_v[e];
+                b.np[e] = e < 2 ? g->ny : g->nx;
+                b.k[e] = i;
+                b.w[e] = w;
+                npmax = std::max(npmax, b.np[e]);
+            }
+            k_bnd<<<dim3((npmax + 127) / 128, 4), 128, 0, s>>>(g->eta[in], g->u[in], g->v[in], g->pitch, g->nx,
+                                                              g->ny, b);
+            CK(cudaGetLastError());
+        }
         fill_step_args(g, a, in, out);
         a.step = st;
         a.yfirst = g->cfg.alternate && ((st - 1) & 1);       // odd steps sweep y first
@@ -1014,6 +1133,7 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
     if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the persistent run sweeps x then y every step");
+    if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "a grid under boundary input runs through cliffs_step_n");
     if (n == 0) return CLIFFS_OK;
     const long long last = g->step + n;
     int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
@@ -1123,6 +1243,7 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
     if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes the x-then-y order only");
     if (g->cfg.solver == 1) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes eq. (solver2) only");
+    if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "the adjoint does not take boundary input");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);

@@ -1,0 +1,132 @@
+"""Boundary input and the nesting chain on the GPU (section "Running Options": boundary
+series for enclosed grids, boundary input, parameter-file fields 5 and 13).
+
+The reading of how input enters the scheme (edge nodes take the input at the current model
+time before each step, S and N owning the corners) is the oracle's; here the GPU is checked
+against the oracle's forced run, the parent -> child chain is checked bit for bit on the GPU
+in open water, and the clock (cuke start, stop at the end of the records) is checked.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG, ERR_STATE
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _open_water(nx=150, ny=130):
+    x = 100.0 * np.arange(nx)
+    y = 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = 40.0 + 8.0 * np.sin(X / 900.0) * np.cos(Y / 700.0)
+    eta0 = 0.8 * np.exp(-((X - 6000.0) ** 2 + (Y - 5000.0) ** 2) / (2 * 700.0 ** 2))
+    return x, y, P.f32(d), P.f32(eta0)
+
+
+def test_nesting_chain_is_bit_exact_on_the_gpu():
+    """Parent on the GPU records the series of an enclosed grid on its own nodes; the child,
+    driven by them, equals the parent inside its edges bit for bit (open water)."""
+    from workloads import Nest
+    x, y, d, eta0 = _open_water()
+    dt, steps = 1.5, 60
+    i0, j0, cx, cy = 41, 33, 70, 64
+    nest = Nest(x[i0], y[j0], 100.0, 100.0, cx, cy)
+    par = CliffsGrid(len(x), len(y), dt, manning_n2=6.25e-4, nests=[nest], bndout=1)
+    par.set_bathy(x, y, d, False)
+    par.set_initial(eta0.astype(np.float32))
+    par.step(steps)
+    series = [par.boundary(0, e) for e in range(4)]
+    pe, pu, pv = par.state()
+    par.close()
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    ch = CliffsGrid(cx, cy, dt, manning_n2=6.25e-4)
+    ch.set_bathy(x[i0:i0 + cx], y[j0:j0 + cy], d[sub], False)
+    ch.set_initial(eta0[sub].astype(np.float32))
+    times = dt * np.arange(steps + 1)
+    for e in range(4):
+        ch.set_boundary_input(e, times, series[e])
+    assert ch.set_boundary_clock() == 0.0
+    ch.step(steps)
+    ce, cu, cv = ch.state()
+    for a, b in ((ce, pe), (cu, pu), (cv, pv)):
+        assert np.array_equal(a[1:-1, 1:-1], b[sub][1:-1, 1:-1])
+    with pytest.raises(CliffsError) as e:
+        ch.step(2, persistent=True)
+    assert e.value.code == ERR_ARG
+    with pytest.raises(CliffsError) as e:
+        ch.adjoint(3, None)
+    assert e.value.code == ERR_ARG
+    ch.close()
+
+
+def test_forced_run_against_the_oracle_on_a_beach():
+    """A child straddling the shoreline of a beach, driven by the oracle parent's series:
+    the GPU's forced run against the oracle's forced run."""
+    from workloads import Nest
+    w = workloads.beach_200(160, 120, steps=150)
+    d64 = P.f32(P.oracle_depth(w))
+    i0, j0, cx, cy = 70, 30, 90, 64                        # reaches past the shoreline
+    nest = Nest(float(w.x[i0]), float(w.y[j0]), 100.0, 100.0, cx, cy)
+    p = oracle.params_from(w)
+    par = oracle.run(p, w.x, w.y, d64, w.eta0, nsteps=w.steps, bndout=1, nests=[nest])
+    times = w.dt * np.arange(w.steps + 1)
+    series = {e: (times, par["boundary"][0][e]) for e in range(4)}
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    gauges = np.array([(10, 32), (40, 32), (70, 32), (85, 20)], np.int32)
+    pc = oracle.params(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2)
+    o = oracle.run_forced(pc, w.x[i0:i0 + cx], w.y[j0:j0 + cy], d64[sub], w.eta0[sub], series,
+                          nsteps=w.steps, gout=1, gauges=gauges)
+    g = CliffsGrid(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, gauges=[tuple(q) for q in gauges])
+    g.set_bathy(w.x[i0:i0 + cx], w.y[j0:j0 + cy], d64[sub], False)
+    g.set_initial(w.eta0[sub].astype(np.float32))
+    for e in range(4):
+        g.set_boundary_input(e, times, series[e][1])
+    g.step(w.steps)
+    rel, absol = P.gauge_errors(g.gauges()[:, :, 0], o["gauges"][:, :, 0])
+    P.report("forced_beach_child", gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0))
+    assert rel.max(initial=0.0) <= P.GAUGE_RTOL and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
+    e32 = g.state()[0]
+    wet32, wet64, near = P.wet_masks(e32, o["eta"], d64[sub], d64[sub], w.h_min)
+    assert np.array_equal(wet32 & ~near, wet64 & ~near)
+    assert np.abs(e32 - o["eta"])[wet64].max() <= 1e-4 * np.abs(w.eta0).max()
+    g.close()
+
+
+def test_boundary_clock_cuke_and_stop_at_end():
+    """Start at the first record whose |eta| exceeds cuke; with stop_at_end the run ends at
+    the last record; without it the last record holds."""
+    x = 50.0 * np.arange(120)
+    d = np.full((1, 120), 10.0)
+    dt = 1.0
+    times = np.arange(0.0, 41.0, 2.0)                       # 21 records, 40 s
+    eta_w = np.where(times >= 10.0, 0.05 * np.sin(0.2 * (times - 10.0)) + 0.002, 0.0)
+    vals = np.zeros((len(times), 3, 1))
+    vals[:, 2, 0] = eta_w
+    g = CliffsGrid(120, 1, dt, manning_n2=0.0)
+    g.set_bathy(x, np.zeros(1), d, False)
+    g.set_initial(np.zeros((1, 120), np.float32))
+    with pytest.raises(CliffsError) as e:
+        g.set_boundary_clock(0.001)
+    assert e.value.code == ERR_STATE
+    with pytest.raises(CliffsError) as e:
+        g.set_boundary_input(2, times, np.zeros((len(times), 3, 120)))    # S runs along the line
+    assert e.value.code == ERR_ARG
+    g.set_boundary_input(0, times, vals)
+    assert g.set_boundary_clock(0.001, stop_at_end=True) == 10.0
+    g.step(1000)
+    assert g.steps_done == 30                                # 10 s .. 40 s at dt = 1 s
+    e1 = g.state()[0]
+    assert np.abs(e1).max() > 0.01                           # the wave came in from the west
+    # the same input from t = 0 without stopping: runs all steps, the last record holds
+    g.set_initial(np.zeros((1, 120), np.float32))
+    assert g.set_boundary_clock(0.0, stop_at_end=False) == 0.0
+    g.step(60)
+    assert g.steps_done == 60
+    # the oracle's forced run from t = 10 s matches the first run
+    o = oracle.run_forced(oracle.params(120, 1, dt, manning_n2=0.0), x, np.zeros(1), d, np.zeros((1, 120)),
+                          {0: (times, vals)}, nsteps=30, t0=10.0)
+    assert np.abs(e1 - o["eta"]).max() <= 1e-4 * 0.05
+    g.close()

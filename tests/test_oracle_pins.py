@@ -571,3 +571,39 @@ def test_runup_of_a_solitary_wave_follows_the_runup_law():
     R = em[em > -1e30].max()
     law = w.extra["runup_law"]
     assert abs(R / law - 1.0) <= 0.10, (R, law)
+
+
+# ----------------------------------------------------------------------------------------
+# Nesting chain (section "Running Options": boundary series for enclosed grids, then boundary
+# input into such a grid). A child on the parent's own nodes, driven by the parent's series,
+# must reproduce the parent inside it exactly in open water: there the update of an
+# interior node reads only its neighbours (the 3-node stencil of eq. (solver2) in each
+# sweep), and the child's edge nodes carry the parent's values at every step.
+
+def _open_water_parent(nx=60, ny=50, steps=40):
+    x = 100.0 * np.arange(nx)
+    y = 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = 40.0 + 8.0 * np.sin(X / 900.0) * np.cos(Y / 700.0)
+    eta0 = 0.8 * np.exp(-((X - 2400.0) ** 2 + (Y - 2100.0) ** 2) / (2 * 500.0 ** 2))
+    p = oracle.params(nx, ny, 1.5, manning_n2=6.25e-4)
+    return x, y, d, eta0, p, steps
+
+
+def test_nesting_chain_reproduces_the_parent_inside_the_child():
+    from workloads import Nest
+    x, y, d, eta0, p, steps = _open_water_parent()
+    i0, j0, cx, cy = 17, 12, 30, 24
+    nest = Nest(x[i0], y[j0], 100.0, 100.0, cx, cy)
+    par = oracle.run(p, x, y, d, eta0, nsteps=steps, bndout=1, nests=[nest])
+    series = par["boundary"][0]                               # W, E, S, N: [nt][3][np]
+    times = 1.5 * np.arange(steps + 1)
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    pc = oracle.params(cx, cy, 1.5, manning_n2=6.25e-4)
+    ch = oracle.run_forced(pc, x[i0:i0 + cx], y[j0:j0 + cy], d[sub], eta0[sub],
+                           {e: (times, series[e]) for e in range(4)}, nsteps=steps)
+    for f in ("eta", "u", "v"):
+        assert np.array_equal(ch[f][1:-1, 1:-1], par[f][sub][1:-1, 1:-1]), f
+    # without the input the child's walls reflect the wave and the interior departs
+    free = oracle.run(pc, x[i0:i0 + cx], y[j0:j0 + cy], d[sub], eta0[sub], nsteps=steps)
+    assert np.abs(free["eta"] - par["eta"][sub]).max() > 1e-3
