@@ -116,6 +116,18 @@ int cliffs_read_depth(cliffs_grid* g, double* depth);
 int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const float* u,
                        const float* v, int quake);
 
+/* Initial state interpolated from a source grid (section "Running Options", "The input to
+ * the computations": the initial conditions need not cover the master grid nor share its
+ * nodes; they are interpolated onto the part of the master grid inside the source grid and
+ * set to zero outside it). sx[snx], sy[sny]: the source nodes, increasing, in the master's
+ * units; eta, u, v: [sny][snx] FP32 (u, v may be NULL for zero). Master nodes inside the
+ * source extent take the bilinear interpolation of the four surrounding source nodes (FP64
+ * weights in coordinate space, rounded once to FP32); a source dimension of one node covers
+ * only master nodes at exactly that coordinate. Then as cliffs_set_initial (scenario >= 0,
+ * or -1 when batch == 1; quake as there). Errors: ERR_STATE before set_bathy; ERR_ARG. */
+int cliffs_set_initial_interp(cliffs_grid* g, int scenario, const double* sx, int32_t snx, const double* sy,
+                              int32_t sny, const float* eta, const float* u, const float* v, int quake);
+
 /* Per-scenario step limits for a batched grid: scenario b stops after steps[b] steps
  * (its state, max-wave and records then stay as they were). Default: unlimited. */
 int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);

@@ -12,6 +12,7 @@ through ctypes:
 * ``run``           - time steps with max-wave, gauges and enclosed-grid boundary series
 * ``run_tlm``       - the tangent-linear model of ``run`` (branches frozen on the primal)
 * ``run_forced``    - ``run`` under boundary input on the domain edges
+* ``interp_initial`` - initial conditions from a source grid onto the master grid
 
 Parity status of each part (what pins it) is listed in the tests under ``tests/test_oracle_*``.
 The spherical metric (reading 7) is pinned only by its Cartesian limit and by propagation
@@ -261,6 +262,41 @@ def run_forced(p: OracleParams, x, y, depth, eta, boundary, u=None, v=None, nste
     if rc != 0:
         raise ValueError("oracle_run_forced failed (%d)" % rc)
     return dict(eta=eta, u=u, v=v, gauges=grec[: ng.value, :G] if G else None)
+
+
+def interp_initial(mx, my, sx, sy, field):
+    """Initial conditions from a source grid (section "Running Options", "The input to the
+    computations"): on master nodes inside the source grid the bilinear interpolation of the
+    four surrounding source nodes, zero outside. A source dimension of one node covers only
+    master nodes at exactly its coordinate."""
+    mx, my, sx, sy = (np.asarray(a, np.float64) for a in (mx, my, sx, sy))
+    field = np.asarray(field, np.float64).reshape(len(sy), len(sx))
+    out = np.zeros((len(my), len(mx)))
+
+    def cell(c, xp):
+        if len(c) == 1:
+            return (0, 0.0) if xp == c[0] else None
+        if xp < c[0] or xp > c[-1]:
+            return None
+        k = int(np.searchsorted(c, xp, side="right")) - 1
+        k = min(max(k, 0), len(c) - 2)
+        return k, (xp - c[k]) / (c[k + 1] - c[k])
+
+    for r, yp in enumerate(my):
+        cr = cell(sy, yp)
+        if cr is None:
+            continue
+        j, b = cr
+        j1 = j + 1 if b > 0 else j
+        for c_, xp in enumerate(mx):
+            cc = cell(sx, xp)
+            if cc is None:
+                continue
+            i, a = cc
+            i1 = i + 1 if a > 0 else i
+            out[r, c_] = ((1 - b) * ((1 - a) * field[j, i] + a * field[j, i1]) +
+                          b * ((1 - a) * field[j1, i] + a * field[j1, i1]))
+    return out
 
 
 def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv=None,

@@ -27,7 +27,7 @@ __all__ = [
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
-    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "EXPORTED",
+    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -40,7 +40,7 @@ EXPORTED = [
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
-    "cliffs_set_boundary_input", "cliffs_set_boundary_clock",
+    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
 ]
 
 
@@ -89,6 +89,7 @@ def lib():
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_set_boundary_input": ([vp, C.c_int, vp, C.c_int64, vp], C.c_int),
             "cliffs_set_boundary_clock": ([vp, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
+            "cliffs_set_initial_interp": ([vp, C.c_int, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, C.c_int], C.c_int),
             "cliffs_steps_done": ([vp, i64p], C.c_int),
             "cliffs_read_gauges": ([vp, C.c_int, vp, i64p], C.c_int),
             "cliffs_read_maxwave": ([vp, C.c_int, vp, vp], C.c_int),
@@ -165,6 +166,15 @@ def cliffs_set_initial(g, scenario, eta, u=None, v=None, quake=0):
     pu, ku = _ptr(u, np.float32)
     pv, kv = _ptr(v, np.float32)
     _check(lib().cliffs_set_initial(g, int(scenario), pe, pu, pv, int(quake)))
+
+
+def cliffs_set_initial_interp(g, scenario, sx, sy, eta, u=None, v=None, quake=0):
+    px, kx = _ptr(sx, np.float64)
+    py, ky = _ptr(sy, np.float64)
+    pe, ke = _ptr(eta, np.float32)
+    pu, ku = _ptr(u, np.float32)
+    pv, kv = _ptr(v, np.float32)
+    _check(lib().cliffs_set_initial_interp(g, int(scenario), px, len(sx), py, len(sy), pe, pu, pv, int(quake)))
 
 
 def cliffs_set_durations(g, steps):
@@ -335,6 +345,9 @@ class CliffsGrid:
 
     def set_initial(self, eta, u=None, v=None, scenario=-1, quake=0):
         cliffs_set_initial(self.h, scenario, eta, u, v, quake)
+
+    def set_initial_interp(self, sx, sy, eta, u=None, v=None, scenario=-1, quake=0):
+        cliffs_set_initial_interp(self.h, scenario, sx, sy, eta, u, v, quake)
 
     def set_durations(self, steps):
         cliffs_set_durations(self.h, steps)

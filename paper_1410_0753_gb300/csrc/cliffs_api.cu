@@ -224,6 +224,23 @@ __global__ void k_bnd(float* eta, float* u, float* v, int pitch, int nx, int ny,
     eta[o] = (float)val[2];
 }
 
+// Bilinear interpolation of a source field [sny][snx] onto the master nodes: per master
+// column the source interval and fraction (col[ix] = (i, a), i < 0 outside), per row alike;
+// zero outside the source grid. FP64 arithmetic, rounded once to FP32.
+struct Ax { int i; double a; };
+__global__ void k_interp(const float* __restrict__ src, int snx, const Ax* __restrict__ col,
+                         const Ax* __restrict__ row, int nx, int ny, float* out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nx * ny) return;
+    const int ix = (int)(idx % nx), iy = (int)(idx / nx);
+    const Ax c = col[ix], r = row[iy];
+    if (c.i < 0 || r.i < 0) { out[idx] = 0.f; return; }
+    const int i1 = c.a > 0.0 ? c.i + 1 : c.i, j1 = r.a > 0.0 ? r.i + 1 : r.i;
+    const double v00 = src[(long long)r.i * snx + c.i], v01 = src[(long long)r.i * snx + i1];
+    const double v10 = src[(long long)j1 * snx + c.i], v11 = src[(long long)j1 * snx + i1];
+    out[idx] = (float)((1.0 - r.a) * ((1.0 - c.a) * v00 + c.a * v01) + r.a * ((1.0 - c.a) * v10 + c.a * v11));
+}
+
 }  // namespace
 
 void cliffs::set_last_error(const char* msg) {
@@ -240,6 +257,7 @@ struct cliffs_grid {
     long long plane = 0;
     cudaStream_t stream = nullptr;
     bool have_bathy = false, have_init = false;
+    std::vector<double> hx, hy;              // node coordinates as given to set_bathy
     float* eta[2] = {nullptr, nullptr};
     float* u[2] = {nullptr, nullptr};
     float* v[2] = {nullptr, nullptr};
@@ -718,6 +736,8 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
     std::vector<double> hx(nx), hy(ny);
     CK(cudaMemcpy(hx.data(), x, sizeof(double) * nx, cudaMemcpyDefault));
     CK(cudaMemcpy(hy.data(), y, sizeof(double) * ny, cudaMemcpyDefault));
+    g->hx = hx;
+    g->hy = hy;
     for (int i = 0; i + 1 < nx; ++i)
         if (!(hx[i + 1] > hx[i])) return set_err(CLIFFS_ERR_ARG, "x must be strictly increasing (index %d)", i);
     for (int j = 0; j + 1 < ny; ++j)
@@ -953,6 +973,55 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
     CK(cudaStreamSynchronize(s));
     g->have_init = true;
     return CLIFFS_OK;
+}
+
+int cliffs_set_initial_interp(cliffs_grid* g, int scenario, const double* sx, int32_t snx, const double* sy,
+                              int32_t sny, const float* eta, const float* u, const float* v, int quake) {
+    g_err[0] = 0;
+    if (!g || !sx || !sy || !eta) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_bathy) return set_err(CLIFFS_ERR_STATE, "set_bathy first");
+    if (snx < 1 || sny < 1) return set_err(CLIFFS_ERR_ARG, "empty source grid");
+    if (scenario < 0 && g->B != 1) return set_err(CLIFFS_ERR_ARG, "interpolate one scenario at a time");
+    std::vector<double> hsx(snx), hsy(sny);
+    CK(cudaMemcpy(hsx.data(), sx, sizeof(double) * snx, cudaMemcpyDefault));
+    CK(cudaMemcpy(hsy.data(), sy, sizeof(double) * sny, cudaMemcpyDefault));
+    for (int i = 0; i + 1 < snx; ++i)
+        if (!(hsx[i + 1] > hsx[i])) return set_err(CLIFFS_ERR_ARG, "source x must increase");
+    for (int j = 0; j + 1 < sny; ++j)
+        if (!(hsy[j + 1] > hsy[j])) return set_err(CLIFFS_ERR_ARG, "source y must increase");
+    const int nx = g->nx, ny = g->ny;
+    std::vector<Ax> col(nx), row(ny);
+    for (int c = 0; c < nx; ++c) {
+        int i; double a;
+        col[c] = locate(hsx, g->hx[c], &i, &a) ? Ax{i, a} : Ax{-1, 0.0};
+    }
+    for (int r = 0; r < ny; ++r) {
+        int j; double b;
+        row[r] = locate(hsy, g->hy[r], &j, &b) ? Ax{j, b} : Ax{-1, 0.0};
+    }
+    const size_t N = (size_t)nx * ny, S = (size_t)snx * sny;
+    int rc = ensure_tmp(g, sizeof(float) * (3 * N + S) + sizeof(Ax) * (nx + ny) + 256);
+    if (rc) return rc;
+    float* out = (float*)g->tmp;
+    float* src = out + 3 * N;
+    Ax* dcol = reinterpret_cast<Ax*>(reinterpret_cast<char*>(g->tmp) + ((sizeof(float) * (3 * N + S) + 15) & ~size_t(15)));
+    Ax* drow = dcol + nx;
+    cudaStream_t s = g->stream;
+    CK(cudaMemcpyAsync(dcol, col.data(), sizeof(Ax) * nx, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(drow, row.data(), sizeof(Ax) * ny, cudaMemcpyHostToDevice, s));
+    const float* fields[3] = {eta, u, v};
+    for (int f = 0; f < 3; ++f) {
+        if (!fields[f]) continue;
+        CK(cudaMemcpyAsync(src, fields[f], sizeof(float) * S, cudaMemcpyDefault, s));
+        k_interp<<<nblk((long long)N), 256, 0, s>>>(src, snx, dcol, drow, nx, ny, out + f * N);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(s));
+    // the interpolated fields are copied out of the scratch by set_initial (which may reuse it)
+    std::vector<float> h(3 * N);
+    CK(cudaMemcpy(h.data(), out, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost));
+    return cliffs_set_initial(g, scenario < 0 ? -1 : scenario, h.data(), u ? h.data() + N : nullptr,
+                              v ? h.data() + 2 * N : nullptr, quake);
 }
 
 int cliffs_set_durations(cliffs_grid* g, const int64_t* steps) {

@@ -130,3 +130,27 @@ def test_boundary_clock_cuke_and_stop_at_end():
                           {0: (times, vals)}, nsteps=30, t0=10.0)
     assert np.abs(e1 - o["eta"]).max() <= 1e-4 * 0.05
     g.close()
+
+
+def test_initial_conditions_interpolated_from_a_source_grid():
+    """A coarser source grid covering part of the master grid: the GPU's interpolated initial
+    state against the oracle's interpolation (both FP64, rounded to FP32), zero outside."""
+    w = workloads.beach_200(140, 110, steps=10)
+    rng = np.random.default_rng(21)
+    sx = np.sort(rng.uniform(1500.0, 11000.0, 37))
+    sy = np.sort(rng.uniform(-500.0, 8000.0, 29))
+    SX, SY = np.meshgrid(sx, sy)
+    eta = (0.4 * np.exp(-((SX - 6000.0) ** 2 + (SY - 4000.0) ** 2) / (2 * 2000.0 ** 2))).astype(np.float32)
+    u = (0.1 * np.sin(SX / 3000.0)).astype(np.float32)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth, False)
+    g.set_initial_interp(sx, sy, eta, u)
+    e32, u32, v32 = g.state()
+    g.close()
+    for got, src in ((e32, eta), (u32, u)):
+        want = P.f32(oracle.interp_initial(w.x, w.y, sx, sy, src))
+        assert np.all(np.abs(got - want) <= 2.5e-7 * np.abs(want) + 1e-12)
+    assert not v32.any()
+    MX, MY = np.meshgrid(w.x, w.y)
+    outside = (MX < sx[0]) | (MX > sx[-1]) | (MY < sy[0]) | (MY > sy[-1])
+    assert outside.any() and not e32[outside].any() and not u32[outside].any()

@@ -607,3 +607,25 @@ def test_nesting_chain_reproduces_the_parent_inside_the_child():
     # without the input the child's walls reflect the wave and the interior departs
     free = oracle.run(pc, x[i0:i0 + cx], y[j0:j0 + cy], d[sub], eta0[sub], nsteps=steps)
     assert np.abs(free["eta"] - par["eta"][sub]).max() > 1e-3
+
+
+# ----------------------------------------------------------------------------------------
+# Initial conditions from a source grid (section "Running Options", "The input to the
+# computations"): interpolated inside the source grid, zero outside it.
+
+def test_initial_condition_interpolation_exact_for_linear_fields_and_zero_outside():
+    rng = np.random.default_rng(9)
+    sx = np.sort(rng.uniform(100.0, 900.0, 23))
+    sy = np.sort(rng.uniform(-300.0, 500.0, 17))
+    SX, SY = np.meshgrid(sx, sy)
+    f = 0.3 + 1e-3 * SX - 2e-3 * SY
+    mx = np.linspace(0.0, 1000.0, 41)
+    my = np.linspace(-400.0, 600.0, 37)
+    out = oracle.interp_initial(mx, my, sx, sy, f)
+    MX, MY = np.meshgrid(mx, my)
+    inside = (MX >= sx[0]) & (MX <= sx[-1]) & (MY >= sy[0]) & (MY <= sy[-1])
+    assert np.abs(out - (0.3 + 1e-3 * MX - 2e-3 * MY))[inside].max() < 1e-12
+    assert not out[~inside].any()
+    # master nodes on source nodes take the source values
+    same = oracle.interp_initial(sx, sy, sx, sy, f)
+    assert np.array_equal(same, f)
