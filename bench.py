@@ -196,7 +196,7 @@ def _event_ms(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_forms(torch, stream):
+def measure_forms(torch, stream, only=None, adjoint_steps=None):
     """The batched ensemble (256 scenarios of uneven duration on one 512 x 512 bathymetry, one
     persistent graph-captured launch) and the adjoint (1024 x 1024, 2000 steps, checkpoint
     every 100), each reported against the plain single-scenario forward on this GPU."""
@@ -204,7 +204,17 @@ def measure_forms(torch, stream):
     from paper_1410_0753_gb300 import CliffsGrid
     out = {}
     s = stream.cuda_stream
-    # batched
+    if only in (None, "batched"):
+        out["batched"] = _form_batched(torch, stream, workloads, CliffsGrid)
+    if only in (None, "stress"):
+        out["stress"] = _form_stress(torch, stream, workloads, CliffsGrid)
+    if only in (None, "adjoint"):
+        out["adjoint"] = _form_adjoint(torch, stream, workloads, CliffsGrid, adjoint_steps)
+    return out
+
+
+def _form_batched(torch, stream, workloads, CliffsGrid):
+    s = stream.cuda_stream
     w = workloads.ensemble_512()
     g = CliffsGrid.from_workload(w, stream=s)
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
@@ -227,7 +237,7 @@ def measure_forms(torch, stream):
     g1.close()
     v_b = useful / (ms_b / 1e3) / 1e9
     v_1 = w.cells * n1 / (ms_1 / 1e3) / 1e9
-    out["batched"] = {
+    return {
         "workload": w.name, "scenarios": int(w.batch), "durations": [int(w.durations.min()), int(w.durations.max())],
         "value": v_b, "unit": UNIT, "ms": ms_b, "launches": 1,
         "rows_per_warp": min(tune, key=tune.get) if tune else None,
@@ -236,11 +246,15 @@ def measure_forms(torch, stream):
         "vs_single_scenario_forward": v_b / v_1,
         "note": "useful cell-updates (each scenario up to its own duration) / time of one "
                 "persistent, cooperative, graph-captured launch"}
+
+
+def _form_stress(torch, stream, workloads, CliffsGrid):
     # the HBM stress grid (8192 x 8192, shorelines around 10 islands), as a pure step and with
     # max-wave every step; its 1.9 GB working set is far larger than L2
+    s = stream.cuda_stream
     w = workloads.shelf_islands()
     peaks, _ = measured_peaks()
-    out["stress"] = {"workload": w.name, "cells": w.cells}
+    out = {"workload": w.name, "cells": w.cells}
     for tag, maxout, bpc in (("pure_step", 10 ** 9, 28), ("maxwave_every_step", 1, 36)):
         g = CliffsGrid.from_workload(w, stream=s, maxout=maxout, gauges=[], nests=[])
         g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
@@ -250,13 +264,17 @@ def measure_forms(torch, stream):
         n = 60
         ms = _event_ms(torch, stream, lambda: g.step(n))
         v = w.cells * n / (ms / 1e3) / 1e9
-        out["stress"][tag] = {"value": v, "unit": UNIT, "steps": n, "ms_per_step": ms / n,
+        out[tag] = {"value": v, "unit": UNIT, "steps": n, "ms_per_step": ms / n,
                               "bytes_per_cell": bpc, "achieved_gbs": v * bpc,
                               "frac": v * bpc / peaks["hbm_gbs"],
                               "rows_per_warp": min(tune, key=tune.get) if tune else None}
         g.close()
-    # adjoint
-    w = workloads.inversion_1024()
+    return out
+
+
+def _form_adjoint(torch, stream, workloads, CliffsGrid, steps=None):
+    s = stream.cuda_stream
+    w = workloads.inversion_1024(steps=steps or 2000)
     g = CliffsGrid.from_workload(w, stream=s)
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
     e0 = w.eta0.astype(np.float32)
@@ -273,14 +291,13 @@ def measure_forms(torch, stream):
     g.set_initial(e0)
     ms_a = _event_ms(torch, stream, lambda: g.adjoint(n, seed, 100, grad))
     g.close()
-    out["adjoint"] = {
+    return {
         "workload": w.name, "steps": n, "checkpoint_every": 100, "gauges": len(w.gauges),
         "gradient_ms": ms_a, "forward_ms": ms_f, "gradient_over_forward": ms_a / ms_f,
         "value": w.cells * n / (ms_a / 1e3) / 1e9, "unit": UNIT,
         "forward_value": w.cells * n / (ms_f / 1e3) / 1e9,
         "note": "gradient = checkpoint pass + segment recomputation + adjoint steps, one call "
                 "of cliffs_adjoint_n; forward = cliffs_step_n over the same steps"}
-    return out
 
 
 def run_cuda(args, world, rank, local):
@@ -442,9 +459,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms-only", choices=["batched", "stress", "adjoint"],
+                    help="measure one form only and print it (no headline line)")
+    ap.add_argument("--adjoint-steps", type=int, default=None)
     args = ap.parse_args()
     world, rank, local = dist_init()
-    if args.impl == "reference":
+    if args.forms_only:
+        import torch
+        from paper_1410_0753_gb300 import _build
+        _build.build()
+        print(json.dumps({"forms": measure_forms(torch, torch.cuda.current_stream(), args.forms_only,
+                                                 args.adjoint_steps)}), flush=True)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_cuda(args, world, rank, local)
