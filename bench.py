@@ -290,12 +290,23 @@ def _form_adjoint(torch, stream, workloads, CliffsGrid, steps=None):
     ms_f = _event_ms(torch, stream, lambda: g.step(n))
     g.set_initial(e0)
     ms_a = _event_ms(torch, stream, lambda: g.adjoint(n, seed, 100, grad))
+    # the same gradient after a forward that recorded its checkpoints (the autograd path)
+    g.set_initial(e0)
+    g.adjoint_record(100)
+    ms_fr = _event_ms(torch, stream, lambda: g.step(n))
+    ms_ar = _event_ms(torch, stream, lambda: g.adjoint_recorded(seed, grad))
+    g.adjoint_record(0)
     g.close()
     return {
         "workload": w.name, "steps": n, "checkpoint_every": 100, "gauges": len(w.gauges),
         "gradient_ms": ms_a, "forward_ms": ms_f, "gradient_over_forward": ms_a / ms_f,
         "value": w.cells * n / (ms_a / 1e3) / 1e9, "unit": UNIT,
         "forward_value": w.cells * n / (ms_f / 1e3) / 1e9,
+        "after_recorded_forward": {"forward_ms": ms_fr, "gradient_ms": ms_ar,
+                                   "gradient_over_forward": ms_ar / ms_f,
+                                   "note": "forward with a checkpoint kept every 100 steps "
+                                           "(cliffs_adjoint_record), then cliffs_adjoint_recorded: "
+                                           "segment recomputation + adjoint steps"},
         "note": "gradient = checkpoint pass + segment recomputation + adjoint steps, one call "
                 "of cliffs_adjoint_n; forward = cliffs_step_n over the same steps"}
 

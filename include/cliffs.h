@@ -197,6 +197,23 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
 int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                      float* dL_deta0);
 
+/* Record the forward run for the adjoint (no counterpart in the paper). With
+ * checkpoint_every = K > 0, called right after cliffs_set_initial, the initial state and then
+ * every K-th state produced by cliffs_step_n are kept (12 bytes per node each, the store grows
+ * as the run does), so that cliffs_adjoint_recorded needs no checkpoint pass of its own. A
+ * later cliffs_set_initial starts a new record with the same spacing; K = 0 stops recording
+ * and frees the store. A recording grid runs through cliffs_step_n only (the persistent run
+ * rejects it). Errors: ERR_STATE before set_initial or after steps since it; ERR_ARG (K < 0,
+ * 1D grid, batch > 1). */
+int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every);
+
+/* cliffs_adjoint_n for the run recorded since the last cliffs_set_initial: n = the steps
+ * done since, X_0 = the recorded initial state, checkpoints = the recorded ones. Each segment
+ * is recomputed once from its checkpoint and the adjoint steps go back through it; the grid's
+ * current state is not used and not changed. Errors: ERR_STATE without a recorded run of at
+ * least one step; otherwise as cliffs_adjoint_n. */
+int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_deta0);
+
 /* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
  * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
  * longer warps, and the count of warps against the resident slots decides the tail). Each

@@ -27,7 +27,8 @@ __all__ = [
     "cliffs_read_maxwave", "cliffs_read_boundary", "cliffs_read_state", "cliffs_kernel_time",
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
-    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp", "EXPORTED",
+    "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -41,6 +42,7 @@ EXPORTED = [
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded",
 ]
 
 
@@ -87,6 +89,8 @@ def lib():
             "cliffs_step_n": ([vp, C.c_int64], C.c_int),
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
+            "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
+            "cliffs_adjoint_recorded": ([vp, vp, vp], C.c_int),
             "cliffs_set_boundary_input": ([vp, C.c_int, vp, C.c_int64, vp], C.c_int),
             "cliffs_set_boundary_clock": ([vp, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
             "cliffs_set_initial_interp": ([vp, C.c_int, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, C.c_int], C.c_int),
@@ -212,6 +216,15 @@ def cliffs_adjoint_n(g, n, checkpoint_every, dL_dgauges, out):
     _check(lib().cliffs_adjoint_n(g, int(n), int(checkpoint_every), ps, _out_ptr(out)))
 
 
+def cliffs_adjoint_record(g, checkpoint_every):
+    _check(lib().cliffs_adjoint_record(g, int(checkpoint_every)))
+
+
+def cliffs_adjoint_recorded(g, dL_dgauges, out):
+    ps, ks = _ptr(dL_dgauges, np.float32)
+    _check(lib().cliffs_adjoint_recorded(g, ps, _out_ptr(out)))
+
+
 def cliffs_set_boundary_input(g, edge, times, vals):
     """Boundary input of one edge (0 W, 1 E, 2 S, 3 N): times[nt], vals[nt][3][np] (u, v, eta);
     times=None removes it."""
@@ -312,6 +325,7 @@ class CliffsGrid:
         self.cfg = cfg
         self.nx, self.ny, self.batch = nx, ny, batch
         self.n_gauges = len(g) // 2
+        self.run_id = 0                 # changes with every set_initial and step through this object
         self.nest_shapes = [(n.nx, n.ny) for n in nests]
         self.h = cliffs_grid_create(cfg)
 
@@ -345,9 +359,11 @@ class CliffsGrid:
 
     def set_initial(self, eta, u=None, v=None, scenario=-1, quake=0):
         cliffs_set_initial(self.h, scenario, eta, u, v, quake)
+        self.run_id += 1
 
     def set_initial_interp(self, sx, sy, eta, u=None, v=None, scenario=-1, quake=0):
         cliffs_set_initial_interp(self.h, scenario, sx, sy, eta, u, v, quake)
+        self.run_id += 1
 
     def set_durations(self, steps):
         cliffs_set_durations(self.h, steps)
@@ -355,6 +371,7 @@ class CliffsGrid:
     def step(self, n, persistent=False):
         """Advance n steps: one launch per step, or (persistent=True) all n in one
         persistent, graph-captured launch with identical results."""
+        self.run_id += 1
         if persistent:
             cliffs_run_persistent(self.h, n)
         else:
@@ -403,6 +420,17 @@ class CliffsGrid:
 
     def set_boundary_clock(self, cuke=0.0, stop_at_end=False):
         return cliffs_set_boundary_clock(self.h, cuke, int(stop_at_end))
+
+    def adjoint_record(self, checkpoint_every=100):
+        """Keep checkpoints of the run from the current initial state (0 stops recording)."""
+        cliffs_adjoint_record(self.h, checkpoint_every)
+
+    def adjoint_recorded(self, dL_dgauges, out=None):
+        """Gradient for the run recorded since the last set_initial (see adjoint)."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        cliffs_adjoint_recorded(self.h, dL_dgauges, out)
+        return out
 
     def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None):
         """Gradient with respect to the current free surface of a loss whose derivative with

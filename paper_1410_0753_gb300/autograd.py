@@ -1,13 +1,16 @@
 """torch.autograd binding of the split-step run: initial free surface -> gauge eta records.
 
-The forward is cliffs_set_initial + cliffs_step_n; the backward is the library's hand-written
-adjoint (cliffs_adjoint_n), which recomputes the forward from checkpoints on the device and
-transposes every sweep with the forward's branches frozen. Argument marshalling only: all
-arithmetic runs in the library's CUDA kernels.
+The forward is cliffs_set_initial + cliffs_step_n with the run recorded for the adjoint
+(cliffs_adjoint_record: a checkpoint every K steps); the backward is the library's
+hand-written adjoint of that recorded run (cliffs_adjoint_recorded), which recomputes each
+segment from its checkpoint and transposes every sweep with the forward's branches frozen.
+If the grid has run something else in between, the backward starts over from eta0
+(cliffs_adjoint_n, with its own checkpoint pass). Argument marshalling only: all arithmetic
+runs in the library's CUDA kernels.
 """
 import torch
 
-from . import CliffsGrid, cliffs_adjoint_n, cliffs_read_gauges
+from . import CliffsGrid, cliffs_adjoint_n, cliffs_adjoint_recorded, cliffs_read_gauges
 
 
 class GaugeRun(torch.autograd.Function):
@@ -17,11 +20,12 @@ class GaugeRun(torch.autograd.Function):
     def forward(ctx, eta0, grid: CliffsGrid, n: int, checkpoint_every: int = 100):
         eta0 = eta0.detach().contiguous().float()
         grid.set_initial(eta0)
+        grid.adjoint_record(checkpoint_every)
         grid.step(n)
         nrec = cliffs_read_gauges(grid.h, 0)
         rec = torch.empty((nrec, grid.n_gauges, 3), dtype=torch.float32, device=eta0.device)
         cliffs_read_gauges(grid.h, 0, rec)
-        ctx.grid, ctx.n, ctx.k = grid, int(n), int(checkpoint_every)
+        ctx.grid, ctx.n, ctx.k, ctx.run_id = grid, int(n), int(checkpoint_every), grid.run_id
         ctx.save_for_backward(eta0)
         return rec[:, :, 0].contiguous()
 
@@ -29,9 +33,14 @@ class GaugeRun(torch.autograd.Function):
     def backward(ctx, grad):
         (eta0,) = ctx.saved_tensors
         grid = ctx.grid
-        grid.set_initial(eta0)                  # the adjoint starts from the run's X_0
         out = torch.empty_like(eta0)
-        cliffs_adjoint_n(grid.h, ctx.n, ctx.k, grad.detach().contiguous().float(), out)
+        seed = grad.detach().contiguous().float()
+        if grid.run_id == ctx.run_id:
+            cliffs_adjoint_recorded(grid.h, seed, out)
+        else:
+            grid.adjoint_record(0)
+            grid.set_initial(eta0)              # the adjoint starts from the run's X_0
+            cliffs_adjoint_n(grid.h, ctx.n, ctx.k, seed, out)
         return out, None, None, None
 
 

@@ -333,6 +333,12 @@ struct cliffs_grid {
     long long adj_seed_cap = 0;
     // boundary input: per edge (W, E, S, N) the record times (host) and (u, v, eta) series
     // (device), the model clock and whether a run stops at the end of the records
+    // forward checkpoints recorded by cliffs_step_n for cliffs_adjoint_recorded: spacing K
+    // (0: off), state every K steps since set_initial, steps recorded
+    int rec_K = 0;
+    float* rec_ckpt = nullptr;
+    long long rec_cap = 0;
+    long long rec_n = 0;
     std::vector<double> bnd_t[4];
     double* bnd_v[4] = {nullptr, nullptr, nullptr, nullptr};
     bool bnd_any = false;
@@ -610,6 +616,29 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.inv_dt2_s1 = g->cfg.solver == 1 ? (float)(1.0 / (g->cfg.dt * g->cfg.dt)) : 0.f;
 }
 
+// Keep the current state of a recorded run as checkpoint `idx` (grows the store by doubling).
+int record_checkpoint(cliffs_grid* g, long long idx) {
+    const size_t st = sizeof(float) * 3 * g->plane;
+    if (idx >= g->rec_cap) {
+        const long long cap = std::max<long long>(idx + 1, 2 * g->rec_cap);
+        float* nb = nullptr;
+        CK(cudaMalloc(&nb, st * cap));
+        if (g->rec_ckpt) {
+            CK(cudaMemcpyAsync(nb, g->rec_ckpt, st * g->rec_cap, cudaMemcpyDeviceToDevice, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            CK(cudaFree(g->rec_ckpt));
+        }
+        g->rec_ckpt = nb;
+        g->rec_cap = cap;
+    }
+    const int cb = (int)(g->step & 1);
+    float* dst = g->rec_ckpt + (size_t)3 * g->plane * idx;
+    CK(cudaMemcpyAsync(dst, g->eta[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
+    CK(cudaMemcpyAsync(dst + g->plane, g->u[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
+    CK(cudaMemcpyAsync(dst + 2 * g->plane, g->v[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
+    return CLIFFS_OK;
+}
+
 void free_grid(cliffs_grid* g) {
     for (int k = 0; k < 2; ++k) { cudaFree(g->eta[k]); cudaFree(g->u[k]); cudaFree(g->v[k]); }
     cudaFree(g->d32); cudaFree(g->d64); cudaFree(g->d64b);
@@ -624,6 +653,7 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
     cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
     for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
+    cudaFree(g->rec_ckpt);
     if (g->cap) cudaStreamDestroy(g->cap);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete g;
@@ -970,6 +1000,11 @@ int cliffs_set_initial(cliffs_grid* g, int scenario, const float* eta, const flo
         std::memcpy(&cour, &cb, sizeof(float));
         if (cour > 1.0f + 1e-6f) return set_err(CLIFFS_ERR_ARG, "Courant number %.4f > 1 after deformation", cour);
     }
+    g->rec_n = 0;
+    if (g->rec_K > 0) {
+        rc = record_checkpoint(g, 0);
+        if (rc) return rc;
+    }
     CK(cudaStreamSynchronize(s));
     g->have_init = true;
     return CLIFFS_OK;
@@ -1183,6 +1218,13 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
             if (g->ev.size() >= 4096) { rc = collect_timing(g); if (rc) return rc; }
         }
         g->step = st;
+        if (g->rec_K > 0) {
+            g->rec_n = st;
+            if (st % g->rec_K == 0) {
+                rc = record_checkpoint(g, st / g->rec_K);
+                if (rc) return rc;
+            }
+        }
     }
     int h[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(h, g->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
@@ -1203,6 +1245,7 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
     if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the persistent run sweeps x then y every step");
     if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "a grid under boundary input runs through cliffs_step_n");
+    if (g->rec_K > 0) return set_err(CLIFFS_ERR_ARG, "a recorded run goes through cliffs_step_n");
     if (n == 0) return CLIFFS_OK;
     const long long last = g->step + n;
     int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
@@ -1303,8 +1346,48 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     return CLIFFS_OK;
 }
 
+static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+                        float* dL_deta0, const float* recorded);
+
 int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                      float* dL_deta0) {
+    return adjoint_core(g, n, checkpoint_every, dL_dgauges, dL_deta0, nullptr);
+}
+
+int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (checkpoint_every < 0) return set_err(CLIFFS_ERR_ARG, "checkpoint_every must be >= 0");
+    if (checkpoint_every == 0) {
+        cudaFree(g->rec_ckpt);
+        g->rec_ckpt = nullptr;
+        g->rec_cap = 0;
+        g->rec_K = 0;
+        g->rec_n = 0;
+        return CLIFFS_OK;
+    }
+    if (g->kind != 0 || g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid with batch == 1");
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    if (g->step != 0) return set_err(CLIFFS_ERR_STATE, "record from the initial state (no steps since set_initial)");
+    g->rec_K = checkpoint_every;
+    g->rec_n = 0;
+    int rc = record_checkpoint(g, 0);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g->stream));
+    return CLIFFS_OK;
+}
+
+int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_deta0) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (g->rec_K <= 0 || g->rec_n < 1) return set_err(CLIFFS_ERR_STATE, "no recorded run");
+    return adjoint_core(g, g->rec_n, g->rec_K, dL_dgauges, dL_deta0, g->rec_ckpt);
+}
+
+// The adjoint steps of cliffs_adjoint_n; `recorded` holds the checkpoints of a recorded run
+// (X_0 included), else a checkpoint pass from the grid's current state makes them.
+static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+                        float* dL_deta0, const float* recorded) {
     g_err[0] = 0;
     if (!g || !dL_deta0) return set_err(CLIFFS_ERR_ARG, "null argument");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
@@ -1340,7 +1423,7 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
             if (rc) return rc;
         }
     }
-    if (g->adj_ncap < nseg || !g->adj_ckpt) {
+    if (!recorded && (g->adj_ncap < nseg || !g->adj_ckpt)) {
         cudaFree(g->adj_ckpt);
         g->adj_ckpt = nullptr;
         CK(cudaMalloc(&g->adj_ckpt, sizeof(float) * 3 * P * nseg));
@@ -1381,13 +1464,16 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
     };
-    // X_0: the grid's current state
+    const float* ckpt = recorded ? recorded : g->adj_ckpt;
+    // X_0: the grid's current state (or the recorded run's first checkpoint)
     const int cb = (int)cur_buf(g, 0);
-    CK(cudaMemcpyAsync(slot(0), g->eta[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(slot(0) + P, g->u[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-    // checkpoint pass: X_{sK} for every segment s
-    for (long long j = 0; j <= (nseg - 1) * K; ++j) {
+    if (!recorded) {
+        CK(cudaMemcpyAsync(slot(0), g->eta[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + P, g->u[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+    }
+    // checkpoint pass: X_{sK} for every segment s (a recorded run has them already)
+    for (long long j = 0; !recorded && j <= (nseg - 1) * K; ++j) {
         const int cur = (int)(j & 1);
         if (j % K == 0)
             CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K), slot(cur), sizeof(float) * 3 * P,
@@ -1424,7 +1510,7 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
     }
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
-        CK(cudaMemcpyAsync(slot(0), g->adj_ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
         for (long long j = j0; j + 1 < j1; ++j) {
             int rc = fwd((int)(j - j0), (int)(j - j0 + 1));
             if (rc) return rc;

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import workloads
-from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG
+from paper_1410_0753_gb300 import CliffsError, CliffsGrid, ERR_ARG, ERR_STATE
 from tests import parity as P
 
 pytestmark = pytest.mark.gpu
@@ -185,4 +185,47 @@ def test_adjoint_argument_errors():
         with pytest.raises(CliffsError) as e:
             g.adjoint(n, None, checkpoint_every=k)
         assert e.value.code == ERR_ARG
+    g.close()
+
+
+def test_recorded_run_gradient_equals_the_checkpoint_pass_gradient():
+    """A forward recorded by cliffs_step_n (a checkpoint every K steps) gives the adjoint the
+    same checkpoints as its own checkpoint pass, so cliffs_adjoint_recorded equals
+    cliffs_adjoint_n bit for bit; the autograd binding uses the record, and falls back to a
+    fresh start when the grid ran something else in between."""
+    import torch
+    from paper_1410_0753_gb300.autograd import gauge_run
+    w = workloads.inversion_1024(nx=128, ny=112, steps=90)
+    n = w.steps
+    seed = np.random.default_rng(8).standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    g = _start(w)
+    ref = g.adjoint(n, seed, checkpoint_every=20)
+    with pytest.raises(CliffsError) as e:
+        g.adjoint_recorded(seed)
+    assert e.value.code == ERR_STATE
+    g.adjoint_record(20)
+    g.step(50)
+    g.step(40)                                   # the record follows the run across calls
+    assert np.array_equal(g.adjoint_recorded(seed), ref)
+    with pytest.raises(CliffsError) as e:
+        g.step(2, persistent=True)
+    assert e.value.code == ERR_ARG
+    g.set_initial(w.eta0.astype(np.float32))     # a new record from the new initial state
+    g.step(n)
+    assert np.array_equal(g.adjoint_recorded(seed), ref)
+    with pytest.raises(CliffsError) as e:
+        g.adjoint_record(10)                     # only from an initial state
+    assert e.value.code == ERR_STATE
+    g.adjoint_record(0)
+    # autograd: recorded path, and the fresh-start path after another run on the grid
+    eta = torch.tensor(w.eta0, device="cuda", requires_grad=True)
+    out = gauge_run(eta, g, n, 20)
+    out.backward(torch.tensor(seed, device="cuda"))
+    a1 = eta.grad.detach().cpu().numpy()
+    eta.grad = None
+    out = gauge_run(eta, g, n, 20)
+    g.step(3)
+    out.backward(torch.tensor(seed, device="cuda"))
+    a2 = eta.grad.detach().cpu().numpy()
+    assert np.array_equal(a1, ref) and np.array_equal(a2, ref)
     g.close()
