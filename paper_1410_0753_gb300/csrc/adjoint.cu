@@ -20,7 +20,8 @@
 //
 // Derivatives are taken on the perturbation form used by the forward kernels (eta kept,
 // c_a - c_b = g (eta_a - eta_b + d_a - d_b)/(c_a + c_b)), which keeps the coefficients
-// free of the cancellation that p = w + 2c would suffer in FP32.
+// free of the cancellation that p = w + 2c would suffer in FP32. Reciprocals in the
+// coefficients come from the hardware approximation (relative error ~1e-7), as in the forward.
 #include "internal.h"
 #include "sweep.cuh"
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ AIface a_iface(const ANode& b, const ANode& a) {
     AIface f;
     const float de = a.e - b.e;
     f.S = a.c + b.c;
-    f.dcs = GRAV * (de + (a.d - b.d)) / f.S;           // c_a - c_b
+    f.dcs = GRAV * (de + (a.d - b.d)) * rcp_approx(f.S);    // c_a - c_b
     f.dw = a.w - b.w;
     f.sw = a.w + b.w;
     f.dtt = a.t - b.t;
@@ -138,10 +139,10 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     if (F.mode == 2) {
         wC += gadt;
     } else if (F.mode == 1 && F.s > 0.f) {
-        const float G = gadt * K.dt_gn2 * F.hm;
-        wC += G * (F.s + C.w * C.w / F.s);
-        tC += G * C.w * C.t / F.s;
-        eC += G * C.w * F.s * (-4.f / 3.f) / (C.e + C.d);
+        const float G = gadt * K.dt_gn2 * F.hm, rs = rcp_approx(F.s);
+        wC += G * (F.s + C.w * C.w * rs);
+        tC += G * C.w * C.t * rs;
+        eC += G * C.w * F.s * (-4.f / 3.f) * rcp_approx(C.e + C.d);
     }
     if (SRC) {
         const float gs = (gdp - gdq) * m.sdt;
@@ -172,11 +173,11 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
         bR.t += T * 0.5f * fr.sw;
         tC -= T * 0.5f * fr.sw;
     }
-    bC.e += eC + cC * 0.5f * GRAV / C.c;
+    bC.e += eC + cC * (0.5f * GRAV) * rcp_approx(C.c);
     bC.w += wC;
     bC.t += tC;
-    bL.e += cL * 0.5f * GRAV / L.c;
-    bR.e += cR * 0.5f * GRAV / R.c;
+    bL.e += cL * (0.5f * GRAV) * rcp_approx(L.c);
+    bR.e += cR * (0.5f * GRAV) * rcp_approx(R.c);
 }
 
 // neighbours across the window: node 0 of a lane is window node 2*lane, node 1 is 2*lane+1
