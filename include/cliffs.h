@@ -258,6 +258,15 @@ int cliffs_read_boundary(cliffs_grid* g, int nest, int edge, double* vals, int64
 /* Current state of one scenario, [ny][nx] each; any pointer may be NULL. */
 int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float* v);
 
+/* The current state of one scenario as library-owned device memory, for zero-copy views
+ * (section "Running Options": the wave state the screenshots hold): eta, u, v point to
+ * [ny] rows of *pitch floats (the first nx of each row are the nodes). The grid alternates
+ * two state buffers, so the pointers are valid until the next call that steps or sets the
+ * state; writing through them changes the state the next step starts from. Any output
+ * pointer may be NULL. Errors: ERR_ARG (scenario out of range). */
+int cliffs_state_ptrs(cliffs_grid* g, int scenario, float** eta, float** u, float** v, int64_t* pitch);
+
+
 /* Kernel timing: enable != 0 records CUDA events around every sweep kernel launch (on the
  * grid's stream) from now on; *ms and *launches (either may be NULL) receive the total
  * device time and count of those launches since timing was enabled or last reset; the call

@@ -28,7 +28,7 @@ __all__ = [
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
-    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "EXPORTED",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -42,7 +42,7 @@ EXPORTED = [
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
-    "cliffs_adjoint_record", "cliffs_adjoint_recorded",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs",
 ]
 
 
@@ -90,6 +90,8 @@ def lib():
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
+            "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                   C.POINTER(C.c_int64)], C.c_int),
             "cliffs_adjoint_recorded": ([vp, vp, vp], C.c_int),
             "cliffs_set_boundary_input": ([vp, C.c_int, vp, C.c_int64, vp], C.c_int),
             "cliffs_set_boundary_clock": ([vp, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
@@ -214,6 +216,23 @@ def cliffs_adjoint_n(g, n, checkpoint_every, dL_dgauges, out):
     gauge-eta adjoint seed ``dL_dgauges`` ([n // gout + 1][G] float32, or None)."""
     ps, ks = _ptr(dL_dgauges, np.float32)
     _check(lib().cliffs_adjoint_n(g, int(n), int(checkpoint_every), ps, _out_ptr(out)))
+
+
+def cliffs_state_ptrs(g, scenario):
+    """(eta, u, v device addresses, pitch in floats) of a scenario's current state."""
+    e, u, v = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    p = C.c_int64()
+    _check(lib().cliffs_state_ptrs(g, int(scenario), C.byref(e), C.byref(u), C.byref(v), C.byref(p)))
+    return e.value, u.value, v.value, p.value
+
+
+class _DeviceArray:
+    """A [ny][nx] FP32 view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr, ny, nx, pitch, owner):
+        self.__cuda_array_interface__ = {"shape": (ny, nx), "strides": (4 * pitch, 4), "typestr": "<f4",
+                                         "data": (ptr, False), "version": 2}
+        self.owner = owner
 
 
 def cliffs_adjoint_record(g, checkpoint_every):
@@ -408,6 +427,14 @@ class CliffsGrid:
         v = np.empty_like(e)
         cliffs_read_state(self.h, scenario, e, u, v)
         return e, u, v
+
+    def state_views(self, scenario=0):
+        """Zero-copy torch views (eta, u, v) of the current state on the device, [ny][nx] with
+        row stride pitch; valid until the next step or set_initial (the state buffers
+        alternate)."""
+        import torch
+        e, u, v, p = cliffs_state_ptrs(self.h, scenario)
+        return tuple(torch.as_tensor(_DeviceArray(a, self.ny, self.nx, p, self), device="cuda") for a in (e, u, v))
 
     def kernel_time(self, enable=1):
         return cliffs_kernel_time(self.h, enable)

@@ -1709,6 +1709,19 @@ int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float*
     return CLIFFS_OK;
 }
 
+int cliffs_state_ptrs(cliffs_grid* g, int scenario, float** eta, float** u, float** v, int64_t* pitch) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    const int cb = (int)cur_buf(g, scenario);
+    const size_t o = (size_t)scenario * g->plane;
+    if (eta) *eta = g->eta[cb] + o;
+    if (u) *u = g->u[cb] + o;
+    if (v) *v = g->v[cb] + o;
+    if (pitch) *pitch = g->pitch;
+    return CLIFFS_OK;
+}
+
 int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");

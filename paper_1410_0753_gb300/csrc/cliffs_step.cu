@@ -10,10 +10,15 @@
 //                finishes the y-sweep three rows behind. The step reads eta, u, v, d and
 //                writes eta, u, v once per cell (28 B/cell-update plus the halo), fused with
 //                the max-wave update (+8 B) and the gauge / enclosed-grid sampling.
+//  k_batch       the same per-warp work in a persistent cooperative kernel that loops over
+//                the steps of a batch of scenarios, with a grid barrier between steps.
 //  k_xsweep      x-sweep alone (1D grids along x).
 //  k_ysweep      y-sweep alone (1D grids along y).
-// Every mbarrier wait is bounded (about a second of clock); on expiry the warp raises the
-// timeout flag, drains the copies it issued (again bounded) and returns.
+// Variants (template parameters): spherical metric (SPH), friction on (FRIC), a y-first step
+// of the alternating order (YF, fused step only) and eq. (solver1) (S1); the launchers pick
+// one from kernel tables. Every mbarrier wait and the grid barrier are bounded (about a
+// second of clock); on expiry the warp raises the timeout flag, drains the copies it issued
+// (again bounded) and returns.
 #include "internal.h"
 #include "sweep.cuh"
 

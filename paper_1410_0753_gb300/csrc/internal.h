@@ -7,11 +7,6 @@
 
 namespace cliffs {
 
-struct SweepConstH {       // mirror of SweepConst for host code
-    float hmin, dwall, half_dt, dt_gn2;
-    int transverse;
-};
-
 // Arguments of one sweep-kernel launch (all device pointers). Fields 2D are pitched:
 // element (b, r, c) lives at b * plane + r * pitch + c.
 struct StepArgs {

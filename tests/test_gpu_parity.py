@@ -418,3 +418,22 @@ def test_autotuned_tile_shape_gives_identical_results():
     for x, y in zip(s0 + m0, s1 + m1):
         assert np.array_equal(x, y)
     assert np.array_equal(g0, g1) and np.array_equal(b0, b1)
+
+
+def test_state_views_are_zero_copy():
+    """cliffs_state_ptrs: torch views of the library's current state buffers equal
+    read_state, follow the alternating buffers, and writes through them are the state."""
+    w = workloads.beach_200(100, 70, steps=6)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    for n in (3, 1):                                   # both buffers of the pair
+        g.step(n)
+        views = g.state_views()
+        for v, s in zip(views, g.state()):
+            assert v.shape == (70, 100) and np.array_equal(v.cpu().numpy(), s)
+    e, u, v = g.state_views()
+    e.fill_(0.25)
+    u.zero_()
+    assert np.all(g.state()[0] == 0.25) and not g.state()[1].any()
+    g.close()
