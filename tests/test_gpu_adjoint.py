@@ -34,11 +34,25 @@ def _start(w, **kw):
     return g
 
 
+def _walls():
+    w = workloads.beach_200(200, 90, steps=400)
+    w.itopo, w.dwall = 0, 5.0                      # a vertical wall where the beach is shallower than 5 m
+    return w
+
+
+def _no_transverse():
+    w = workloads.inversion_1024(nx=128, ny=112, steps=120)
+    w.transverse, w.manning_n2 = 0, 0.0
+    return w
+
+
 def _cases():
     return {
         "inversion_slope": lambda: workloads.inversion_1024(nx=128, ny=112, steps=160),
-        "beach_runup": lambda: workloads.beach_200(120, 90, steps=120),
+        "beach_runup": lambda: workloads.beach_200(200, 90, steps=400),   # the wave runs up the shore
         "spherical_coast": lambda: workloads.spherical_coast(160, 150, steps=60),
+        "walls_itopo0": _walls,
+        "no_transverse_no_friction": _no_transverse,
     }
 
 
@@ -53,6 +67,8 @@ def test_adjoint_dot_product_against_oracle_tlm(case):
     seed = rng.standard_normal((nrec, G)).astype(np.float32)
     grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
     assert np.isfinite(grad).all()
+    if case in ("beach_runup", "walls_itopo0", "inversion_slope", "spherical_coast"):
+        assert (w.depth < (w.dwall if w.itopo == 0 else w.h_min)).any()   # dry land or walls in play
     d64 = P.f32(P.oracle_depth(w))
     p = oracle.params_from(w)
     yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")

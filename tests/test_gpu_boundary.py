@@ -66,9 +66,9 @@ def test_forced_run_against_the_oracle_on_a_beach():
     """A child straddling the shoreline of a beach, driven by the oracle parent's series:
     the GPU's forced run against the oracle's forced run."""
     from workloads import Nest
-    w = workloads.beach_200(160, 120, steps=150)
+    w = workloads.beach_200(200, 120, steps=400)
     d64 = P.f32(P.oracle_depth(w))
-    i0, j0, cx, cy = 70, 30, 90, 64                        # reaches past the shoreline
+    i0, j0, cx, cy = 110, 30, 90, 64                       # covers the shoreline (column 182)
     nest = Nest(float(w.x[i0]), float(w.y[j0]), 100.0, 100.0, cx, cy)
     p = oracle.params_from(w)
     par = oracle.run(p, w.x, w.y, d64, w.eta0, nsteps=w.steps, bndout=1, nests=[nest])

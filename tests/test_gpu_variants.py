@@ -34,7 +34,7 @@ def _run_both(w, n, **kw):
 @pytest.mark.parametrize("case", ["beach", "spherical"])
 def test_alternating_order_against_oracle(case):
     if case == "beach":
-        w = workloads.beach_200(120, 96, steps=240)
+        w = workloads.beach_200(200, 96, steps=400)          # the wave runs up the shore
     else:
         w = workloads.spherical_coast(220, 190, steps=160)
         w.nests = []
@@ -86,7 +86,7 @@ def test_solver1_against_oracle(case):
     and spherical grids, with the alternating order, and on 1D lines along x and along y."""
     alt = 0
     if case == "beach":
-        w = workloads.beach_200(120, 96, steps=240)
+        w = workloads.beach_200(200, 96, steps=400)          # the wave runs up the shore
     elif case == "spherical_alternate":
         w = workloads.spherical_coast(220, 190, steps=160)
         w.nests = []
