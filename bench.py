@@ -315,6 +315,7 @@ def run_cuda(args, world, rank, local):
     import torch
     import workloads
     from paper_1410_0753_gb300 import CliffsGrid, _build
+    from paper_1410_0753_gb300.ranks import max_over_ranks
 
     if world > 1:
         import torch.distributed as dist
@@ -354,10 +355,7 @@ def run_cuda(args, world, rank, local):
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     ms, launches = g.kernel_time(0)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms)
     ms_step = ms_max / args.steps
     value = world * w.cells * args.steps / (ms_max / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
@@ -388,11 +386,7 @@ def run_cuda(args, world, rank, local):
                 cliffs_read_boundary(g.h, m, e, pin_b[m][e].numpy())
         torch.cuda.synchronize()
         barrier()
-        te = time.perf_counter() - t
-        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te_t, op=torch.distributed.ReduceOp.MAX)
-        te = float(te_t.item())
+        te = max_over_ranks(time.perf_counter() - t)
         d2h = pin_g.numel() * 4 + 2 * pin_em.numel() * 4 + sum(b.numel() * 8 for bb in pin_b for b in bb)
         e2e = {"value": world * w.cells * args.steps / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": pin_eta.numel() * 4 / args.steps,
