@@ -15,8 +15,9 @@
 //                 written transposed for the next step's y-sweep adjoint.
 // A warp holds 64 nodes of a line (two per lane); each stage of the sweep needs its line
 // neighbours once, so after the six stages (b), (d), the tests of (e), and the adjoints of
-// (e), (d) and (b), the middle 52 nodes are exact. A block stages its 32 lines x 52 nodes
-// in shared memory and writes them transposed, so every load and store is coalesced.
+// (e), (d) and (b), the middle 52 nodes are exact. A block stages its 8 lines x 52 nodes
+// in shared memory and writes them transposed (32-byte segments), so every load and store is
+// coalesced; blocks this small keep the last partial wave of the grid short.
 //
 // Derivatives are taken on the perturbation form used by the forward kernels (eta kept,
 // c_a - c_b = g (eta_a - eta_b + d_a - d_b)/(c_a + c_b)), which keeps the coefficients
@@ -29,8 +30,8 @@ namespace cliffs {
 
 constexpr int AHALO = 6;                    // nodes of a window without their full dependency
 constexpr int AOUT = XWIN - 2 * AHALO;      // nodes a window finishes
-constexpr int ALINES = 32;                  // lines per block
-constexpr int AWARPS = 8;                   // warps per block (4 lines each)
+constexpr int ALINES = 8;                   // lines per block (one per warp: a short tail wave)
+constexpr int AWARPS = 8;                   // warps per block
 constexpr int TP = ALINES + 1;              // shared tile pitch (no bank conflicts)
 
 struct ANode { float e, w, t, d, c; };      // post-(b) state of a node or of a mirror ghost
@@ -180,6 +181,140 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     bR.e += cR * (0.5f * GRAV) * rcp_approx(R.c);
 }
 
+// ------------------------------------------------------------------ packed open water
+// The same adjoint of (d) for the two nodes of a lane at once (packed FP32x2), for windows
+// where every node is wet: real neighbours, no ghosts.
+__device__ __forceinline__ float2 rcp2(float2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
+
+struct N2 { float2 e, w, t, d, c; };
+struct AIface2 { float2 dw, dcs, sw, S, dtt, qp, qq, qt; };
+
+__device__ __forceinline__ AIface2 a_iface2(const N2& b, const N2& a) {
+    AIface2 f;
+    const float2 de = sub2(a.e, b.e);
+    f.S = add2(a.c, b.c);
+    f.dcs = mul2(mul2(v2(GRAV), add2(de, sub2(a.d, b.d))), rcp2(f.S));
+    f.dw = sub2(a.w, b.w);
+    f.sw = add2(a.w, b.w);
+    f.dtt = sub2(a.t, b.t);
+    const float2 y = mul2(f.sw, f.dcs), z = mul2(v2(GRAV), de), hdw = mul2(v2(0.5f), f.dw);
+    f.qp = fma2(hdw, add2(f.sw, f.S), add2(z, y));
+    f.qq = fma2(hdw, sub2(f.sw, f.S), sub2(z, y));
+    f.qt = mul2(mul2(v2(0.5f), f.sw), f.dtt);
+    return f;
+}
+
+// unclamped-friction part of the adjoint for one node
+__device__ __forceinline__ void fric_adj1(float gadt, float w, float t, float e, float d, float s, float hm,
+                                          bool clamped, const SweepConst& K, float& wC, float& tC, float& eC) {
+    if (clamped) {
+        wC += gadt;
+    } else if (s > 0.f) {
+        const float G = gadt * K.dt_gn2 * hm, rs = rcp_approx(s);
+        wC += G * (s + w * w * rs);
+        tC += G * w * t * rs;
+        eC += G * w * s * (-4.f / 3.f) * rcp_approx(e + d);
+    }
+}
+
+template <bool SRC>
+__device__ __forceinline__ void a_dstage_adj2(const N2& L, const N2& C, const N2& R, float2 il, float2 ir,
+                                              float2 k2, float2 sdt, const SweepConst& K, float2 ge, float2 gw,
+                                              float2 gt, float2 (&bL)[3], float2 (&bC)[3], float2 (&bR)[3]) {
+    const AIface2 fl = a_iface2(L, C), fr = a_iface2(C, R);
+    const float2 QpL = mul2(fl.qp, il), QpR = mul2(fr.qp, ir), QqL = mul2(fl.qq, il), QqR = mul2(fr.qq, ir);
+    const float2 QtL = mul2(fl.qt, il), QtR = mul2(fr.qt, ir);
+    const float2 nh = v2(-K.half_dt);
+    const float2 lp = add2(C.w, C.c), lq = sub2(C.w, C.c);
+    const float2 dQp = sub2(QpR, QpL), dQq = sub2(QqR, QqL);
+    float2 dp = fma2(mul2(lp, k2), dQp, mul2(nh, add2(QpL, QpR)));
+    float2 dq = fma2(mul2(lq, k2), dQq, mul2(nh, add2(QqL, QqR)));
+    float2 s = v2(0.f), hm = v2(0.f);
+    bool clA = false, clB = false;
+    const bool fric = K.dt_gn2 > 0.f;
+    if (fric) {
+        const float2 s2 = fma2(C.w, C.w, mul2(C.t, C.t));
+        s = make_float2(s2.x * rsqrt_approx(fmaxf(s2.x, 1e-30f)), s2.y * rsqrt_approx(fmaxf(s2.y, 1e-30f)));
+        const float2 h = add2(C.e, C.d);
+        hm = make_float2(pow_m43(h.x), pow_m43(h.y));
+        float2 adt = mul2(mul2(mul2(v2(K.dt_gn2), C.w), s), hm);
+        clA = fabsf(adt.x) > fabsf(C.w.x);
+        clB = fabsf(adt.y) > fabsf(C.w.y);
+        if (clA) adt.x = C.w.x;
+        if (clB) adt.y = C.w.y;
+        dp = sub2(dp, adt);
+        dq = sub2(dq, adt);
+    }
+    if (SRC) {
+        const float2 sw_ = mul2(mul2(sdt, C.c), C.w);
+        dp = add2(dp, sw_);
+        dq = sub2(dq, sw_);
+    }
+    const float2 dcn = mul2(v2(0.25f), sub2(dp, dq));
+    // reverse sweep
+    float2 eC = ge, wC = gw, tC = gt;
+    float2 cC = mul2(ge, mul2(v2(2.f * INV_GRAV), dcn));
+    const float2 gdcn = mul2(ge, mul2(v2(2.f * INV_GRAV), add2(C.c, dcn)));
+    const float2 gdp = fma2(v2(0.5f), gw, mul2(v2(0.25f), gdcn));
+    const float2 gdq = fma2(v2(0.5f), gw, mul2(v2(-0.25f), gdcn));
+    float2 gQtL = v2(0.f), gQtR = v2(0.f);
+    if (K.transverse) {
+        const float2 wk = mul2(C.w, k2);
+        gQtL = mul2(gt, sub2(nh, wk));
+        gQtR = mul2(gt, add2(nh, wk));
+        wC = fma2(mul2(gt, k2), sub2(QtR, QtL), wC);
+    }
+    const float2 lpk = mul2(lp, k2), lqk = mul2(lq, k2);
+    const float2 gQpL = mul2(gdp, sub2(nh, lpk)), gQpR = mul2(gdp, add2(nh, lpk));
+    const float2 gQqL = mul2(gdq, sub2(nh, lqk)), gQqR = mul2(gdq, add2(nh, lqk));
+    const float2 glp = mul2(mul2(gdp, k2), dQp), glq = mul2(mul2(gdq, k2), dQq);
+    wC = add2(wC, add2(glp, glq));
+    cC = add2(cC, sub2(glp, glq));
+    if (fric) {
+        const float2 gadt = mul2(v2(-1.f), add2(gdp, gdq));
+        fric_adj1(gadt.x, C.w.x, C.t.x, C.e.x, C.d.x, s.x, hm.x, clA, K, wC.x, tC.x, eC.x);
+        fric_adj1(gadt.y, C.w.y, C.t.y, C.e.y, C.d.y, s.y, hm.y, clB, K, wC.y, tC.y, eC.y);
+    }
+    if (SRC) {
+        const float2 gs = mul2(sub2(gdp, gdq), sdt);
+        cC = fma2(gs, C.w, cC);
+        wC = fma2(gs, C.c, wC);
+    }
+    float2 cL, cR;
+    {   // left interface: b = L, a = C
+        const float2 A = mul2(gQpL, il), B = mul2(gQqL, il), T = mul2(gQtL, il);
+        const float2 hp = fma2(v2(0.5f), fl.dw, fl.dcs), hq = fma2(v2(0.5f), fl.dw, mul2(v2(-1.f), fl.dcs));
+        const float2 sp = add2(fl.sw, fl.S), sq = sub2(fl.sw, fl.S);
+        const float2 hsp = mul2(v2(0.5f), sp), hsq = mul2(v2(0.5f), sq);
+        const float2 tdt = mul2(mul2(v2(0.5f), T), fl.dtt), tsw = mul2(mul2(v2(0.5f), T), fl.sw);
+        wC = add2(wC, fma2(A, add2(hp, hsp), fma2(B, add2(hq, hsq), tdt)));
+        bL[1] = fma2(A, sub2(hp, hsp), fma2(B, sub2(hq, hsq), tdt));
+        cC = add2(cC, sub2(mul2(A, add2(hp, sp)), mul2(B, add2(hq, sq))));
+        cL = sub2(mul2(A, sub2(hp, sp)), mul2(B, sub2(hq, sq)));
+        tC = add2(tC, tsw);
+        bL[2] = mul2(v2(-1.f), tsw);
+    }
+    {   // right interface: b = C, a = R
+        const float2 A = mul2(gQpR, ir), B = mul2(gQqR, ir), T = mul2(gQtR, ir);
+        const float2 hp = fma2(v2(0.5f), fr.dw, fr.dcs), hq = fma2(v2(0.5f), fr.dw, mul2(v2(-1.f), fr.dcs));
+        const float2 sp = add2(fr.sw, fr.S), sq = sub2(fr.sw, fr.S);
+        const float2 hsp = mul2(v2(0.5f), sp), hsq = mul2(v2(0.5f), sq);
+        const float2 tdt = mul2(mul2(v2(0.5f), T), fr.dtt), tsw = mul2(mul2(v2(0.5f), T), fr.sw);
+        bR[1] = fma2(A, add2(hp, hsp), fma2(B, add2(hq, hsq), tdt));
+        wC = add2(wC, fma2(A, sub2(hp, hsp), fma2(B, sub2(hq, hsq), tdt)));
+        cR = sub2(mul2(A, add2(hp, sp)), mul2(B, add2(hq, sq)));
+        cC = add2(cC, sub2(mul2(A, sub2(hp, sp)), mul2(B, sub2(hq, sq))));
+        bR[2] = tsw;
+        tC = sub2(tC, tsw);
+    }
+    const float2 hg = v2(0.5f * GRAV);
+    bC[0] = fma2(mul2(cC, hg), rcp2(C.c), eC);
+    bC[1] = wC;
+    bC[2] = tC;
+    bL[0] = mul2(mul2(cL, hg), rcp2(L.c));
+    bR[0] = mul2(mul2(cR, hg), rcp2(R.c));
+}
+
 // neighbours across the window: node 0 of a lane is window node 2*lane, node 1 is 2*lane+1
 __device__ __forceinline__ void nbr(const float (&x)[2], float (&l)[2], float (&r)[2]) {
     l[0] = __shfl_up_sync(FULL, x[1], 1);
@@ -216,20 +351,21 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         for (int i = 0; i < 2; ++i) c[i] = wave_speed(e[i] + d[i]);
         float eL[2], eR[2], wL[2], wR[2], tL[2], tR[2], dL[2], dR[2], cL[2], cR[2];
         nbr(e, eL, eR); nbr(w, wL, wR); nbr(t, tL, tR); nbr(d, dL, dR); nbr(c, cL, cR);
-        ABar bL[2], bC[2], bR[2];
+        auto f2 = [](const float (&x)[2]) { return make_float2(x[0], x[1]); };
+        const N2 Ln{f2(eL), f2(wL), f2(tL), f2(dL), f2(cL)}, Cn{f2(e), f2(w), f2(t), f2(d), f2(c)};
+        const N2 Rn{f2(eR), f2(wR), f2(tR), f2(dR), f2(cR)};
+        float2 bL[3], bC[3], bR[3];
+        a_dstage_adj2<SRC>(Ln, Cn, Rn, make_float2(m[0].il, m[1].il), make_float2(m[0].ir, m[1].ir),
+                           make_float2(m[0].k2, m[1].k2), make_float2(m[0].sdt, m[1].sdt), K, f2(ge), f2(gw),
+                           f2(gt), bL, bC, bR);
+        // node A gathers from B's left part and lane-1's B's right part; B from A's right
+        // part and lane+1's A's left part
+        float* out[3] = {oe, ow, ot};
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            bL[i] = bC[i] = bR[i] = ABar{0.f, 0.f, 0.f};
-            a_dstage_adj<SRC>(ANode{eL[i], wL[i], tL[i], dL[i], cL[i]}, ANode{e[i], w[i], t[i], d[i], c[i]},
-                              ANode{eR[i], wR[i], tR[i], dR[i], cR[i]}, m[i], K, ge[i], gw[i], gt[i],
-                              bL[i], bC[i], bR[i]);
+        for (int f = 0; f < 3; ++f) {
+            out[f][0] = bC[f].x + bL[f].y + __shfl_up_sync(FULL, bR[f].y, 1);
+            out[f][1] = bC[f].y + bR[f].x + __shfl_down_sync(FULL, bL[f].x, 1);
         }
-        oe[0] = bC[0].e + bL[1].e + __shfl_up_sync(FULL, bR[1].e, 1);
-        ow[0] = bC[0].w + bL[1].w + __shfl_up_sync(FULL, bR[1].w, 1);
-        ot[0] = bC[0].t + bL[1].t + __shfl_up_sync(FULL, bR[1].t, 1);
-        oe[1] = bC[1].e + bR[0].e + __shfl_down_sync(FULL, bL[0].e, 1);
-        ow[1] = bC[1].w + bR[0].w + __shfl_down_sync(FULL, bL[0].w, 1);
-        ot[1] = bC[1].t + bR[0].t + __shfl_down_sync(FULL, bL[0].t, 1);
         return;
     }
     // (b) flooding from the wetter neighbour (left on a tie), start-of-sweep values
