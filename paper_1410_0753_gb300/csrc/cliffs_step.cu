@@ -92,15 +92,6 @@ __device__ __forceinline__ void load_pair(const StepArgs& a, size_t boff, int r,
     }
 }
 
-// max-wave update of one node (section "Running Options", field maxout): wet nodes only
-__device__ __forceinline__ void max_upd(float& em, float& sm, float e, float u, float v,
-                                        float d, const StepArgs& a, bool& ch) {
-    if (!((d >= a.dwall) && (e + d >= a.hmin))) return;
-    if (e > em) { em = e; ch = true; }
-    const float s2 = fmaf(u, u, v * v);
-    if (s2 > sm * sm) { sm = fmaxf(sm, s2 * rsqrt_approx(fmaxf(s2, 1e-30f))); ch = true; }
-}
-
 __device__ __forceinline__ int runaway(float e, float u, float v) {
     return !(fabsf(e) + fabsf(u) + fabsf(v) < 3e5f);
 }
@@ -122,8 +113,10 @@ __device__ __forceinline__ StepOut step_out(const StepMaps* M, const StepArgs& a
     return StepOut{M, a.eta_out, a.u_out, a.v_out, a.emax, a.smax, a.rec_g, a.rec_n};
 }
 
-// Store a finished pair of nodes of row r. With max-wave due, (em, sm) hold the stored
-// maxima of the pair (loaded beforehand) and are written back where they grow.
+// Store a finished pair of nodes of row r. With max-wave due (section "Running Options",
+// field maxout), (em, sm) hold the stored maxima of the pair (loaded beforehand); on wet
+// nodes they take the new eta and speed sqrt(u^2 + v^2) where these are larger and are
+// written back.
 __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, size_t o, bool va, bool vb,
                                           float2 E, float2 U, float2 V, float2 D,
                                           float2 em, float2 sm, int& bad) {
@@ -138,10 +131,19 @@ __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, s
         bad |= runaway(E.x, U.x, V.x);
     }
     if (O.emax) {
-        bool ch = false;
-        max_upd(em.x, sm.x, E.x, U.x, V.x, D.x, a, ch);
-        if (vb) max_upd(em.y, sm.y, E.y, U.y, V.y, D.y, a, ch);
-        if (ch) {
+        // max-wave of the pair (wet nodes only), the tests in packed form
+        const float2 h = add2(E, D);
+        const float2 s2 = fma2(U, U, mul2(V, V));
+        const float2 sm2 = mul2(sm, sm);
+        const bool wA = (D.x >= a.dwall) && (h.x >= a.hmin);
+        const bool wB = vb && (D.y >= a.dwall) && (h.y >= a.hmin);
+        const bool eA = wA && E.x > em.x, eB = wB && E.y > em.y;
+        const bool sA = wA && s2.x > sm2.x, sB = wB && s2.y > sm2.y;
+        if (eA || eB || sA || sB) {
+            if (eA) em.x = E.x;
+            if (eB) em.y = E.y;
+            if (sA) sm.x = fmaxf(sm.x, s2.x * rsqrt_approx(fmaxf(s2.x, 1e-30f)));
+            if (sB) sm.y = fmaxf(sm.y, s2.y * rsqrt_approx(fmaxf(s2.y, 1e-30f)));
             if (vb) {
                 *reinterpret_cast<float2*>(O.emax + o) = em;
                 *reinterpret_cast<float2*>(O.smax + o) = sm;
