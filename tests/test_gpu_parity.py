@@ -437,3 +437,70 @@ def test_state_views_are_zero_copy():
     u.zero_()
     assert np.all(g.state()[0] == 0.25) and not g.state()[1].any()
     g.close()
+
+
+# ---------------------------------------------------------------------------- degenerate cases
+
+def _run_pair(x, y, d, eta, steps, u=None, **kw):
+    """GPU and oracle on the same small grid (no depth filter); returns (gpu state, oracle run)."""
+    nx, ny = len(x), len(y)
+    dt = kw.pop("dt")
+    g = CliffsGrid(nx, ny, dt, **kw)
+    g.set_bathy(x, y, d, False)
+    g.set_initial(eta.astype(np.float32), None if u is None else u.astype(np.float32))
+    g.step(steps)
+    st = g.state()
+    g.close()
+    p = oracle.params(nx, ny, dt, **{k: v for k, v in kw.items() if k in ("h_min", "manning_n2", "itopo", "dwall")})
+    o = oracle.run(p, x, y, P.f32(d), P.f32(eta), None if u is None else P.f32(u), None, nsteps=steps)
+    return st, o
+
+
+@pytest.mark.parametrize("case", ["all_land", "single_wet_cell", "exact_threshold", "flood_tie", "walls_only"])
+def test_degenerate_cases_against_oracle(case):
+    """Inputs at the method's edges, with dyadic values so that FP32 and FP64 take the same
+    decisions: an all-dry grid (nothing moves, velocities forced to zero), a single wet cell
+    in a dry basin, a node exactly at h = h_min (wet, reading 1), a dry node between two wet
+    neighbours of equal eta (reading 2: the left one wins, visible in the copied velocity),
+    and a grid of vertical walls only (itopo = 0)."""
+    n = 24
+    x = 8.0 * np.arange(n)
+    y = 8.0 * np.arange(n)
+    kw = dict(dt=0.25, h_min=0.125, manning_n2=0.0)
+    u = None
+    if case == "all_land":
+        d = np.full((n, n), -2.0)
+        eta = np.full((n, n), 0.5)
+        u = np.full((n, n), 0.75)
+    elif case == "single_wet_cell":
+        d = np.full((n, n), -1.0)
+        d[12, 12] = 4.0
+        eta = np.zeros((n, n))
+        eta[12, 12] = 0.5
+    elif case == "exact_threshold":
+        d = np.full((n, n), 4.0)
+        d[:, 16:] = -0.125
+        eta = np.zeros((n, n))
+        eta[:, 16] = 0.25                         # h = 0.25 - 0.125 = h_min exactly: wet
+    elif case == "flood_tie":
+        d = np.full((n, n), 4.0)
+        d[:, 12] = -1.0                           # a dry column between two wet ones
+        eta = np.full((n, n), 0.5)                # equal eta both sides: eta + d_i = -0.5 ...
+        d[:, 12] = 0.0                            # ... make it floodable: eta_j + d_i = 0.5 > h_min
+        eta[:, 12] = -0.5                         # dry: h = -0.5 < h_min
+        u = np.zeros((n, n))
+        u[:, 11] = 0.25                           # left neighbour moves right, right one left
+        u[:, 13] = -0.5
+    else:                                         # walls only
+        d = np.full((n, n), 2.0)
+        eta = 0.25 * np.ones((n, n))
+        kw.update(itopo=0, dwall=3.0)
+    st, o = _run_pair(x, y, d, eta, 6, u, **kw)
+    for a, b in zip(st, (o["eta"], o["u"], o["v"])):
+        assert np.allclose(a, b, rtol=0, atol=1e-6), np.abs(a - b).max()
+    if case == "all_land" or case == "walls_only":
+        assert np.array_equal(st[0], eta.astype(np.float32)) and not st[1].any() and not st[2].any()
+    if case == "flood_tie":
+        s1, o1 = _run_pair(x, y, d, eta, 1, u, **dict(kw))
+        assert np.all(o1["u"][:, 12] != 0.0)     # the flooded column took a neighbour's velocity
+        assert np.allclose(s1[1][:, 12], o1["u"][:, 12], rtol=0, atol=1e-6)
