@@ -214,6 +214,12 @@ int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every);
  * least one step; otherwise as cliffs_adjoint_n. */
 int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_deta0);
 
+/* The rest of the last adjoint's result: dL/du and dL/dv of the initial state ([ny][nx] each,
+ * host or device; either may be NULL), for the loss whose gauge-eta derivative the last
+ * successful cliffs_adjoint_n or cliffs_adjoint_recorded call was given. Errors: ERR_STATE
+ * when no adjoint has run. */
+int cliffs_adjoint_velocity(cliffs_grid* g, float* dL_du0, float* dL_dv0);
+
 /* Choose the tile shape of the 2D step kernel by measurement (the rows S each warp of the
  * fused step owns: a warp walks S + 6 rows, so larger S means less halo work but fewer,
  * longer warps, and the count of warps against the resident slots decides the tail). Each

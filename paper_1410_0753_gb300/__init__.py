@@ -28,7 +28,8 @@ __all__ = [
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
-    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "EXPORTED",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
+    "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -42,7 +43,7 @@ EXPORTED = [
     "cliffs_destroy", "cliffs_last_error", "cliffs_abi_version", "cliffs_depth_filter_noalloc",
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
-    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs",
+    "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
 ]
 
 
@@ -93,6 +94,7 @@ def lib():
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
             "cliffs_adjoint_recorded": ([vp, vp, vp], C.c_int),
+            "cliffs_adjoint_velocity": ([vp, vp, vp], C.c_int),
             "cliffs_set_boundary_input": ([vp, C.c_int, vp, C.c_int64, vp], C.c_int),
             "cliffs_set_boundary_clock": ([vp, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
             "cliffs_set_initial_interp": ([vp, C.c_int, vp, C.c_int32, vp, C.c_int32, vp, vp, vp, C.c_int], C.c_int),
@@ -242,6 +244,10 @@ def cliffs_adjoint_record(g, checkpoint_every):
 def cliffs_adjoint_recorded(g, dL_dgauges, out):
     ps, ks = _ptr(dL_dgauges, np.float32)
     _check(lib().cliffs_adjoint_recorded(g, ps, _out_ptr(out)))
+
+
+def cliffs_adjoint_velocity(g, du=None, dv=None):
+    _check(lib().cliffs_adjoint_velocity(g, _out_ptr(du), _out_ptr(dv)))
 
 
 def cliffs_set_boundary_input(g, edge, times, vals):
@@ -458,6 +464,13 @@ class CliffsGrid:
             out = np.empty((self.ny, self.nx), np.float32)
         cliffs_adjoint_recorded(self.h, dL_dgauges, out)
         return out
+
+    def adjoint_velocity(self):
+        """(dL/du0, dL/dv0) of the last adjoint call."""
+        du = np.empty((self.ny, self.nx), np.float32)
+        dv = np.empty_like(du)
+        cliffs_adjoint_velocity(self.h, du, dv)
+        return du, dv
 
     def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None):
         """Gradient with respect to the current free surface of a loss whose derivative with

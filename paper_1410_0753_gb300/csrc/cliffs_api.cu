@@ -339,6 +339,7 @@ struct cliffs_grid {
     float* rec_ckpt = nullptr;
     long long rec_cap = 0;
     long long rec_n = 0;
+    bool adj_done = false;                   // the adjoint state of the last adjoint call is kept
     std::vector<double> bnd_t[4];
     double* bnd_v[4] = {nullptr, nullptr, nullptr, nullptr};
     bool bnd_any = false;
@@ -1525,7 +1526,9 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
             if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
         }
     }
-    // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]
+    // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]; the u and v parts stay for
+    // cliffs_adjoint_velocity
+    g->adj_done = false;
     int rc = ensure_tmp(g, sizeof(float) * (size_t)nx * ny);
     if (rc) return rc;
     le = launch_transpose(LT, tp, (float*)g->tmp, nx, nx, ny, s);
@@ -1539,6 +1542,28 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
         if (h[0] & ERRF_TIMEOUT) return set_err(CLIFFS_ERR_TIMEOUT, "a bounded device wait gave up");
         return set_err(CLIFFS_ERR_UNSTABLE, "non-finite or runaway state in the forward recomputation");
     }
+    g->adj_done = true;
+    return CLIFFS_OK;
+}
+
+int cliffs_adjoint_velocity(cliffs_grid* g, float* dL_du0, float* dL_dv0) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->adj_done) return set_err(CLIFFS_ERR_STATE, "no adjoint has run");
+    const int nx = g->nx, ny = g->ny, tp = (ny + 31) / 32 * 32;
+    const long long TPL = (long long)tp * nx;
+    const float* LT = g->adj_t + 3 * TPL;
+    cudaStream_t s = g->stream;
+    int rc = ensure_tmp(g, sizeof(float) * (size_t)nx * ny);
+    if (rc) return rc;
+    float* outs[2] = {dL_du0, dL_dv0};
+    for (int f = 0; f < 2; ++f) {
+        if (!outs[f]) continue;
+        const cudaError_t le = launch_transpose(LT + (1 + f) * TPL, tp, (float*)g->tmp, nx, nx, ny, s);
+        if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "transpose: %s", cudaGetErrorString(le));
+        CK(cudaMemcpyAsync(outs[f], g->tmp, sizeof(float) * (size_t)nx * ny, cudaMemcpyDefault, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return CLIFFS_OK;
 }
 

@@ -245,3 +245,34 @@ def test_recorded_run_gradient_equals_the_checkpoint_pass_gradient():
     a2 = eta.grad.detach().cpu().numpy()
     assert np.array_equal(a1, ref) and np.array_equal(a2, ref)
     g.close()
+
+
+def test_adjoint_with_respect_to_initial_velocities():
+    """dL/du0 and dL/dv0 from the same adjoint run, against the oracle's tangent-linear model
+    along velocity directions (the dot-product identity)."""
+    w = workloads.inversion_1024(nx=128, ny=112, steps=100)
+    n = w.steps
+    g = _start(w)
+    with pytest.raises(CliffsError) as e:
+        g.adjoint_velocity()
+    assert e.value.code == ERR_STATE
+    rng = np.random.default_rng(23)
+    seed = rng.standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    g.adjoint(n, seed, checkpoint_every=30)
+    du, dv = g.adjoint_velocity()
+    g.close()
+    d64 = P.f32(P.oracle_depth(w))
+    p = oracle.params_from(w)
+    yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
+    z = np.zeros((w.ny, w.nx))
+    worst = 0.0
+    for k in range(2):
+        dirn = np.exp(-((xx - rng.uniform(30, 90)) ** 2 + (yy - rng.uniform(30, 80)) ** 2) / (2 * 12.0 ** 2))
+        args = (dict(du=dirn, dv=z), dict(du=z, dv=dirn))[k]
+        _, gtan, _, _ = oracle.run_tlm(p, w.x, w.y, d64, w.eta0, z, nsteps=n, gout=w.gout, gauges=w.gauges, **args)
+        terms = seed.astype(np.float64) * gtan
+        got = float(((du, dv)[k].astype(np.float64) * dirn).sum())
+        err = abs(got - terms.sum()) / max(np.abs(terms).max(), 1e-12)
+        worst = max(worst, err)
+        assert err <= DOT_RTOL, (k, got, terms.sum())
+    P.report("adjoint_dot_velocity", rel_err=worst)
