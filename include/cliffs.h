@@ -67,8 +67,7 @@ typedef struct cliffs_config {
     double  dwall;
     double  dt;                 /* time step, s; the CFL number |lambda| dt/dx must be <= 1 */
     int32_t transverse;         /* 1: advect the transverse velocity, eq. (pq3) */
-    int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) (not with
-                                   cliffs_adjoint_n) */
+    int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) */
     int32_t alternate;          /* 0: x then y every step; 1: y first on the odd steps
                                    (counted from 0 at set_initial), the alternating reading of
                                    section "Numerics"; cliffs_step_n only (the persistent run

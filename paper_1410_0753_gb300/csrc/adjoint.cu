@@ -76,14 +76,24 @@ __device__ __forceinline__ AFric a_friction(const ANode& C, const SweepConst& K)
 
 // (d) at a wet node C with neighbours L and R (mirror ghosts already substituted): the
 // new eta and w, which the tests of (e) compare.
-template <bool SRC>
+// With S1, eq. (solver1): the first-order term is dt Q(R, L) across the double interval
+// (1/(dx_{j-1} + dx_j) = k2 / dt^2) instead of dt/2 (Q_L + Q_R).
+template <bool SRC, bool S1>
 __device__ __forceinline__ void a_dstage(const ANode& L, const ANode& C, const ANode& R, const AMet& m,
                                          const SweepConst& K, float& e2, float& w2) {
     const AIface fl = a_iface(L, C), fr = a_iface(C, R);
     const float QpL = fl.qp * m.il, QpR = fr.qp * m.ir, QqL = fl.qq * m.il, QqR = fr.qq * m.ir;
     const float hdt = K.half_dt;
-    float dp = -hdt * (QpL + QpR) + (C.w + C.c) * m.k2 * (QpR - QpL);
-    float dq = -hdt * (QqL + QqR) + (C.w - C.c) * m.k2 * (QqR - QqL);
+    float dp, dq;
+    if (S1) {
+        const AIface flr = a_iface(L, R);
+        const float f = -2.f * hdt * m.k2 * K.inv_dt2;
+        dp = f * flr.qp + (C.w + C.c) * m.k2 * (QpR - QpL);
+        dq = f * flr.qq + (C.w - C.c) * m.k2 * (QqR - QqL);
+    } else {
+        dp = -hdt * (QpL + QpR) + (C.w + C.c) * m.k2 * (QpR - QpL);
+        dq = -hdt * (QqL + QqR) + (C.w - C.c) * m.k2 * (QqR - QqL);
+    }
     const AFric F = a_friction(C, K);
     dp -= F.adt;
     dq -= F.adt;
@@ -99,7 +109,7 @@ __device__ __forceinline__ void a_dstage(const ANode& L, const ANode& C, const A
 
 // Adjoint of (d) at a wet node: given the adjoints (ge, gw, gt) of its new (eta, w, t), add
 // the adjoints of the post-(b) states of L, C and R (c folded into eta by dc/deta = g/2c).
-template <bool SRC>
+template <bool SRC, bool S1>
 __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, const ANode& R, const AMet& m,
                                              const SweepConst& K, float ge, float gw, float gt,
                                              ABar& bL, ABar& bC, ABar& bR) {
@@ -108,8 +118,18 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     const float QtL = fl.qt * m.il, QtR = fr.qt * m.ir;
     const float hdt = K.half_dt;
     const float lp = C.w + C.c, lq = C.w - C.c;
-    float dp = -hdt * (QpL + QpR) + lp * m.k2 * (QpR - QpL);
-    float dq = -hdt * (QqL + QqR) + lq * m.k2 * (QqR - QqL);
+    AIface flr{};
+    float ilr = 0.f;
+    float dp, dq;
+    if (S1) {
+        flr = a_iface(L, R);
+        ilr = m.k2 * K.inv_dt2;
+        dp = -2.f * hdt * flr.qp * ilr + lp * m.k2 * (QpR - QpL);
+        dq = -2.f * hdt * flr.qq * ilr + lq * m.k2 * (QqR - QqL);
+    } else {
+        dp = -hdt * (QpL + QpR) + lp * m.k2 * (QpR - QpL);
+        dq = -hdt * (QqL + QqR) + lq * m.k2 * (QqR - QqL);
+    }
     const AFric F = a_friction(C, K);
     dp -= F.adt;
     dq -= F.adt;
@@ -123,16 +143,19 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     float eC = ge, wC = gw, tC = gt, cC = ge * 2.f * dcn * INV_GRAV, cL = 0.f, cR = 0.f;
     const float gdcn = ge * 2.f * (C.c + dcn) * INV_GRAV;
     const float gdp = 0.5f * gw + 0.25f * gdcn, gdq = 0.5f * gw - 0.25f * gdcn;
-    // t2 = t - dt/2 (QtL + QtR) + w k2 (QtR - QtL)   (eq. (pq3))
-    float gQtL = 0.f, gQtR = 0.f;
+    // t2 = t - dt/2 (QtL + QtR) + w k2 (QtR - QtL)   (eq. (pq3)); with S1 the first term is
+    // -dt Qt(R, L) over the double interval
+    const float hh = S1 ? 0.f : hdt;
+    float gQtL = 0.f, gQtR = 0.f, gF1t = 0.f;
     if (K.transverse) {
-        gQtL = gt * (-hdt - C.w * m.k2);
-        gQtR = gt * (-hdt + C.w * m.k2);
+        gQtL = gt * (-hh - C.w * m.k2);
+        gQtR = gt * (-hh + C.w * m.k2);
+        if (S1) gF1t = gt * (-2.f * hdt);
         wC += gt * m.k2 * (QtR - QtL);
     }
     // dp = -dt/2 (QpL + QpR) + (w + c) k2 (QpR - QpL) - adt + sdt c w, dq alike with w - c
-    const float gQpL = gdp * (-hdt - lp * m.k2), gQpR = gdp * (-hdt + lp * m.k2);
-    const float gQqL = gdq * (-hdt - lq * m.k2), gQqR = gdq * (-hdt + lq * m.k2);
+    const float gQpL = gdp * (-hh - lp * m.k2), gQpR = gdp * (-hh + lp * m.k2);
+    const float gQqL = gdq * (-hh - lq * m.k2), gQqR = gdq * (-hh + lq * m.k2);
     const float glp = gdp * m.k2 * (QpR - QpL), glq = gdq * m.k2 * (QqR - QqL);
     wC += glp + glq;
     cC += glp - glq;
@@ -173,6 +196,17 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
         cC += A * (hp - sp) - B * (hq - sq);
         bR.t += T * 0.5f * fr.sw;
         tC -= T * 0.5f * fr.sw;
+    }
+    if (S1) {   // the flux across the double interval: b = L, a = R
+        const float A = gdp * (-2.f * hdt) * ilr, B = gdq * (-2.f * hdt) * ilr, T = gF1t * ilr;
+        const float hp = 0.5f * flr.dw + flr.dcs, hq = 0.5f * flr.dw - flr.dcs;
+        const float sp = flr.sw + flr.S, sq = flr.sw - flr.S;
+        bR.w += A * (hp + 0.5f * sp) + B * (hq + 0.5f * sq) + T * 0.5f * flr.dtt;
+        bL.w += A * (hp - 0.5f * sp) + B * (hq - 0.5f * sq) + T * 0.5f * flr.dtt;
+        cR += A * (hp + sp) - B * (hq + sq);
+        cL += A * (hp - sp) - B * (hq - sq);
+        bR.t += T * 0.5f * flr.sw;
+        bL.t -= T * 0.5f * flr.sw;
     }
     bC.e += eC + cC * (0.5f * GRAV) * rcp_approx(C.c);
     bC.w += wC;
@@ -332,7 +366,7 @@ __device__ __forceinline__ void nbr(const int (&x)[2], int (&l)[2], int (&r)[2])
 // Adjoint of one sweep of a 64-node line window. In: the sweep's input (e, w, t, d) and the
 // adjoint (ge, gw, gt) of its output. Out: the adjoint of its input, exact at window
 // nodes 6..57.
-template <bool SRC>
+template <bool SRC, bool S1>
 __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&w)[2], const float (&t)[2],
                                              const float (&d)[2], const float (&ge)[2], const float (&gw)[2],
                                              const float (&gt)[2], const AMet (&m)[2], const SweepConst& K,
@@ -344,7 +378,7 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         fl[i] = d[i] >= K.dwall;
         o[i] = fl[i] && (e[i] + d[i] >= K.hmin);
     }
-    if (__all_sync(FULL, o[0] && o[1])) {
+    if (!S1 && __all_sync(FULL, o[0] && o[1])) {
         // every node of the window wet: no (b), no walls, no (e); only the stencil of (d)
         float c[2];
 #pragma unroll
@@ -412,7 +446,7 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         Rn[i] = wtR[i] ? ANode{e1R[i], w1R[i], t1R[i], dR[i], cR[i]} : G;
         if (wt[i]) {
             float ee, ww;
-            a_dstage<SRC>(Ln[i], Cn[i], Rn[i], m[i], K, ee, ww);
+            a_dstage<SRC, S1>(Ln[i], Cn[i], Rn[i], m[i], K, ee, ww);
             h2[i] = ee + d[i];
             w2[i] = ww;
         } else {
@@ -450,7 +484,7 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         bL[i] = bR[i] = ABar{0.f, 0.f, 0.f};
         if (wt[i]) {
             bC[i] = ABar{0.f, 0.f, 0.f};
-            a_dstage_adj<SRC>(Ln[i], Cn[i], Rn[i], m[i], K, De, Dw, gt[i], bL[i], bC[i], bR[i]);
+            a_dstage_adj<SRC, S1>(Ln[i], Cn[i], Rn[i], m[i], K, De, Dw, gt[i], bL[i], bC[i], bR[i]);
             if (!wtL[i]) {                       // the ghost mirrors C: (eta, -w, t)
                 bC[i].e += bL[i].e; bC[i].w -= bL[i].w; bC[i].t += bL[i].t;
                 bL[i] = ABar{0.f, 0.f, 0.f};
@@ -504,14 +538,14 @@ __device__ __forceinline__ void load2(const float* p, long long o, int pos, int 
 // Adjoint of the sweeps along one direction. DIR 0: lines are rows of row-major data and
 // the output is written transposed; DIR 1: lines are rows of transposed data (columns of
 // the grid) and the output is written row-major.
-template <int DIR, bool SPH>
+template <int DIR, bool SPH, bool S1>
 __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const AdjLineArgs A) {
     __shared__ float tile[3][AOUT][TP];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int strip = blockIdx.x, l0 = blockIdx.y * ALINES;
     const int p0 = strip * AOUT - AHALO;
     const int pA = p0 + 2 * lane;
-    const SweepConst K{A.hmin, A.dwall, A.half_dt, A.dt_gn2, A.transverse};
+    const SweepConst K{A.hmin, A.dwall, A.half_dt, A.dt_gn2, A.transverse, A.inv_dt2_s1};
     AMet mb[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -544,7 +578,7 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
             for (int i = 0; i < 2; ++i) { m[i].il *= f; m[i].ir *= f; m[i].k2 *= f; }
         }
         float oe[2], ow[2], ot[2];
-        line_adjoint<DIR == 1 && SPH>(e, w, t, d, ge, gw, gt, m, K, oe, ow, ot);
+        line_adjoint<DIR == 1 && SPH, S1>(e, w, t, d, ge, gw, gt, m, K, oe, ow, ot);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int q = 2 * lane + i - AHALO;
@@ -574,7 +608,7 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
 
 // The forward x-sweep of a stored state, written transposed ([nx][tpitch]): the same
 // window loads, edge treatment and sweep as the fused step kernel.
-template <bool SPH, bool FRIC>
+template <bool SPH, bool FRIC, bool S1>
 __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, const float* __restrict__ pe,
                                                           const float* __restrict__ pu,
                                                           const float* __restrict__ pv, float* te, float* tu,
@@ -583,7 +617,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int strip = blockIdx.x, r0 = blockIdx.y * ALINES;
     const int c0 = strip * XOUT - 4, cA = c0 + 2 * lane;
-    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse};
+    const SweepConst K{a.hmin, a.dwall, a.half_dt, a.dt_gn2, a.transverse, a.inv_dt2_s1};
     const bool colA = cA >= 0 && cA < a.nx, colB = cA + 1 >= 0 && cA + 1 < a.nx;
     float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
     if (colA) { il.x = a.xa[cA]; ir.x = a.xb[cA]; k2.x = a.xk[cA]; }
@@ -603,7 +637,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
             const float2 f = v2(a.xrow[r]);
             m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
         }
-        xsweep2<FRIC>(E, U, V, D, m, K, lane);
+        xsweep2<FRIC, S1>(E, U, V, D, m, K, lane);
         const float vals[3][2] = {{E.x, E.y}, {U.x, U.y}, {V.x, V.y}};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -648,28 +682,28 @@ __global__ void k_adj_seed(float* te, int tpitch, const int* gxy, int G, const f
 
 cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s) {
     const dim3 grid((A.npos + AOUT - 1) / AOUT, (A.nlines + ALINES - 1) / ALINES);
-    if (dir == 0) {
-        if (sph) k_adj_line<0, true><<<grid, AWARPS * 32, 0, s>>>(A);
-        else k_adj_line<0, false><<<grid, AWARPS * 32, 0, s>>>(A);
-    } else {
-        if (sph) k_adj_line<1, true><<<grid, AWARPS * 32, 0, s>>>(A);
-        else k_adj_line<1, false><<<grid, AWARPS * 32, 0, s>>>(A);
-    }
-    return cudaGetLastError();
+    static const void* const t[8] = {(const void*)k_adj_line<0, false, false>, (const void*)k_adj_line<0, true, false>,
+                                     (const void*)k_adj_line<1, false, false>, (const void*)k_adj_line<1, true, false>,
+                                     (const void*)k_adj_line<0, false, true>, (const void*)k_adj_line<0, true, true>,
+                                     (const void*)k_adj_line<1, false, true>, (const void*)k_adj_line<1, true, true>};
+    AdjLineArgs aa = A;
+    void* args[] = {&aa};
+    return cudaLaunchKernel(t[(sph ? 1 : 0) + (dir ? 2 : 0) + (A.inv_dt2_s1 > 0.f ? 4 : 0)], grid,
+                            dim3(AWARPS * 32), args, 0, s);
 }
 
 cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
                             float* tu, float* tv, int tpitch, cudaStream_t s) {
     const dim3 grid((a.nx + XOUT - 1) / XOUT, (a.ny + ALINES - 1) / ALINES);
-    const bool f = a.dt_gn2 > 0.f;
-    if (a.sph) {
-        if (f) k_adj_xfwd<true, true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
-        else k_adj_xfwd<true, false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
-    } else {
-        if (f) k_adj_xfwd<false, true><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
-        else k_adj_xfwd<false, false><<<grid, AWARPS * 32, 0, s>>>(a, e, u, v, te, tu, tv, tpitch);
-    }
-    return cudaGetLastError();
+    static const void* const t[8] = {
+        (const void*)k_adj_xfwd<false, false, false>, (const void*)k_adj_xfwd<true, false, false>,
+        (const void*)k_adj_xfwd<false, true, false>, (const void*)k_adj_xfwd<true, true, false>,
+        (const void*)k_adj_xfwd<false, false, true>, (const void*)k_adj_xfwd<true, false, true>,
+        (const void*)k_adj_xfwd<false, true, true>, (const void*)k_adj_xfwd<true, true, true>};
+    StepArgs aa = a;
+    void* args[] = {&aa, (void*)&e, (void*)&u, (void*)&v, &te, &tu, &tv, &tpitch};
+    return cudaLaunchKernel(t[(a.sph ? 1 : 0) + (a.dt_gn2 > 0.f ? 2 : 0) + (a.inv_dt2_s1 > 0.f ? 4 : 0)], grid,
+                            dim3(AWARPS * 32), args, 0, s);
 }
 
 cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,

@@ -1395,7 +1395,6 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
     if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes the x-then-y order only");
-    if (g->cfg.solver == 1) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes eq. (solver2) only");
     if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "the adjoint does not take boundary input");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
@@ -1508,6 +1507,7 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     for (AdjLineArgs* A : {&X, &Y}) {
         A->hmin = a.hmin; A->dwall = a.dwall; A->half_dt = a.half_dt; A->dt_gn2 = a.dt_gn2;
         A->transverse = a.transverse;
+        A->inv_dt2_s1 = a.inv_dt2_s1;
     }
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);

@@ -92,6 +92,7 @@ struct AdjLineArgs {
     const float* seed;               // dL/d eta at the gauges for this step, or null
     float hmin, dwall, half_dt, dt_gn2;
     int transverse;
+    float inv_dt2_s1;                // 1/dt^2 with eq. (solver1), else 0
 };
 
 cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s);

@@ -46,8 +46,15 @@ def _no_transverse():
     return w
 
 
+def _solver1():
+    w = workloads.beach_200(200, 90, steps=300)
+    w.extra["solver"] = 1                          # eq. (solver1), run-up included
+    return w
+
+
 def _cases():
     return {
+        "solver1_beach": _solver1,
         "inversion_slope": lambda: workloads.inversion_1024(nx=128, ny=112, steps=160),
         "beach_runup": lambda: workloads.beach_200(200, 90, steps=400),   # the wave runs up the shore
         "spherical_coast": lambda: workloads.spherical_coast(160, 150, steps=60),
@@ -60,17 +67,18 @@ def _cases():
 def test_adjoint_dot_product_against_oracle_tlm(case):
     w = _cases()[case]()
     n = w.steps
-    g = _start(w)
+    solver = w.extra.get("solver", 2)
+    g = _start(w, solver=solver)
     nrec = n // w.gout + 1
     G = len(w.gauges)
     rng = np.random.default_rng(17)
     seed = rng.standard_normal((nrec, G)).astype(np.float32)
     grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
     assert np.isfinite(grad).all()
-    if case in ("beach_runup", "walls_itopo0", "inversion_slope", "spherical_coast"):
+    if case in ("beach_runup", "walls_itopo0", "inversion_slope", "spherical_coast", "solver1_beach"):
         assert (w.depth < (w.dwall if w.itopo == 0 else w.h_min)).any()   # dry land or walls in play
     d64 = P.f32(P.oracle_depth(w))
-    p = oracle.params_from(w)
+    p = oracle.params_from(w, solver=solver)
     yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
     worst = 0.0
     for k in range(3):
