@@ -340,6 +340,8 @@ struct cliffs_grid {
     long long rec_cap = 0;
     long long rec_n = 0;
     bool adj_done = false;                   // the adjoint state of the last adjoint call is kept
+    float* adj_alt = nullptr;                // alternating order: y-swept state (3 row-major planes)
+                                             // and an intermediate adjoint (3 transposed planes)
     std::vector<double> bnd_t[4];
     double* bnd_v[4] = {nullptr, nullptr, nullptr, nullptr};
     bool bnd_any = false;
@@ -655,6 +657,7 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
     for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
     cudaFree(g->rec_ckpt);
+    cudaFree(g->adj_alt);
     if (g->cap) cudaStreamDestroy(g->cap);
     for (auto& e : g->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete g;
@@ -1361,6 +1364,7 @@ int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
     if (checkpoint_every < 0) return set_err(CLIFFS_ERR_ARG, "checkpoint_every must be >= 0");
     if (checkpoint_every == 0) {
         cudaFree(g->rec_ckpt);
+    cudaFree(g->adj_alt);
         g->rec_ckpt = nullptr;
         g->rec_cap = 0;
         g->rec_K = 0;
@@ -1385,6 +1389,48 @@ int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_d
     return adjoint_core(g, g->rec_n, g->rec_K, dL_dgauges, dL_deta0, g->rec_ckpt);
 }
 
+// Adjoint of a y-first step j of the alternating order, X_{j+1} = x-sweep(y-sweep(X_j)),
+// from lambda_{j+1} (transposed, in the second third of adj_t) to lambda_j in the same place:
+// the y-sweep of X_j is recomputed row-major, the x-sweep adjoint runs over it, then the
+// y-sweep adjoint over X_j transposed, with transposes where the layouts differ.
+static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineArgs& X, const AdjLineArgs& Y,
+                               const float* st, long long j, bool seeded) {
+    const int nx = g->nx, ny = g->ny, tp = (ny + 31) / 32 * 32;
+    const long long P = g->plane, TPL = (long long)tp * nx;
+    cudaStream_t s = g->stream;
+    if (!g->adj_alt) CK(cudaMalloc(&g->adj_alt, sizeof(float) * (3 * P + 3 * TPL)));
+    float* XT = g->adj_t;
+    float* LT = g->adj_t + 3 * TPL;
+    float* LB = g->adj_lb;
+    float* XR = g->adj_alt;
+    float* LT2 = g->adj_alt + 3 * P;
+    cudaError_t le = cudaSuccess;
+    for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // lambda_{j+1} row-major
+        le = launch_transpose(LT + f * TPL, tp, LB + f * P, g->pitch, nx, ny, s);
+    StepArgs ay = a;                                             // y-sweep of X_j
+    ay.eta_in = st; ay.u_in = st + P; ay.v_in = st + 2 * P;
+    ay.eta_out = XR; ay.u_out = XR + P; ay.v_out = XR + 2 * P;
+    ay.emax = ay.smax = nullptr; ay.rec_g = ay.rec_n = nullptr; ay.samp_ptr = nullptr; ay.limit = nullptr;
+    ay.nstrips = (nx + XWIN - 1) / XWIN; ay.S = 64; ay.nseg = (ny + 63) / 64;
+    if (le == cudaSuccess) le = launch_ysweep(ay, 1, s);
+    AdjLineArgs X2 = X;                                          // x-sweep adjoint over it
+    X2.pe = XR; X2.pw = XR + P; X2.pt = XR + 2 * P;
+    X2.oe = LT2; X2.ow = LT2 + TPL; X2.ot = LT2 + 2 * TPL;
+    X2.seed = nullptr;
+    if (le == cudaSuccess) le = launch_adj_line(X2, 0, a.sph, s);
+    for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // X_j transposed
+        le = launch_transpose(st + f * P, g->pitch, XT + f * TPL, tp, ny, nx, s);
+    AdjLineArgs Y2 = Y;                                          // y-sweep adjoint -> row-major
+    Y2.ge = LT2; Y2.gw = LT2 + 2 * TPL; Y2.gt = LT2 + TPL;
+    if (le == cudaSuccess) le = launch_adj_line(Y2, 1, a.sph, s);
+    for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // lambda_j transposed
+        le = launch_transpose(LB + f * P, g->pitch, LT + f * TPL, tp, ny, nx, s);
+    if (le == cudaSuccess && seeded && j % g->cfg.gout == 0)
+        le = launch_adj_seed(LT, tp, g->adj_gxy, g->G, g->adj_seed + (j / g->cfg.gout) * g->G, s);
+    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+    return CLIFFS_OK;
+}
+
 // The adjoint steps of cliffs_adjoint_n; `recorded` holds the checkpoints of a recorded run
 // (X_0 included), else a checkpoint pass from the grid's current state makes them.
 static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
@@ -1394,7 +1440,6 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
-    if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the adjoint transposes the x-then-y order only");
     if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "the adjoint does not take boundary input");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
@@ -1457,9 +1502,11 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     fill_step_args(g, a, 0, 1);
     a.limit = nullptr;
     a.step = 1;
-    auto fwd = [&](int from, int to) -> int {
+    // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating order)
+    auto fwd = [&](int from, int to, long long j) -> int {
         a.eta_in = slot(from); a.u_in = slot(from) + P; a.v_in = slot(from) + 2 * P;
         a.eta_out = slot(to); a.u_out = slot(to) + P; a.v_out = slot(to) + 2 * P;
+        a.yfirst = g->cfg.alternate && (j & 1);
         const cudaError_t le = launch_step_fused(a, g->adj_maps[from], 1, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
@@ -1479,7 +1526,7 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
             CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K), slot(cur), sizeof(float) * 3 * P,
                                cudaMemcpyDeviceToDevice, s));
         if (j < (nseg - 1) * K) {
-            int rc = fwd(cur, 1 - cur);
+            int rc = fwd(cur, 1 - cur, j);
             if (rc) return rc;
         }
     }
@@ -1513,11 +1560,16 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
         CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
         for (long long j = j0; j + 1 < j1; ++j) {
-            int rc = fwd((int)(j - j0), (int)(j - j0 + 1));
+            int rc = fwd((int)(j - j0), (int)(j - j0 + 1), j);
             if (rc) return rc;
         }
         for (long long j = j1 - 1; j >= j0; --j) {
             const float* st = slot((int)(j - j0));
+            if (g->cfg.alternate && (j & 1)) {
+                int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, seeded);
+                if (rc2) return rc2;
+                continue;
+            }
             le = launch_adj_xfwd(a, st, st + P, st + 2 * P, XT, XT + TPL, XT + 2 * TPL, tp, s);
             if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
             X.pe = st; X.pw = st + P; X.pt = st + 2 * P;

@@ -52,9 +52,16 @@ def _solver1():
     return w
 
 
+def _alternate():
+    w = workloads.spherical_coast(160, 150, steps=61)
+    w.extra["alternate"] = 1                       # y first on the odd steps
+    return w
+
+
 def _cases():
     return {
         "solver1_beach": _solver1,
+        "alternate_spherical": _alternate,
         "inversion_slope": lambda: workloads.inversion_1024(nx=128, ny=112, steps=160),
         "beach_runup": lambda: workloads.beach_200(200, 90, steps=400),   # the wave runs up the shore
         "spherical_coast": lambda: workloads.spherical_coast(160, 150, steps=60),
@@ -67,18 +74,19 @@ def _cases():
 def test_adjoint_dot_product_against_oracle_tlm(case):
     w = _cases()[case]()
     n = w.steps
-    solver = w.extra.get("solver", 2)
-    g = _start(w, solver=solver)
+    solver, alternate = w.extra.get("solver", 2), w.extra.get("alternate", 0)
+    g = _start(w, solver=solver, alternate=alternate)
     nrec = n // w.gout + 1
     G = len(w.gauges)
     rng = np.random.default_rng(17)
     seed = rng.standard_normal((nrec, G)).astype(np.float32)
     grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
     assert np.isfinite(grad).all()
-    if case in ("beach_runup", "walls_itopo0", "inversion_slope", "spherical_coast", "solver1_beach"):
+    if case in ("beach_runup", "walls_itopo0", "inversion_slope", "spherical_coast", "solver1_beach",
+                "alternate_spherical"):
         assert (w.depth < (w.dwall if w.itopo == 0 else w.h_min)).any()   # dry land or walls in play
     d64 = P.f32(P.oracle_depth(w))
-    p = oracle.params_from(w, solver=solver)
+    p = oracle.params_from(w, solver=solver, alternate=alternate)
     yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
     worst = 0.0
     for k in range(3):

@@ -73,9 +73,7 @@ def test_alternating_order_keeps_1d_equal_2d():
     with pytest.raises(CliffsError) as e:
         g2.step(2, persistent=True)
     assert e.value.code == ERR_ARG
-    with pytest.raises(CliffsError) as e:
-        g2.adjoint(4, None)
-    assert e.value.code == ERR_ARG
+    assert not np.any(g2.adjoint(4, None))      # the adjoint takes the alternating order too
     g1.close()
     g2.close()
 
