@@ -70,8 +70,8 @@ typedef struct cliffs_config {
     int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) */
     int32_t alternate;          /* 0: x then y every step; 1: y first on the odd steps
                                    (counted from 0 at set_initial), the alternating reading of
-                                   section "Numerics"; cliffs_step_n only (the persistent run
-                                   and the adjoint reject it) */
+                                   section "Numerics"; cliffs_step_n and the adjoint (the
+                                   persistent run rejects it) */
     int32_t maxout;             /* steps between max-wave updates (> 0) */
     int32_t gout;               /* steps between gauge records (> 0) */
     int32_t bndout;             /* steps between boundary-series records (> 0) */
@@ -140,8 +140,8 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
  * values at the current model time, linearly interpolated between records (the first or last
  * record outside their span), edges in the order W, E, S, N (S and N own the corners); an
  * edge without input stays a reflecting wall. nt = 0 removes the edge's input. batch == 1
- * only; a grid with input runs through cliffs_step_n (not the persistent run or the
- * adjoint). Errors: ERR_ARG (edge, sizes, times not increasing, batch > 1). */
+ * only; a grid with input runs through cliffs_step_n (not the persistent run); the adjoint
+ * takes the input as fixed (the imposed edge values carry no sensitivity). Errors: ERR_ARG (edge, sizes, times not increasing, batch > 1). */
 int cliffs_set_boundary_input(cliffs_grid* g, int edge, const double* times, int64_t nt, const double* vals);
 
 /* Model clock under boundary input (parameter-file fields 5, cuke, and 13). The run starts at
@@ -187,7 +187,9 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
  * of the y-sweep, then of the x-sweep (eqs. (eqQ), (solver2), (stateu), (stateh), (pq3)),
  * with every branch of the inundation steps (a)-(e), the mirror walls and the friction
  * clamp taken as in the forward run. The grid's state, records and maxima are unchanged.
- * dL_dgauges may be NULL (the gradient is then zero). 2D grids with batch == 1 only.
+ * Under boundary input each adjoint step zeroes the input edges of the adjoint state (the
+ * edge values were overwritten before the step) before the gauge records of that state are
+ * added. dL_dgauges may be NULL (the gradient is then zero). 2D grids with batch == 1 only.
  * Memory: (checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per node,
  * kept for later calls.
  * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, batch > 1, n < 1,

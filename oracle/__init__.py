@@ -91,6 +91,10 @@ def _bind(L):
     L.oracle_run_forced.argtypes = [P(OracleParams), dp, dp, dp, dp, dp, dp, C.c_long, C.c_long, C.c_double,
                                     P(dp), lp, P(dp), C.c_int, C.c_int, ip, dp, C.c_long, lp]
     L.oracle_run_forced.restype = C.c_int
+    L.oracle_run_tlm_forced.argtypes = [P(OracleParams), dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                        C.c_long, C.c_long, C.c_int, C.c_int, ip, dp, dp, C.c_long, lp,
+                                        C.c_double, P(dp), lp, P(dp)]
+    L.oracle_run_tlm_forced.restype = C.c_int
     return L
 
 
@@ -297,6 +301,42 @@ def interp_initial(mx, my, sx, sy, field):
             out[r, c_] = ((1 - b) * ((1 - a) * field[j, i] + a * field[j, i1]) +
                           b * ((1 - a) * field[j1, i] + a * field[j1, i1]))
     return out
+
+
+def run_tlm_forced(p: OracleParams, x, y, depth, eta, deta, boundary, nsteps=0, t0=0.0, gout=1, gauges=None):
+    """Tangent-linear run under boundary input (see ``run_forced``): the imposed edge values
+    carry no tangent. Returns (gauge values [nrec][G], gauge tangents [nrec][G])."""
+    L = lib()
+    ny, nx = depth.shape
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    depth = np.ascontiguousarray(depth, np.float64)
+    eta = np.array(eta, np.float64).reshape(ny, nx)
+    deta = np.array(deta, np.float64).reshape(ny, nx)
+    z = [np.zeros_like(eta) for _ in range(4)]
+    keep = []
+    tp = (C.POINTER(C.c_double) * 4)()
+    vp = (C.POINTER(C.c_double) * 4)()
+    nt = (C.c_long * 4)()
+    for e in range(4):
+        if e in boundary:
+            t, vals = boundary[e]
+            t = np.ascontiguousarray(t, np.float64)
+            vals = np.ascontiguousarray(vals, np.float64)
+            keep += [t, vals]
+            tp[e], vp[e], nt[e] = _d(t), _d(vals), len(t)
+    gix = np.ascontiguousarray(np.asarray(gauges, np.int32).reshape(-1))
+    G = len(gix) // 2
+    cap = nsteps + 1
+    gval = np.zeros((cap, G))
+    gtan = np.zeros((cap, G))
+    n = C.c_long(0)
+    rc = L.oracle_run_tlm_forced(C.byref(p), _d(x), _d(y), _d(depth), _d(eta), _d(z[0]), _d(z[1]), _d(deta),
+                                 _d(z[2]), _d(z[3]), 0, int(nsteps), int(gout), G, _i(gix), _d(gval), _d(gtan),
+                                 cap, C.byref(n), float(t0), tp, nt, vp)
+    if rc != 0:
+        raise ValueError("oracle_run_tlm_forced failed (%d)" % rc)
+    return gval[: n.value], gtan[: n.value]
 
 
 def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv=None,

@@ -587,7 +587,9 @@ int oracle_run(const oracle_params* p, const double* x, const double* y, const d
 // interpolated between records (the first or last record outside their span); the edges
 // are set in the order W, E, S, N, so S and N own the corners. An edge with no series is
 // left to the scheme (a reflecting wall).
-static void impose_edge(const Params& P, double* eta, double* u, double* v, int edge,
+extern "C++" {
+template <typename T>
+static void impose_edge(const Params& P, T* eta, T* u, T* v, int edge,
                         const double* times, long nt, const double* vals, double t) {
     const int np = (edge < 2) ? P.ny : P.nx;
     long k = 0;
@@ -608,9 +610,10 @@ static void impose_edge(const Params& P, double* eta, double* u, double* v, int 
             const double b = (w > 0.0) ? vals[((k + 1) * 3 + f) * np + q] : a;
             val[f] = (1.0 - w) * a + w * b;
         }
-        u[c] = val[0]; v[c] = val[1]; eta[c] = val[2];
+        u[c] = T(val[0]); v[c] = T(val[1]); eta[c] = T(val[2]);   // the input does not depend on the state
     }
 }
+}  // extern "C++"
 
 // A run under boundary input from model time t0: before step k the edges are set at time
 // t0 + (k - step0) dt. Gauges (eta, u, v) are recorded as in oracle_run.
@@ -629,12 +632,19 @@ int oracle_run_forced(const oracle_params* p, const double* x, const double* y, 
     for (long k = step0; k < step0 + nsteps; ++k) {
         const double t = t0 + (double)(k - step0) * P.dt;
         for (int e = 0; e < 4; ++e)
-            if (times[e] && nt[e] > 0) impose_edge(P, eta, u, v, e, times[e], nt[e], vals[e], t);
+            if (times[e] && nt[e] > 0) impose_edge<double>(P, eta, u, v, e, times[e], nt[e], vals[e], t);
         step<double>(Gd, k, eta, u, v);
         record<double>(Gd, k + 1, eta, u, v, &O);
     }
     return 0;
 }
+
+static int run_tlm_impl(const oracle_params* p, const double* x, const double* y, const double* d,
+                        double* eta, double* u, double* v, double* deta, double* du, double* dv,
+                        long step0, long nsteps, int record_initial,
+                        int gout, int n_gauges, const int* gauge_ixiy,
+                        double* gauge_val, double* gauge_tan, long cap, long* nrec,
+                        double t0, const double* const* times, const long* nt, const double* const* vals);
 
 // Tangent-linear run: the primal (eta,u,v) and a tangent (deta,du,dv) advance together;
 // every branch is decided on the primal. Gauge tangents of eta are written to
@@ -644,6 +654,28 @@ int oracle_run_tlm(const oracle_params* p, const double* x, const double* y, con
                    long step0, long nsteps, int record_initial,
                    int gout, int n_gauges, const int* gauge_ixiy,
                    double* gauge_val, double* gauge_tan, long cap, long* nrec) {
+    return run_tlm_impl(p, x, y, d, eta, u, v, deta, du, dv, step0, nsteps, record_initial, gout, n_gauges,
+                        gauge_ixiy, gauge_val, gauge_tan, cap, nrec, 0.0, nullptr, nullptr, nullptr);
+}
+
+// The tangent-linear model of oracle_run_forced: the imposed edge values carry no tangent.
+int oracle_run_tlm_forced(const oracle_params* p, const double* x, const double* y, const double* d,
+                          double* eta, double* u, double* v, double* deta, double* du, double* dv,
+                          long step0, long nsteps, int gout, int n_gauges, const int* gauge_ixiy,
+                          double* gauge_val, double* gauge_tan, long cap, long* nrec,
+                          double t0, const double* const* times, const long* nt, const double* const* vals) {
+    return run_tlm_impl(p, x, y, d, eta, u, v, deta, du, dv, step0, nsteps, 1, gout, n_gauges, gauge_ixiy,
+                        gauge_val, gauge_tan, cap, nrec, t0, times, nt, vals);
+}
+
+}  // extern "C"
+
+static int run_tlm_impl(const oracle_params* p, const double* x, const double* y, const double* d,
+                        double* eta, double* u, double* v, double* deta, double* du, double* dv,
+                        long step0, long nsteps, int record_initial,
+                        int gout, int n_gauges, const int* gauge_ixiy,
+                        double* gauge_val, double* gauge_tan, long cap, long* nrec,
+                        double t0, const double* const* times, const long* nt, const double* const* vals) {
     Params P = to_params(p);
     if ((P.nx > 1 && P.nx < 3) || (P.ny > 1 && P.ny < 3)) return -1;
     Grid Gd{P, x, y, d};
@@ -662,6 +694,11 @@ int oracle_run_tlm(const oracle_params* p, const double* x, const double* y, con
     };
     if (record_initial) rec(step0);
     for (long k = step0; k < step0 + nsteps; ++k) {
+        if (times) {
+            const double t = t0 + (double)(k - step0) * P.dt;
+            for (int e = 0; e < 4; ++e)
+                if (times[e] && nt[e] > 0) impose_edge<Dual>(P, E.data(), U.data(), V.data(), e, times[e], nt[e], vals[e], t);
+        }
         step<Dual>(Gd, k, E.data(), U.data(), V.data());
         rec(k + 1);
     }
@@ -673,4 +710,4 @@ int oracle_run_tlm(const oracle_params* p, const double* x, const double* y, con
     return 0;
 }
 
-}  // extern "C"
+

@@ -680,6 +680,28 @@ __global__ void k_adj_seed(float* te, int tpitch, const int* gxy, int G, const f
     if (k < G) atomicAdd(te + (long long)gxy[2 * k] * tpitch + gxy[2 * k + 1], seed[k]);
 }
 
+// lambda = 0 on the edges whose nodes the boundary input overwrites before a step (mask:
+// 1 W, 2 E, 4 S, 8 N), on the transposed adjoint ([nx][tpitch], three fields)
+__global__ void k_adj_zero_edges(float* t, int tpitch, long long tplane, int nx, int ny, int mask) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.y;
+    if (!((mask >> e) & 1)) return;
+    const int np = e < 2 ? ny : nx;
+    if (q >= np) return;
+    const int ix = e == 0 ? 0 : e == 1 ? nx - 1 : q;
+    const int iy = e == 2 ? 0 : e == 3 ? ny - 1 : q;
+    const long long o = (long long)ix * tpitch + iy;
+    t[o] = 0.f;
+    t[o + tplane] = 0.f;
+    t[o + 2 * tplane] = 0.f;
+}
+
+cudaError_t launch_adj_zero_edges(float* t, int tpitch, int nx, int ny, int mask, cudaStream_t s) {
+    const int np = nx > ny ? nx : ny;
+    k_adj_zero_edges<<<dim3((np + 127) / 128, 4), 128, 0, s>>>(t, tpitch, (long long)tpitch * nx, nx, ny, mask);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s) {
     const dim3 grid((A.npos + AOUT - 1) / AOUT, (A.nlines + ALINES - 1) / ALINES);
     static const void* const t[8] = {(const void*)k_adj_line<0, false, false>, (const void*)k_adj_line<0, true, false>,

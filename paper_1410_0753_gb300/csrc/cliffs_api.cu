@@ -642,6 +642,40 @@ int record_checkpoint(cliffs_grid* g, long long idx) {
     return CLIFFS_OK;
 }
 
+// Boundary input at model time t into the edge nodes of a state (batch 1).
+int impose_boundary(cliffs_grid* g, float* eta, float* u, float* v, double t) {
+    BndStep b{};
+    int npmax = 0;
+    for (int e = 0; e < 4; ++e) {
+        const std::vector<double>& T = g->bnd_t[e];
+        if (T.empty()) continue;
+        long long i = 0;
+        double w = 0.0;
+        if (t <= T.front() || T.size() == 1) i = 0;
+        else if (t >= T.back()) i = (long long)T.size() - 1;
+        else {
+            i = (long long)(std::upper_bound(T.begin(), T.end(), t) - T.begin()) - 1;
+            w = (t - T[i]) / (T[i + 1] - T[i]);
+        }
+        b.vals[e] = g->bnd_v[e];
+        b.np[e] = e < 2 ? g->ny : g->nx;
+        b.k[e] = i;
+        b.w[e] = w;
+        npmax = std::max(npmax, b.np[e]);
+    }
+    k_bnd<<<dim3((npmax + 127) / 128, 4), 128, 0, g->stream>>>(eta, u, v, g->pitch, g->nx, g->ny, b);
+    CK(cudaGetLastError());
+    return CLIFFS_OK;
+}
+
+// edges with boundary input as a mask (1 W, 2 E, 4 S, 8 N)
+int input_edges(const cliffs_grid* g) {
+    int m = 0;
+    for (int e = 0; e < 4; ++e)
+        if (!g->bnd_t[e].empty()) m |= 1 << e;
+    return m;
+}
+
 void free_grid(cliffs_grid* g) {
     for (int k = 0; k < 2; ++k) { cudaFree(g->eta[k]); cudaFree(g->u[k]); cudaFree(g->v[k]); }
     cudaFree(g->d32); cudaFree(g->d64); cudaFree(g->d64b);
@@ -1170,28 +1204,8 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
         if (g->bnd_any) {
             const double t = g->t_start + (double)g->step * g->cfg.dt;
             if (g->bnd_stop && t + g->cfg.dt > t_end * (1.0 + 1e-12) + 1e-9 * g->cfg.dt) break;
-            BndStep b{};
-            int npmax = 0;
-            for (int e = 0; e < 4; ++e) {
-                const std::vector<double>& T = g->bnd_t[e];
-                if (T.empty()) continue;
-                long long i = 0;
-                double w = 0.0;
-                if (t <= T.front() || T.size() == 1) i = 0;
-                else if (t >= T.back()) i = (long long)T.size() - 1;
-                else {
-                    i = (long long)(std::upper_bound(T.begin(), T.end(), t) - T.begin()) - 1;
-                    w = (t - T[i]) / (T[i + 1] - T[i]);
-                }
-                b.vals[e] = g->bnd_v[e];
-                b.np[e] = e < 2 ? g->ny : g->nx;
-                b.k[e] = i;
-                b.w[e] = w;
-                npmax = std::max(npmax, b.np[e]);
-            }
-            k_bnd<<<dim3((npmax + 127) / 128, 4), 128, 0, s>>>(g->eta[in], g->u[in], g->v[in], g->pitch, g->nx,
-                                                              g->ny, b);
-            CK(cudaGetLastError());
+            rc = impose_boundary(g, g->eta[in], g->u[in], g->v[in], t);
+            if (rc) return rc;
         }
         fill_step_args(g, a, in, out);
         a.step = st;
@@ -1440,7 +1454,6 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
-    if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "the adjoint does not take boundary input");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);
@@ -1503,10 +1516,16 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     a.limit = nullptr;
     a.step = 1;
     // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating order)
+    const long long s0 = recorded ? 0 : g->step;           // steps done before X_0
     auto fwd = [&](int from, int to, long long j) -> int {
         a.eta_in = slot(from); a.u_in = slot(from) + P; a.v_in = slot(from) + 2 * P;
         a.eta_out = slot(to); a.u_out = slot(to) + P; a.v_out = slot(to) + 2 * P;
         a.yfirst = g->cfg.alternate && (j & 1);
+        if (g->bnd_any) {                                  // boundary input, as in cliffs_step_n
+            const int rci = impose_boundary(g, slot(from), slot(from) + P, slot(from) + 2 * P,
+                                            g->t_start + (double)(s0 + j) * g->cfg.dt);
+            if (rci) return rci;
+        }
         const cudaError_t le = launch_step_fused(a, g->adj_maps[from], 1, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
@@ -1565,17 +1584,31 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
         }
         for (long long j = j1 - 1; j >= j0; --j) {
             const float* st = slot((int)(j - j0));
-            if (g->cfg.alternate && (j & 1)) {
-                int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, seeded);
-                if (rc2) return rc2;
-                continue;
+            // with boundary input the stored state is imposed again first (the step ran on the
+            // imposed state), and the seed goes in after the input edges of lambda_j are zeroed
+            if (g->bnd_any) {
+                const int rci = impose_boundary(g, const_cast<float*>(st), const_cast<float*>(st) + P,
+                                                const_cast<float*>(st) + 2 * P,
+                                                g->t_start + (double)(s0 + j) * g->cfg.dt);
+                if (rci) return rci;
             }
-            le = launch_adj_xfwd(a, st, st + P, st + 2 * P, XT, XT + TPL, XT + 2 * TPL, tp, s);
-            if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
-            X.pe = st; X.pw = st + P; X.pt = st + 2 * P;
-            X.seed = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * G : nullptr;
-            if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
-            if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+            const float* seed_j = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * G : nullptr;
+            if (g->cfg.alternate && (j & 1)) {
+                int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, g->bnd_any ? false : seeded);
+                if (rc2) return rc2;
+            } else {
+                le = launch_adj_xfwd(a, st, st + P, st + 2 * P, XT, XT + TPL, XT + 2 * TPL, tp, s);
+                if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
+                X.pe = st; X.pw = st + P; X.pt = st + 2 * P;
+                X.seed = g->bnd_any ? nullptr : seed_j;
+                if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
+                if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+            }
+            if (g->bnd_any) {
+                le = launch_adj_zero_edges(LT, tp, nx, ny, input_edges(g), s);
+                if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, g->adj_gxy, G, seed_j, s);
+                if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+            }
         }
     }
     // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]; the u and v parts stay for

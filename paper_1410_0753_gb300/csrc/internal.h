@@ -101,6 +101,7 @@ cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, c
 cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,
                              cudaStream_t s);
 cudaError_t launch_adj_seed(float* te, int tpitch, const int* gxy, int G, const float* seed, cudaStream_t s);
+cudaError_t launch_adj_zero_edges(float* t, int tpitch, int nx, int ny, int mask, cudaStream_t s);
 
 // launchers (cliffs_step.cu)
 cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s);

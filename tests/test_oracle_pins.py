@@ -609,6 +609,38 @@ def test_nesting_chain_reproduces_the_parent_inside_the_child():
     assert np.abs(free["eta"] - par["eta"][sub]).max() > 1e-3
 
 
+def test_forced_tlm_matches_central_differences_of_the_forced_run():
+    """Under boundary input the edge nodes take the input before each step, so their tangent
+    is zero there; the forced tangent model against central differences of the forced run on
+    an enclosed grid of a sloping parent (the wave crosses the child's edges)."""
+    from workloads import Nest
+    x, y, d, eta0, p, steps = _open_water_parent()
+    i0, j0, cx, cy = 17, 12, 30, 24
+    nest = Nest(x[i0], y[j0], 100.0, 100.0, cx, cy)
+    par = oracle.run(p, x, y, d, eta0, nsteps=steps, bndout=1, nests=[nest])
+    times = 1.5 * np.arange(steps + 1)
+    bnd = {e: (times, par["boundary"][0][e]) for e in range(4)}
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    pc = oracle.params(cx, cy, 1.5, manning_n2=6.25e-4)
+    cxs, cys = x[i0:i0 + cx], y[j0:j0 + cy]
+    X, Y = np.meshgrid(cxs, cys)
+    dirn = np.exp(-((X - cxs[4]) ** 2 + (Y - cys[12]) ** 2) / (2 * 400.0 ** 2))   # reaches the W edge
+    gauges = [(2, 12), (15, 12), (27, 20)]
+    gval, gtan = oracle.run_tlm_forced(pc, cxs, cys, d[sub], eta0[sub], dirn, bnd, nsteps=steps, gauges=gauges)
+    h = 1e-3
+    rp = oracle.run_forced(pc, cxs, cys, d[sub], eta0[sub] + h * dirn, bnd, nsteps=steps, gauges=gauges)
+    rm = oracle.run_forced(pc, cxs, cys, d[sub], eta0[sub] - h * dirn, bnd, nsteps=steps, gauges=gauges)
+    fd = (rp["gauges"][:, :, 0] - rm["gauges"][:, :, 0]) / (2 * h)
+    scale = np.abs(gtan).max()
+    assert scale > 1e-3
+    assert np.abs(fd - gtan).max() <= 1e-6 * scale, np.abs(fd - gtan).max() / scale
+    r0 = oracle.run_forced(pc, cxs, cys, d[sub], eta0[sub], bnd, nsteps=steps, gauges=gauges)
+    assert np.array_equal(r0["gauges"][:, :, 0], gval)
+    # the unforced tangent differs: the perturbation leaving through the edges is not replaced
+    _, free, _, _ = oracle.run_tlm(pc, cxs, cys, d[sub], eta0[sub], dirn, nsteps=steps, gauges=gauges)
+    assert np.abs(free - gtan).max() > 1e-3 * scale
+
+
 # ----------------------------------------------------------------------------------------
 # Initial conditions from a source grid (section "Running Options", "The input to the
 # computations"): interpolated inside the source grid, zero outside it.
