@@ -295,7 +295,9 @@ struct FusedWarp {
         if (vA && !oA) bad |= !(fabsf(E.x) < 1e5f);
         if (vB && !oB) bad |= !(fabsf(E.y) < 1e5f);
         const int r = k - 3;
-        ym.template push<PH, SPH, FRIC, S1>(E, V, U, D, oA, oB, m2, K, vA, vB,
+        // the y-sweep results a lane must get right: its own output columns, and with YF every
+        // column of the window (the x-sweep on the way out reads three columns past the outputs)
+        ym.template push<PH, SPH, FRIC, S1>(E, V, U, D, oA, oB, m2, K, YF ? colA : vA, YF ? colB : vB,
             [&](float2 oe, float2 ow, float2 ot, float2 od) {
                 if (r >= r0 && r < r1) {
                     if (YF) {

@@ -130,3 +130,32 @@ def test_solver1_persistent_equals_per_step():
     for x, y in zip(runs[0], runs[1]):
         for p, q in zip(x if isinstance(x, tuple) else (x,), y if isinstance(y, tuple) else (y,)):
             assert np.array_equal(p, q)
+
+
+def test_alternating_order_island_in_the_window_halo():
+    """With y first, a warp's y-sweep results in the three columns past its outputs feed the
+    x-sweep that follows, so they must be exact too. A small island in columns 56-58 lies in
+    the halo of the first strip of columns (outputs 0-55) while that strip's own columns are
+    open water; its north and south edges are walls in the y-sweep. Checked against the
+    oracle next to the island, where column 55 reads columns 56-58."""
+    nx, ny, dx, dt, steps = 120, 80, 50.0, 1.8, 120
+    x, y = dx * np.arange(nx), dx * np.arange(ny)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    d = np.full((ny, nx), 15.0)
+    d[30:46, 56:59] = -1.0
+    eta0 = 0.5 * np.exp(-((X - 30.0) ** 2 + (Y - 38.0) ** 2) / (2 * 6.0 ** 2))
+    gauges = np.array([(55, 29), (55, 46), (55, 38), (53, 30), (59, 28), (20, 38)], np.int32)
+    kw = dict(h_min=0.01, manning_n2=6.25e-4)
+    g = CliffsGrid(nx, ny, dt, alternate=1, gauges=[tuple(q) for q in gauges], **kw)
+    g.set_bathy(x, y, d, False)
+    d64 = P.f32(g.depth())
+    g.set_initial(eta0.astype(np.float32))
+    g.step(steps)
+    o = oracle.run(oracle.params(nx, ny, dt, alternate=1, **kw), x, y, d64, eta0, nsteps=steps, gout=1,
+                   gauges=gauges)
+    _assert_gauges("alternate_island_halo", g.gauges(), o["gauges"])
+    e32 = g.state()[0]
+    wet32, wet64, near = P.wet_masks(e32, o["eta"], d64, d64, 0.01)
+    assert np.array_equal(wet32 & ~near, wet64 & ~near)
+    assert np.abs(e32 - o["eta"])[wet64].max() <= 1e-4 * 0.5
+    g.close()
