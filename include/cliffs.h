@@ -80,6 +80,13 @@ typedef struct cliffs_config {
     int32_t n_nests;
     const cliffs_nest* nests;   /* [n_nests]; copied at create; 2D grids, batch == 1 only */
     void*   stream;             /* cudaStream_t for all work, or NULL (default stream) */
+    int32_t open_edges;         /* open (radiating) outer edges, bits W 1, E 2, S 4, N 8;
+                                   the others are reflecting walls. The paper gives no
+                                   condition for an open edge; the reading taken: the ghost
+                                   beyond a wet edge node carries the node's outgoing Riemann
+                                   invariant and the incoming invariant of still water at the
+                                   node's depth (sqrt(g max(d, 0))), the node's depth and
+                                   transverse velocity. Not taken by the adjoint (ERR_ARG). */
 } cliffs_config;
 
 /* Create a grid with the given parameters. Allocates the device state ([batch][ny][nx] of
@@ -310,7 +317,7 @@ void cliffs_destroy(cliffs_grid* g);
 /* Message of the last error on the calling thread ("" if none). */
 const char* cliffs_last_error(void);
 
-/* ABI version of this header. */
+/* ABI version of this header (2: cliffs_config gained open_edges). */
 int cliffs_abi_version(void);
 
 #ifdef __cplusplus

@@ -50,7 +50,7 @@ class OracleParams(C.Structure):
                 ("h_min", C.c_double), ("manning_n2", C.c_double),
                 ("itopo", C.c_int32), ("dwall", C.c_double), ("dt", C.c_double),
                 ("transverse", C.c_int32), ("solver", C.c_int32), ("form", C.c_int32),
-                ("alternate", C.c_int32)]
+                ("alternate", C.c_int32), ("open_edges", C.c_int32)]
 
 
 def lib():
@@ -112,14 +112,16 @@ def _i(a):
 
 
 def params(nx, ny, dt, coords=1, h_min=0.01, manning_n2=0.0, itopo=1, dwall=0.0, transverse=1,
-           solver=2, form=0, alternate=0) -> OracleParams:
+           solver=2, form=0, alternate=0, open_edges=0) -> OracleParams:
+    """open_edges: bits W 1, E 2, S 4, N 8 mark open (radiating) outer edges; the others are
+    reflecting walls."""
     return OracleParams(nx, ny, coords, h_min, manning_n2, itopo, dwall, dt, transverse,
-                        solver, form, alternate)
+                        solver, form, alternate, open_edges)
 
 
-def params_from(w, form=0, solver=2, alternate=0) -> OracleParams:
+def params_from(w, form=0, solver=2, alternate=0, open_edges=0) -> OracleParams:
     return params(w.nx, w.ny, w.dt, w.coords, w.h_min, w.manning_n2, w.itopo, w.dwall,
-                  w.transverse, solver, form, alternate)
+                  w.transverse, solver, form, alternate, open_edges)
 
 
 def depth_filter(depth, alpha=2.0, min_depth=0.1, max_passes=100):

@@ -90,6 +90,7 @@ struct Params {
     int solver;                // 2: eq. (solver2) (current Cliffs); 1: eq. (solver1)
     int form;                  // 0: literal Riemann-invariant form; 1: perturbation form
     int alternate;             // 1: y-sweep first on odd steps (alternating splitting)
+    int open_edges;            // open outer edges, bits W 1, E 2, S 4, N 8 (others walls)
 };
 
 // Per-node state as seen by the solver: a real wet node or a mirror ghost.
@@ -141,12 +142,30 @@ inline T Qt(T w_a, T w_b, T t_a, T t_b, double ds) {
     return 0.5 * (w_a + w_b) * (t_a - t_b) / ds;
 }
 
+// Open outer edge (the paper gives no condition for one): the ghost beyond a wet edge node
+// carries the node's outgoing Riemann invariant and the incoming invariant of still water at
+// the node's depth, c0 = sqrt(g max(d, 0)); its depth and transverse velocity are the node's.
+// At the right end (east, north) p leaves and q enters: p_g = w + 2c, q_g = -2 c0; at the
+// left end q leaves and p enters: q_g = w - 2c, p_g = 2 c0. A ghost whose c would be
+// negative (an inflow past the critical speed) is taken dry, c_g = 0.
+template <typename T>
+Node<T> open_ghost(const Node<T>& C, bool right, double g) {
+    const T c = sqrt(g * (C.eta + C.d));
+    const double c0 = std::sqrt(g * std::max(C.d, 0.0));
+    const T p = right ? C.w + 2.0 * c : T(2.0 * c0);
+    const T q = right ? T(-2.0 * c0) : C.w - 2.0 * c;
+    T cg = 0.25 * (p - q);
+    if (val(cg) < 0.0) cg = T(0.0);
+    return Node<T>{cg * cg / g - C.d, 0.5 * (p + q), C.t, C.d};
+}
+
 // One sweep of one line (a row in the x-sweep, a column in the y-sweep).
 //   n     nodes on the line (n >= 3)
 //   ds    n-1 intervals between consecutive nodes, in metres
 //   d     depth, positive down
 //   src   spherical continuity factor tan(phi)/R per node, or null (see reading 7)
 //   eta, w, t  free surface, along-line velocity, transverse velocity (in/out)
+//   open  bit 0: the end at j = 0 is an open edge, bit 1: the end at j = n-1 (else walls)
 // Readings of the paper where it is silent (binding on both the oracle and the GPU):
 //  1. (a) dry means h = eta + d < h_min (the algorithm text; "at and below" in the
 //     parameter list conflicts). A dry cell carries no velocity; its eta is left as is.
@@ -164,7 +183,7 @@ inline T Qt(T w_a, T w_b, T t_a, T t_b, double ds) {
 //     q -= dt c v tan(phi)/R; no Coriolis and no metric momentum terms.
 template <typename T>
 void sweep_line(const Params& P, int n, const double* ds, const double* d, const double* src,
-                T* eta, T* w, T* t, Scratch<T>& S, PhaseRec* rec)
+                T* eta, T* w, T* t, Scratch<T>& S, PhaseRec* rec, int open = 0)
 {
     const double g = GRAV, hmin = P.h_min, dt = P.dt;
     S.resize(n);
@@ -205,6 +224,8 @@ void sweep_line(const Params& P, int n, const double* ds, const double* d, const
         Node<T> Gh{S.e1[j], -S.w1[j], S.t1[j], d[j]};
         Node<T> L = (j > 0 && S.wet1[j - 1]) ? Node<T>{S.e1[j - 1], S.w1[j - 1], S.t1[j - 1], d[j - 1]} : Gh;
         Node<T> R = (j < n - 1 && S.wet1[j + 1]) ? Node<T>{S.e1[j + 1], S.w1[j + 1], S.t1[j + 1], d[j + 1]} : Gh;
+        if (j == 0 && (open & 1)) L = open_ghost(C, false, g);
+        if (j == n - 1 && (open & 2)) R = open_ghost(C, true, g);
 
         T hC = C.eta + C.d, hL = L.eta + L.d, hR = R.eta + R.d;
         T cC = sqrt(g * hC), cL = sqrt(g * hL), cR = sqrt(g * hR);
@@ -334,7 +355,8 @@ void x_sweep(const Grid& Gd, T* eta, T* u, T* v) {
         for (int jy = 0; jy < ny; ++jy) {
             Gd.row_ds(jy, ds.data());
             const size_t o = (size_t)jy * nx;
-            sweep_line<T>(Gd.P, nx, ds.data(), Gd.d + o, nullptr, eta + o, u + o, v + o, S, nullptr);
+            sweep_line<T>(Gd.P, nx, ds.data(), Gd.d + o, nullptr, eta + o, u + o, v + o, S, nullptr,
+                          Gd.P.open_edges & 3);
         }
     }
 }
@@ -360,7 +382,7 @@ void y_sweep(const Grid& Gd, T* eta, T* u, T* v) {
                 e[j] = eta[o]; a[j] = v[o]; b[j] = u[o]; dd[j] = Gd.d[o];
             }
             sweep_line<T>(Gd.P, ny, ds.data(), dd.data(), src.empty() ? nullptr : src.data(),
-                          e.data(), a.data(), b.data(), S, nullptr);
+                          e.data(), a.data(), b.data(), S, nullptr, (Gd.P.open_edges >> 2) & 3);
             for (int j = 0; j < ny; ++j) {
                 const size_t o = (size_t)j * nx + ix;
                 eta[o] = e[j]; v[o] = a[j]; u[o] = b[j];
@@ -461,6 +483,7 @@ struct oracle_params {
     int32_t itopo;
     double dwall, dt;
     int32_t transverse, solver, form, alternate;
+    int32_t open_edges;
 };
 
 static Params to_params(const oracle_params* p) {
@@ -469,6 +492,7 @@ static Params to_params(const oracle_params* p) {
     P.manning_n2 = p->manning_n2; P.itopo = p->itopo; P.dwall = p->dwall; P.dt = p->dt;
     P.transverse = p->transverse; P.solver = p->solver == 1 ? 1 : 2; P.form = p->form;
     P.alternate = p->alternate;
+    P.open_edges = p->open_edges;
     return P;
 }
 
@@ -537,7 +561,7 @@ int oracle_sweep_line(const oracle_params* p, int n, const double* ds, const dou
     Params P = to_params(p);
     Scratch<double> S;
     PhaseRec rec{wet0, wet1, srcidx, eta_b, w_b, t_b, eta_d, w_d, t_d};
-    sweep_line<double>(P, n, ds, d, src, eta, w, t, S, &rec);
+    sweep_line<double>(P, n, ds, d, src, eta, w, t, S, &rec, P.open_edges & 3);
     return 0;
 }
 

@@ -66,7 +66,7 @@ class cliffs_config(C.Structure):
                 ("maxout", C.c_int32), ("gout", C.c_int32), ("bndout", C.c_int32),
                 ("n_gauges", C.c_int32), ("gauge_ixiy", C.POINTER(C.c_int32)),
                 ("n_nests", C.c_int32), ("nests", C.POINTER(cliffs_nest)),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("open_edges", C.c_int32)]
 
 
 _lib = None
@@ -335,7 +335,8 @@ class CliffsGrid:
 
     def __init__(self, nx, ny, dt, *, batch=1, coords=1, h_min=0.01, manning_n2=0.0, itopo=1,
                  dwall=0.0, transverse=1, solver=2, alternate=0, maxout=1, gout=1, bndout=1,
-                 gauges: Sequence = (), nests: Sequence = (), stream: Optional[int] = None):
+                 gauges: Sequence = (), nests: Sequence = (), stream: Optional[int] = None,
+                 open_edges=0):
         g = np.ascontiguousarray(np.asarray(gauges, np.int32).reshape(-1))
         self._gauges = g
         ns = (cliffs_nest * max(1, len(nests)))()
@@ -346,7 +347,7 @@ class CliffsGrid:
                             solver, alternate, maxout, gout, bndout, len(g) // 2,
                             g.ctypes.data_as(C.POINTER(C.c_int32)) if len(g) else None,
                             len(nests), ns if len(nests) else None,
-                            C.c_void_p(stream) if stream else None)
+                            C.c_void_p(stream) if stream else None, int(open_edges))
         self.cfg = cfg
         self.nx, self.ny, self.batch = nx, ny, batch
         self.n_gauges = len(g) // 2

@@ -617,6 +617,7 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.tx_pad = 0;
     a.yfirst = 0;
     a.inv_dt2_s1 = g->cfg.solver == 1 ? (float)(1.0 / (g->cfg.dt * g->cfg.dt)) : 0.f;
+    a.open_edges = g->cfg.open_edges;
 }
 
 // Keep the current state of a recorded run as checkpoint `idx` (grows the store by doubling).
@@ -719,7 +720,7 @@ extern "C" {
 
 const char* cliffs_last_error(void) { return g_err; }
 
-int cliffs_abi_version(void) { return 1; }
+int cliffs_abi_version(void) { return 2; }
 
 int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
     g_err[0] = 0;
@@ -738,6 +739,8 @@ int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out) {
         return set_err(CLIFFS_ERR_ARG, "maxout, gout and bndout must be >= 1");
     if (!(cfg->solver == 0 || cfg->solver == 1 || cfg->solver == 2))
         return set_err(CLIFFS_ERR_ARG, "solver must be 1 or 2 (0 means 2)");
+    if (cfg->open_edges < 0 || cfg->open_edges > 15)
+        return set_err(CLIFFS_ERR_ARG, "open_edges is a mask of W 1, E 2, S 4, N 8");
     if (cfg->alternate != 0 && cfg->alternate != 1) return set_err(CLIFFS_ERR_ARG, "alternate must be 0 or 1");
     if (cfg->n_gauges < 0 || (cfg->n_gauges > 0 && !cfg->gauge_ixiy))
         return set_err(CLIFFS_ERR_ARG, "bad gauge list");
@@ -1386,6 +1389,7 @@ int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
         return CLIFFS_OK;
     }
     if (g->kind != 0 || g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid with batch == 1");
+    if (g->cfg.open_edges) return set_err(CLIFFS_ERR_ARG, "the adjoint takes reflecting outer edges only");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->step != 0) return set_err(CLIFFS_ERR_STATE, "record from the initial state (no steps since set_initial)");
     g->rec_K = checkpoint_every;
@@ -1454,6 +1458,7 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
+    if (g->cfg.open_edges) return set_err(CLIFFS_ERR_ARG, "the adjoint takes reflecting outer edges only");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);

@@ -37,6 +37,7 @@ struct StepArgs {
     int sph;                         // geographic grid: x metric scaled per row
     int yfirst;                      // this step sweeps y, then x (alternating order)
     float inv_dt2_s1;                // 1/dt^2 with eq. (solver1), 0 with eq. (solver2)
+    int open_edges;                  // open outer edges: bits W 1, E 2, S 4, N 8
     long long wait_cycles;           // limit of every mbarrier wait (clock cycles)
     unsigned tx_pad;                 // extra bytes each ring slot expects (fault injection; 0)
 };

@@ -119,6 +119,37 @@ __device__ __forceinline__ void ghost_right(float w, float c, float inv, float& 
     p = -f; q = f; t = 0.f;
 }
 
+// Open outer edge (no condition in the paper): the ghost beyond a wet edge node carries the
+// node's outgoing Riemann invariant and the incoming invariant of still water at its depth,
+// c0 = sqrt(g max(d, 0)). With delta = c - c0 (= g eta / (c + c0) for d > 0, else c):
+//   right end (p leaves, q = -2 c0 enters): w_g = w/2 + delta, c_g = c + w/4 - delta/2;
+//   left end  (q leaves, p = 2 c0 enters):  w_g = w/2 - delta, c_g = c - w/4 - delta/2;
+// eta_g = eta + (c_g - c)(c_g + c)/g, the node's depth and transverse velocity. A ghost
+// whose c_g would be negative is dry (c_g = 0). At rest (eta = w = 0) the ghost equals the
+// node exactly, so the edge flux vanishes.
+__device__ __forceinline__ void open_ghost(float e, float w, float d, float c, bool right,
+                                           float& eg, float& wg, float& cg) {
+    const bool deep = d > 0.f;
+    const float c0 = deep ? wave_speed(d) : 0.f;
+    const float delta = deep ? GRAV * e * rcp_approx(c + c0) : c;
+    const float s = right ? 1.f : -1.f;
+    wg = fmaf(0.5f, w, s * delta);
+    float gam = fmaf(s * 0.25f, w, -0.5f * delta);           // c_g - c
+    if (c + gam < 0.f) gam = -c;
+    cg = c + gam;
+    eg = fmaf(gam * (2.f * c + gam), INV_GRAV, e);
+}
+
+// Fluxes at the open edge of a node (scalar; the .x lane of the packed form). Kept out of
+// line: open edges are rare, and inlined they would take registers from the sweeps.
+static __device__ __noinline__ void open_flux(float e, float w, float t, float d, float c, float inv, bool right,
+                                          float& p, float& q, float& tf, float& eg, float& wg, float& cg) {
+    open_ghost(e, w, d, c, right, eg, wg, cg);
+    const Flux2 F = right ? iface2(v2(e), v2(w), v2(t), v2(d), v2(c), v2(eg), v2(wg), v2(t), v2(d), v2(cg), v2(inv))
+                          : iface2(v2(eg), v2(wg), v2(t), v2(d), v2(cg), v2(e), v2(w), v2(t), v2(d), v2(c), v2(inv));
+    p = F.p.x; q = F.q.x; tf = F.t.x;
+}
+
 // (d): eq. (solver2) at two nodes given their left and right interface fluxes.
 //   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep (SRC).
 // Friction: alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3) at time level n on both p and q,
@@ -196,9 +227,10 @@ struct XMet2 { float2 inv_l, inv_r, k2; };   // per pair: 1/dx_{j-1}, 1/dx_j, dt
 // and B = 2l + 1 (.y). Neighbours across lanes come by shuffles. On return (E, W, T) hold
 // the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each side
 // lack their 3-node dependency radius). W is the velocity along the row, T across it.
-template <bool FRIC, bool S1 = false>
+// ends: this lane's nodes at open outer edges, bits 1 A left, 2 A right, 4 B left, 8 B right.
+template <bool FRIC, bool S1 = false, bool OPEN = false>
 __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
-                                        const SweepConst& K, int lane) {
+                                        const SweepConst& K, int lane, unsigned ends = 0u) {
     const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
     const unsigned bA = __ballot_sync(FULL, oA), bB = __ballot_sync(FULL, oB);
     const bool allwet = (bA & bB) == FULL;
@@ -254,6 +286,13 @@ __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 
         if (!wA) ghost_left(W.y, C.y, m.inv_l.y, FL.p.y, FL.q.y, FL.t.y);
         if (!wetR) ghost_right(W.y, C.y, m.inv_r.y, FR.p.y, FR.q.y, FR.t.y);
     }
+    float2 gE = v2(0.f), gW = v2(0.f), gC = v2(0.f);   // open-edge ghosts of A (.x) and B (.y)
+    if (OPEN && ends) {
+        if ((ends & 1u) && wA) open_flux(E.x, W.x, T.x, D.x, C.x, m.inv_l.x, false, FL.p.x, FL.q.x, FL.t.x, gE.x, gW.x, gC.x);
+        if ((ends & 2u) && wA) open_flux(E.x, W.x, T.x, D.x, C.x, m.inv_r.x, true, FR.p.x, FR.q.x, FR.t.x, gE.x, gW.x, gC.x);
+        if ((ends & 4u) && wB) open_flux(E.y, W.y, T.y, D.y, C.y, m.inv_l.y, false, FL.p.y, FL.q.y, FL.t.y, gE.y, gW.y, gC.y);
+        if ((ends & 8u) && wB) open_flux(E.y, W.y, T.y, D.y, C.y, m.inv_r.y, true, FR.p.y, FR.q.y, FR.t.y, gE.y, gW.y, gC.y);
+    }
     Flux2 F1;
     if (S1) {
         // eq. (solver1): flux between the two neighbours of each node, mirror ghosts for dry ones
@@ -267,6 +306,12 @@ __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 
             if (!wB) { re.x = E.x; rw.x = -W.x; rt.x = T.x; rd.x = D.x; rc.x = C.x; }
             if (!wA) { le.y = E.y; lw.y = -W.y; lt.y = T.y; ld.y = D.y; lc.y = C.y; }
             if (!wetR) { re.y = E.y; rw.y = -W.y; rt.y = T.y; rd.y = D.y; rc.y = C.y; }
+        }
+        if (OPEN && ends) {                // an open edge's neighbour is its ghost
+            if (ends & 1u) { le.x = gE.x; lw.x = gW.x; lt.x = T.x; ld.x = D.x; lc.x = gC.x; }
+            if (ends & 2u) { re.x = gE.x; rw.x = gW.x; rt.x = T.x; rd.x = D.x; rc.x = gC.x; }
+            if (ends & 4u) { le.y = gE.y; lw.y = gW.y; lt.y = T.y; ld.y = D.y; lc.y = gC.y; }
+            if (ends & 8u) { re.y = gE.y; rw.y = gW.y; rt.y = T.y; rd.y = D.y; rc.y = gC.y; }
         }
         F1 = iface2(le, lw, lt, ld, lc, re, rw, rt, rd, rc, mul2(m.k2, v2(K.inv_dt2)));
     }
@@ -332,8 +377,11 @@ struct YMarch2 {
 
     // eq. (solver1): flux between rows k-3 and k-1 around row k-2 (P), with mirror ghosts
     // of P for a neighbour row that is dry after (b)
+    // of P for a neighbour row that is dry after (b); at an open edge (pend 1: row k-2 is the
+    // first row, 2: the last) the neighbour beyond it is the open ghost (ge, gw, gc)
     __device__ __forceinline__ Flux2 f1(const YRow& P, const YRow& B1, bool open, float k2,
-                                        const SweepConst& K) const {
+                                        const SweepConst& K, int pend = 0, float2 ge = v2(0.f),
+                                        float2 gw = v2(0.f), float2 gc = v2(0.f)) const {
         float2 le = pe, lw = pw, lt = pt, ld = pd, lc = pc;
         float2 re = B1.e, rw = B1.w, rt = B1.t, rd = B1.d, rc = B1.c;
         if (!open) {
@@ -342,16 +390,19 @@ struct YMarch2 {
             if (!B1.wA) { re.x = P.e.x; rw.x = -P.w.x; rt.x = P.t.x; rd.x = P.d.x; rc.x = P.c.x; }
             if (!B1.wB) { re.y = P.e.y; rw.y = -P.w.y; rt.y = P.t.y; rd.y = P.d.y; rc.y = P.c.y; }
         }
+        if (pend == 1) { le = ge; lw = gw; lt = P.t; ld = P.d; lc = gc; }
+        if (pend == 2) { re = ge; rw = gw; rt = P.t; rd = P.d; rc = gc; }
         return iface2(le, lw, lt, ld, lc, re, rw, rt, rd, rc, v2(k2 * K.inv_dt2));
     }
 
     // m2: metric of row k-2 (1/dy_{j-1}, 1/dy_j, dt^2/(dy_{j-1}+dy_j), dt tan(phi)/R).
     // emit(e, w, t, d) receives the finished row k-3; o0A/o0B: the incoming row's wet marks.
     // careA/careB: whether this lane's columns are emitted; the others may compute anything.
-    template <int PH, bool SRC, bool FRIC, bool S1, class Emit>
+    // pend: row k-2 is the first row of the grid at an open edge (1) or the last (2), else 0.
+    template <int PH, bool SRC, bool FRIC, bool S1, bool OPEN, class Emit>
     __device__ __forceinline__ void push(float2 E0, float2 W0, float2 T0, float2 D0, bool o0A, bool o0B,
                                          float4 m2, const SweepConst& K, bool careA, bool careB,
-                                         Emit&& emit) {
+                                         Emit&& emit, int pend = 0) {
         YRow& P = bank[PH];
         YRow& B1 = bank[1 - PH];
         Flux2& F3 = fb[PH];
@@ -399,9 +450,22 @@ struct YMarch2 {
             if (P.wA && !B1.wA) ghost_right(P.w.x, P.c.x, m2.y, R.p.x, R.q.x, R.t.x);
             if (P.wB && !f3B) ghost_left(P.w.y, P.c.y, m2.x, L.p.y, L.q.y, L.t.y);
             if (P.wB && !B1.wB) ghost_right(P.w.y, P.c.y, m2.y, R.p.y, R.q.y, R.t.y);
+            float2 ge = v2(0.f), gw = v2(0.f), gc = v2(0.f);
+            if (OPEN && pend) {
+                // an open outer edge: the flux across it from the open ghost (wet nodes only)
+                const bool right = pend == 2;
+                Flux2 Fo;
+                open_flux(P.e.x, P.w.x, P.t.x, P.d.x, P.c.x, right ? m2.y : m2.x, right, Fo.p.x, Fo.q.x, Fo.t.x,
+                          ge.x, gw.x, gc.x);
+                open_flux(P.e.y, P.w.y, P.t.y, P.d.y, P.c.y, right ? m2.y : m2.x, right, Fo.p.y, Fo.q.y, Fo.t.y,
+                          ge.y, gw.y, gc.y);
+                Flux2& S = right ? R : L;
+                if (P.wA) { S.p.x = Fo.p.x; S.q.x = Fo.q.x; S.t.x = Fo.t.x; }
+                if (P.wB) { S.p.y = Fo.p.y; S.q.y = Fo.q.y; S.t.y = Fo.t.y; }
+            }
             float2 ne, nw, nt;
             Flux2 F1;
-            if (S1) F1 = f1(P, B1, false, m2.z, K);
+            if (S1) F1 = f1(P, B1, false, m2.z, K, pend, ge, gw, gc);
             node_update2<SRC, FRIC, S1>(P.e, P.w, P.t, P.d, P.c, L, R, v2(m2.z), v2(m2.w), K, ne, nw, nt, &F1);
             if (!P.wA) { ne.x = P.e.x; nw.x = P.w.x; nt.x = P.t.x; }
             if (!P.wB) { ne.y = P.e.y; nw.y = P.w.y; nt.y = P.t.y; }

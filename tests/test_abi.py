@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(built):
 
 
 def test_abi_version_without_gpu(built):
-    assert pk.cliffs_abi_version() == 1
+    assert pk.cliffs_abi_version() == 2
     assert pk.cliffs_last_error() == ""
 
 
@@ -57,7 +57,7 @@ int main(void) {
   F(cliffs_config, solver); F(cliffs_config, alternate); F(cliffs_config, maxout);
   F(cliffs_config, gout); F(cliffs_config, bndout); F(cliffs_config, n_gauges);
   F(cliffs_config, gauge_ixiy); F(cliffs_config, n_nests); F(cliffs_config, nests);
-  F(cliffs_config, stream);
+  F(cliffs_config, stream); F(cliffs_config, open_edges);
   F(cliffs_nest, x0); F(cliffs_nest, y0); F(cliffs_nest, dx); F(cliffs_nest, dy);
   F(cliffs_nest, nx); F(cliffs_nest, ny);
   return 0;

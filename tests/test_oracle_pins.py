@@ -661,3 +661,89 @@ def test_initial_condition_interpolation_exact_for_linear_fields_and_zero_outsid
     # master nodes on source nodes take the source values
     same = oracle.interp_initial(sx, sy, sx, sy, f)
     assert np.array_equal(same, f)
+
+
+# ----------------------------------------------------------------------------------------
+# Open outer edges (the paper gives no condition): the ghost beyond an edge node carries the
+# node's outgoing Riemann invariant and still water's incoming one.
+
+def _channel(n=400, dx=50.0, d0=10.0):
+    x = dx * np.arange(n)
+    return x, np.full((1, n), d0)
+
+
+def test_open_edges_keep_a_lake_at_rest():
+    nx, ny = 40, 30
+    x, y = 100.0 * np.arange(nx), 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = 20.0 + 10.0 * np.sin(X / 700.0) * np.cos(Y / 500.0)
+    p = oracle.params(nx, ny, 1.0, manning_n2=6.25e-4, open_edges=15)
+    r = oracle.run(p, x, y, d, np.zeros((ny, nx)), nsteps=50)
+    assert np.abs(r["eta"]).max() < 1e-12 and np.abs(r["u"]).max() < 1e-12 and np.abs(r["v"]).max() < 1e-12
+
+
+def test_open_edge_lets_a_simple_wave_leave():
+    """A right-going linear wave (u = eta sqrt(g/d)) on a flat channel leaves through an open
+    east edge: what stays behind is below 1 % of the amplitude; a wall sends it all back."""
+    x, d = _channel()
+    c0 = np.sqrt(9.81 * 10.0)
+    A, x0, sig = 0.05, 8000.0, 800.0
+    eta0 = A * np.exp(-((x - x0) ** 2) / (2 * sig ** 2))
+    u0 = eta0 * c0 / 10.0
+    dt = 0.5 * 50.0 / c0
+    steps = int((x[-1] - x0 + 6 * sig) / c0 / dt) + 40
+    res = {}
+    for name, edges in (("open", 2), ("wall", 0)):
+        p = oracle.params(len(x), 1, dt, open_edges=edges)
+        r = oracle.run(p, x, np.zeros(1), d, eta0[None, :], u0[None, :], nsteps=steps)
+        res[name] = np.abs(r["eta"]).max()
+    assert res["open"] < 0.01 * A, res
+    assert res["wall"] > 0.5 * A, res
+
+
+def test_open_edges_drain_a_raised_level_toward_still_water():
+    """A uniform raised level at rest in a channel open at both ends runs out toward the
+    still-water level of the incoming invariants (a zero-gradient edge would keep it)."""
+    x, d = _channel(n=200)
+    c0 = np.sqrt(9.81 * 10.0)
+    dt = 0.5 * 50.0 / c0
+    eta0 = np.full((1, len(x)), 0.2)
+    p = oracle.params(len(x), 1, dt, open_edges=3)
+    r = oracle.run(p, x, np.zeros(1), d, eta0, nsteps=int(6 * x[-1] / c0 / dt))
+    assert np.abs(r["eta"]).max() < 0.02 * 0.2
+    closed = oracle.run(oracle.params(len(x), 1, dt), x, np.zeros(1), d, eta0, nsteps=200)
+    assert np.abs(closed["eta"] - eta0).max() < 1e-12
+
+
+def test_open_edges_columns_equal_rows():
+    """The S and N bits act on a column exactly as W and E act on a row."""
+    x, d = _channel(n=150)
+    c0 = np.sqrt(9.81 * 10.0)
+    dt = 0.5 * 50.0 / c0
+    eta0 = 0.3 * np.exp(-((x - 5000.0) ** 2) / (2 * 600.0 ** 2))
+    u0 = 0.2 * np.sin(x / 900.0)
+    for ew, sn in ((1, 4), (2, 8), (3, 12)):
+        rx = oracle.run(oracle.params(len(x), 1, dt, open_edges=ew), x, np.zeros(1), d, eta0[None, :],
+                        u0[None, :], nsteps=180)
+        ry = oracle.run(oracle.params(1, len(x), dt, open_edges=sn), np.zeros(1), x, d.T.copy(), eta0[:, None],
+                        None, u0[:, None], nsteps=180)
+        assert np.array_equal(rx["eta"][0], ry["eta"][:, 0])
+        assert np.array_equal(rx["u"][0], ry["v"][:, 0])
+
+
+def test_open_edges_let_a_radial_wave_leave_a_square():
+    """A radial wave in a square open on all four sides: once it has passed the edges little
+    is left (oblique incidence reflects a little); with walls it stays in the basin."""
+    n = 120
+    x = 100.0 * np.arange(n)
+    X, Y = np.meshgrid(x, x)
+    d = np.full((n, n), 20.0)
+    c0 = np.sqrt(9.81 * 20.0)
+    dt = 0.5 * 100.0 / c0
+    eta0 = 0.1 * np.exp(-((X - 6000.0) ** 2 + (Y - 6000.0) ** 2) / (2 * 700.0 ** 2))
+    steps = int(1.6 * 6000.0 / c0 / dt)
+    r = oracle.run(oracle.params(n, n, dt, open_edges=15), x, x, d, eta0, nsteps=steps)
+    w = oracle.run(oracle.params(n, n, dt), x, x, d, eta0, nsteps=steps)
+    E_open = np.sum(r["eta"] ** 2 + (20.0 / 9.81) * (r["u"] ** 2 + r["v"] ** 2))
+    E_wall = np.sum(w["eta"] ** 2 + (20.0 / 9.81) * (w["u"] ** 2 + w["v"] ** 2))
+    assert E_open < 0.05 * E_wall, (E_open, E_wall)
