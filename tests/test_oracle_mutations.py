@@ -79,6 +79,18 @@ MUTATIONS = [
      "return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));",
      "return Dual(a.v / b.v, (a.d * b.v + a.v * b.d) / (b.v * b.v));",
      ["test_tlm_matches_central_differences"]),
+    ("open edge as a zero-gradient ghost",
+     "    const T p = right ? C.w + 2.0 * c : T(2.0 * c0);\n    const T q = right ? T(-2.0 * c0) : C.w - 2.0 * c;",
+     "    const T p = C.w + 2.0 * c;\n    const T q = C.w - 2.0 * c;",
+     ["test_open_edges_drain_a_raised_level_toward_still_water"]),
+    ("open edge with the ends' invariants swapped",
+     "if (j == n - 1 && (open & 2)) R = open_ghost(C, true, g);",
+     "if (j == n - 1 && (open & 2)) R = open_ghost(C, false, g);",
+     ["test_open_edge_lets_a_simple_wave_leave"]),
+    ("incoming invariant of still water with the wrong sign",
+     "const T q = right ? T(-2.0 * c0) : C.w - 2.0 * c;",
+     "const T q = right ? T(2.0 * c0) : C.w - 2.0 * c;",
+     ["test_open_edges_keep_a_lake_at_rest", "test_open_edge_lets_a_simple_wave_leave"]),
 ]
 
 
