@@ -59,7 +59,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "cliffs_step.cu", "internal.h"):
+    for f in ("sweep.cuh", "step_kernels.cuh", "cliffs_step.cu", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1410_0753_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

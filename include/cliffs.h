@@ -86,7 +86,8 @@ typedef struct cliffs_config {
                                    beyond a wet edge node carries the node's outgoing Riemann
                                    invariant and the incoming invariant of still water at the
                                    node's depth (sqrt(g max(d, 0))), the node's depth and
-                                   transverse velocity. Not taken by the adjoint (ERR_ARG). */
+                                   transverse velocity; the adjoint takes the ghost as a
+                                   function of the edge node. */
 } cliffs_config;
 
 /* Create a grid with the given parameters. Allocates the device state ([batch][ny][nx] of

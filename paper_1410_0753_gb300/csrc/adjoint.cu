@@ -215,6 +215,27 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     bR.e += cR * (0.5f * GRAV) * rcp_approx(R.c);
 }
 
+// ------------------------------------------------------------------ open outer edges
+// The open ghost of a wet edge node C (the forward's open_ghost, as a stencil node) and the
+// transpose of its map: with delta = c - c0 the ghost is w_g = w/2 + s delta,
+// c_g = c/2 + s w/4 + c0/2 (s = +1 at the right end, -1 at the left; c_g = 0 when clamped),
+// eta_g = c_g^2/g - d, t_g = t, so dw_g = dw/2 + s dc, dc_g = s dw/4 + dc/2 with
+// dc = g/(2c) deta, and deta_g = 2 c_g/g dc_g.
+__device__ __forceinline__ ANode a_open_ghost(const ANode& C, bool right) {
+    float eg, wg, cg;
+    open_ghost(C.e, C.w, C.d, C.c, right, eg, wg, cg);
+    return ANode{eg, wg, C.t, C.d, cg};
+}
+__device__ __forceinline__ void a_open_ghost_adj(const ANode& C, const ANode& Gh, bool right, const ABar& bg,
+                                                 ABar& bC) {
+    const float s = right ? 1.f : -1.f;
+    const float gcg = Gh.c > 0.f ? bg.e * 2.f * Gh.c * INV_GRAV : 0.f;   // adjoint of c_g
+    const float gc = s * bg.w + 0.5f * gcg;                               // adjoint of c
+    bC.w += 0.5f * bg.w + s * 0.25f * gcg;
+    bC.e += gc * (0.5f * GRAV) * rcp_approx(C.c);
+    bC.t += bg.t;
+}
+
 // ------------------------------------------------------------------ packed open water
 // The same adjoint of (d) for the two nodes of a lane at once (packed FP32x2), for windows
 // where every node is wet: real neighbours, no ghosts.
@@ -366,11 +387,13 @@ __device__ __forceinline__ void nbr(const int (&x)[2], int (&l)[2], int (&r)[2])
 // Adjoint of one sweep of a 64-node line window. In: the sweep's input (e, w, t, d) and the
 // adjoint (ge, gw, gt) of its output. Out: the adjoint of its input, exact at window
 // nodes 6..57.
+// ends: this lane's nodes at open outer edges, bits 1 node 0 left, 2 node 0 right, 4 node 1
+// left, 8 node 1 right (their outside neighbour is the open ghost instead of a mirror).
 template <bool SRC, bool S1>
 __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&w)[2], const float (&t)[2],
                                              const float (&d)[2], const float (&ge)[2], const float (&gw)[2],
                                              const float (&gt)[2], const AMet (&m)[2], const SweepConst& K,
-                                             float (&oe)[2], float (&ow)[2], float (&ot)[2]) {
+                                             float (&oe)[2], float (&ow)[2], float (&ot)[2], unsigned ends = 0u) {
     // (a) wet marks at the start of the sweep
     int o[2], fl[2];
 #pragma unroll
@@ -444,6 +467,10 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         const ANode G{e1[i], -w1[i], t1[i], d[i], c1[i]};
         Ln[i] = wtL[i] ? ANode{e1L[i], w1L[i], t1L[i], dL[i], cL[i]} : G;
         Rn[i] = wtR[i] ? ANode{e1R[i], w1R[i], t1R[i], dR[i], cR[i]} : G;
+        if (ends && wt[i]) {
+            if (ends & (1u << (2 * i))) Ln[i] = a_open_ghost(Cn[i], false);
+            if (ends & (2u << (2 * i))) Rn[i] = a_open_ghost(Cn[i], true);
+        }
         if (wt[i]) {
             float ee, ww;
             a_dstage<SRC, S1>(Ln[i], Cn[i], Rn[i], m[i], K, ee, ww);
@@ -485,11 +512,17 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
         if (wt[i]) {
             bC[i] = ABar{0.f, 0.f, 0.f};
             a_dstage_adj<SRC, S1>(Ln[i], Cn[i], Rn[i], m[i], K, De, Dw, gt[i], bL[i], bC[i], bR[i]);
-            if (!wtL[i]) {                       // the ghost mirrors C: (eta, -w, t)
+            if (ends & (1u << (2 * i))) {        // the open ghost is a function of C
+                a_open_ghost_adj(Cn[i], Ln[i], false, bL[i], bC[i]);
+                bL[i] = ABar{0.f, 0.f, 0.f};
+            } else if (!wtL[i]) {                // the ghost mirrors C: (eta, -w, t)
                 bC[i].e += bL[i].e; bC[i].w -= bL[i].w; bC[i].t += bL[i].t;
                 bL[i] = ABar{0.f, 0.f, 0.f};
             }
-            if (!wtR[i]) {
+            if (ends & (2u << (2 * i))) {
+                a_open_ghost_adj(Cn[i], Rn[i], true, bR[i], bC[i]);
+                bR[i] = ABar{0.f, 0.f, 0.f};
+            } else if (!wtR[i]) {
                 bC[i].e += bR[i].e; bC[i].w -= bR[i].w; bC[i].t += bR[i].t;
                 bR[i] = ABar{0.f, 0.f, 0.f};
             }
@@ -578,7 +611,12 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
             for (int i = 0; i < 2; ++i) { m[i].il *= f; m[i].ir *= f; m[i].k2 *= f; }
         }
         float oe[2], ow[2], ot[2];
-        line_adjoint<DIR == 1 && SPH, S1>(e, w, t, d, ge, gw, gt, m, K, oe, ow, ot);
+        unsigned ends = 0u;
+        if (A.open_lo | A.open_hi) {
+            if (A.open_lo) ends |= (pA == 0 ? 1u : 0u) | (pA + 1 == 0 ? 4u : 0u);
+            if (A.open_hi) ends |= (pA == A.npos - 1 ? 2u : 0u) | (pA + 1 == A.npos - 1 ? 8u : 0u);
+        }
+        line_adjoint<DIR == 1 && SPH, S1>(e, w, t, d, ge, gw, gt, m, K, oe, ow, ot, ends);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int q = 2 * lane + i - AHALO;
@@ -608,7 +646,7 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
 
 // The forward x-sweep of a stored state, written transposed ([nx][tpitch]): the same
 // window loads, edge treatment and sweep as the fused step kernel.
-template <bool SPH, bool FRIC, bool S1>
+template <bool SPH, bool FRIC, bool S1, bool OPEN>
 __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, const float* __restrict__ pe,
                                                           const float* __restrict__ pu,
                                                           const float* __restrict__ pv, float* te, float* tu,
@@ -637,7 +675,12 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
             const float2 f = v2(a.xrow[r]);
             m.inv_l = mul2(m.inv_l, f); m.inv_r = mul2(m.inv_r, f); m.k2 = mul2(m.k2, f);
         }
-        xsweep2<FRIC, S1>(E, U, V, D, m, K, lane);
+        unsigned ends = 0u;                         // open outer edges among this lane's columns
+        if (OPEN) {
+            if (a.open_edges & 1) ends |= (cA == 0 ? 1u : 0u) | (cA + 1 == 0 ? 4u : 0u);
+            if (a.open_edges & 2) ends |= (cA == a.nx - 1 ? 2u : 0u) | (cA + 1 == a.nx - 1 ? 8u : 0u);
+        }
+        xsweep2<FRIC, S1, OPEN>(E, U, V, D, m, K, lane, ends);
         const float vals[3][2] = {{E.x, E.y}, {U.x, U.y}, {V.x, V.y}};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -717,15 +760,20 @@ cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_
 cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
                             float* tu, float* tv, int tpitch, cudaStream_t s) {
     const dim3 grid((a.nx + XOUT - 1) / XOUT, (a.ny + ALINES - 1) / ALINES);
-    static const void* const t[8] = {
-        (const void*)k_adj_xfwd<false, false, false>, (const void*)k_adj_xfwd<true, false, false>,
-        (const void*)k_adj_xfwd<false, true, false>, (const void*)k_adj_xfwd<true, true, false>,
-        (const void*)k_adj_xfwd<false, false, true>, (const void*)k_adj_xfwd<true, false, true>,
-        (const void*)k_adj_xfwd<false, true, true>, (const void*)k_adj_xfwd<true, true, true>};
+    static const void* const t[16] = {
+        (const void*)k_adj_xfwd<false, false, false, false>, (const void*)k_adj_xfwd<true, false, false, false>,
+        (const void*)k_adj_xfwd<false, true, false, false>, (const void*)k_adj_xfwd<true, true, false, false>,
+        (const void*)k_adj_xfwd<false, false, true, false>, (const void*)k_adj_xfwd<true, false, true, false>,
+        (const void*)k_adj_xfwd<false, true, true, false>, (const void*)k_adj_xfwd<true, true, true, false>,
+        (const void*)k_adj_xfwd<false, false, false, true>, (const void*)k_adj_xfwd<true, false, false, true>,
+        (const void*)k_adj_xfwd<false, true, false, true>, (const void*)k_adj_xfwd<true, true, false, true>,
+        (const void*)k_adj_xfwd<false, false, true, true>, (const void*)k_adj_xfwd<true, false, true, true>,
+        (const void*)k_adj_xfwd<false, true, true, true>, (const void*)k_adj_xfwd<true, true, true, true>};
     StepArgs aa = a;
     void* args[] = {&aa, (void*)&e, (void*)&u, (void*)&v, &te, &tu, &tv, &tpitch};
-    return cudaLaunchKernel(t[(a.sph ? 1 : 0) + (a.dt_gn2 > 0.f ? 2 : 0) + (a.inv_dt2_s1 > 0.f ? 4 : 0)], grid,
-                            dim3(AWARPS * 32), args, 0, s);
+    return cudaLaunchKernel(t[(a.sph ? 1 : 0) + (a.dt_gn2 > 0.f ? 2 : 0) + (a.inv_dt2_s1 > 0.f ? 4 : 0) +
+                              (a.open_edges ? 8 : 0)],
+                            grid, dim3(AWARPS * 32), args, 0, s);
 }
 
 cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,

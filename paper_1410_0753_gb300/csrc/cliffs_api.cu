@@ -1389,7 +1389,6 @@ int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
         return CLIFFS_OK;
     }
     if (g->kind != 0 || g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid with batch == 1");
-    if (g->cfg.open_edges) return set_err(CLIFFS_ERR_ARG, "the adjoint takes reflecting outer edges only");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->step != 0) return set_err(CLIFFS_ERR_STATE, "record from the initial state (no steps since set_initial)");
     g->rec_K = checkpoint_every;
@@ -1458,7 +1457,6 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
-    if (g->cfg.open_edges) return set_err(CLIFFS_ERR_ARG, "the adjoint takes reflecting outer edges only");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);
@@ -1580,6 +1578,8 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
         A->transverse = a.transverse;
         A->inv_dt2_s1 = a.inv_dt2_s1;
     }
+    X.open_lo = g->cfg.open_edges & 1; X.open_hi = (g->cfg.open_edges >> 1) & 1;     // W, E
+    Y.open_lo = (g->cfg.open_edges >> 2) & 1; Y.open_hi = (g->cfg.open_edges >> 3) & 1;   // S, N
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
         CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));

@@ -94,6 +94,7 @@ struct AdjLineArgs {
     float hmin, dwall, half_dt, dt_gn2;
     int transverse;
     float inv_dt2_s1;                // 1/dt^2 with eq. (solver1), else 0
+    int open_lo, open_hi;            // the line's first / last node is at an open outer edge
 };
 
 cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s);

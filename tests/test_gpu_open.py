@@ -144,15 +144,45 @@ def test_open_edges_persistent_run_equals_per_step():
     g.close()
 
 
-def test_open_edges_argument_checks_and_adjoint():
+def test_open_edges_argument_checks():
     with pytest.raises(CliffsError) as e:
         CliffsGrid(40, 30, 1.0, open_edges=16)
     assert e.value.code == ERR_ARG
-    x, y, d64, eta0, _ = _basin(40, 30)
-    g = CliffsGrid(40, 30, 1.0, open_edges=1)
+    with pytest.raises(CliffsError) as e:
+        CliffsGrid(40, 30, 1.0, open_edges=-1)
+    assert e.value.code == ERR_ARG
+
+
+@pytest.mark.parametrize("variant", ["solver2", "solver1", "alternate"])
+def test_adjoint_with_open_edges_dot_product_against_oracle_tlm(variant):
+    """<dL/d eta0, delta> from the GPU adjoint against the oracle's tangent model through the
+    open ghosts (1e-4 of the largest term, as in test_gpu_adjoint.py), gauges on the W, N and
+    E edge nodes and inside, directions that reach the edges."""
+    nx, ny, steps = 150, 128, 200
+    x, y, d64, eta0, gauges = _basin(nx, ny)
+    kw = {"solver1": dict(solver=1), "alternate": dict(alternate=1)}.get(variant, {})
+    g = CliffsGrid(nx, ny, 1.0, h_min=0.01, manning_n2=6.25e-4, gauges=[tuple(q) for q in gauges],
+                   open_edges=15, **kw)
     g.set_bathy(x, y, d64, False)
     g.set_initial(eta0.astype(np.float32))
-    with pytest.raises(CliffsError) as e:
-        g.adjoint(3, None)
-    assert e.value.code == ERR_ARG
+    rng = np.random.default_rng(29)
+    seed = rng.standard_normal((steps + 1, len(gauges))).astype(np.float32)
+    grad = g.adjoint(steps, seed, checkpoint_every=37).astype(np.float64)
+    assert np.isfinite(grad).all()
+    p = oracle.params(nx, ny, 1.0, h_min=0.01, manning_n2=6.25e-4, open_edges=15, **kw)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    worst = 0.0
+    for k, (cx, cy, sig) in enumerate(((8.0, 85.0, 10.0), (40.0, 120.0, 9.0), (140.0, 70.0, 10.0), (75.0, 64.0, 30.0))):
+        delta = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig ** 2))
+        if k == 3:
+            delta = delta + 0.1 * rng.standard_normal(delta.shape)
+        _, gtan, _, _ = oracle.run_tlm(p, x, y, d64, eta0, delta, nsteps=steps, gauges=gauges)
+        terms = seed.astype(np.float64) * gtan
+        want = terms.sum()
+        got = float((grad * delta).sum())
+        scale = max(np.abs(terms).max(), 1e-12)
+        err = abs(got - want) / scale
+        worst = max(worst, err)
+        assert err <= 1e-4, (variant, k, got, want, scale)
+    P.report("adjoint_dot_open_" + variant, rel_err=worst)
     g.close()

@@ -751,3 +751,29 @@ def test_open_edges_let_a_radial_wave_leave_a_square():
     E_open = np.sum(r["eta"] ** 2 + (20.0 / 9.81) * (r["u"] ** 2 + r["v"] ** 2))
     E_wall = np.sum(w["eta"] ** 2 + (20.0 / 9.81) * (w["u"] ** 2 + w["v"] ** 2))
     assert E_open < 0.05 * E_wall, (E_open, E_wall)
+
+
+def test_tlm_with_open_edges_matches_central_differences():
+    """The tangent model through the open ghost (a function of the edge node) against central
+    differences, with the perturbation crossing the W and N edges."""
+    nx, ny = 36, 28
+    x, y = 100.0 * np.arange(nx), 100.0 * np.arange(ny)
+    X, Y = np.meshgrid(x, y)
+    d = 15.0 + 5.0 * np.cos(X / 800.0) * np.sin(Y / 600.0)
+    eta0 = 0.3 * np.exp(-((X - 800.0) ** 2 + (Y - 2000.0) ** 2) / (2 * 400.0 ** 2))
+    dirn = np.exp(-((X - 500.0) ** 2 + (Y - 2300.0) ** 2) / (2 * 350.0 ** 2))
+    gauges = [(0, 20), (1, 24), (10, 27), (20, 14)]
+    p = oracle.params(nx, ny, 2.0, manning_n2=6.25e-4, open_edges=15)
+    steps = 60
+    gval, gtan, _, _ = oracle.run_tlm(p, x, y, d, eta0, dirn, nsteps=steps, gauges=gauges)
+    h = 1e-4
+    rp = oracle.run(p, x, y, d, eta0 + h * dirn, nsteps=steps, gout=1, gauges=gauges)
+    rm = oracle.run(p, x, y, d, eta0 - h * dirn, nsteps=steps, gout=1, gauges=gauges)
+    fd = (rp["gauges"][:, :, 0] - rm["gauges"][:, :, 0]) / (2 * h)
+    scale = np.abs(gtan).max()
+    assert scale > 1e-2
+    assert np.abs(fd - gtan).max() <= 1e-6 * scale, np.abs(fd - gtan).max() / scale
+    # the tangent sees the open edges: with walls it differs
+    _, gw, _, _ = oracle.run_tlm(oracle.params(nx, ny, 2.0, manning_n2=6.25e-4), x, y, d, eta0, dirn,
+                                 nsteps=steps, gauges=gauges)
+    assert np.abs(gw - gtan).max() > 1e-2 * scale
