@@ -197,14 +197,24 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
  * clamp taken as in the forward run. The grid's state, records and maxima are unchanged.
  * Under boundary input each adjoint step zeroes the input edges of the adjoint state (the
  * edge values were overwritten before the step) before the gauge records of that state are
- * added. dL_dgauges may be NULL (the gradient is then zero). 2D grids with batch == 1 only.
+ * added. dL_dgauges may be NULL (the gradient is then zero). 2D grids; on a batched grid
+ * this is scenario 0 (cliffs_adjoint_scenario takes any). With the alternating order the
+ * steps keep the forward's parity (steps counted from set_initial).
  * Memory: (checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per node,
  * kept for later calls.
- * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, batch > 1, n < 1,
- * checkpoint_every < 1, NULL output); ERR_UNSTABLE, ERR_TIMEOUT from the forward
+ * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 1, checkpoint_every < 1,
+ * NULL output); ERR_UNSTABLE, ERR_TIMEOUT from the forward
  * recomputation; ERR_CUDA. */
 int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                      float* dL_deta0);
+
+/* cliffs_adjoint_n for scenario `scenario` of a batched grid (cliffs_adjoint_n is scenario 0):
+ * X_0 is that scenario's current state, dL_dgauges its gauge records' adjoint. With
+ * per-scenario durations (cliffs_set_durations) the scenario must still run n more steps.
+ * The other scenarios are untouched. Errors: as cliffs_adjoint_n, and ERR_ARG for a
+ * scenario outside 0..batch-1 or a run that stops before n steps. */
+int cliffs_adjoint_scenario(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
+                            const float* dL_dgauges, float* dL_deta0);
 
 /* Record the forward run for the adjoint (no counterpart in the paper). With
  * checkpoint_every = K > 0, called right after cliffs_set_initial, the initial state and then

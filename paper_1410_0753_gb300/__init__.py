@@ -29,7 +29,7 @@ __all__ = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
-    "EXPORTED",
+    "cliffs_adjoint_scenario", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -44,6 +44,7 @@ EXPORTED = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
+    "cliffs_adjoint_scenario",
 ]
 
 
@@ -90,6 +91,7 @@ def lib():
             "cliffs_step_n": ([vp, C.c_int64], C.c_int),
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
+            "cliffs_adjoint_scenario": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
@@ -218,6 +220,12 @@ def cliffs_adjoint_n(g, n, checkpoint_every, dL_dgauges, out):
     gauge-eta adjoint seed ``dL_dgauges`` ([n // gout + 1][G] float32, or None)."""
     ps, ks = _ptr(dL_dgauges, np.float32)
     _check(lib().cliffs_adjoint_n(g, int(n), int(checkpoint_every), ps, _out_ptr(out)))
+
+
+def cliffs_adjoint_scenario(g, scenario, n, checkpoint_every, dL_dgauges, out):
+    """cliffs_adjoint_n for one scenario of a batched grid."""
+    ps, ks = _ptr(dL_dgauges, np.float32)
+    _check(lib().cliffs_adjoint_scenario(g, int(scenario), int(n), int(checkpoint_every), ps, _out_ptr(out)))
 
 
 def cliffs_state_ptrs(g, scenario):
@@ -473,10 +481,11 @@ class CliffsGrid:
         cliffs_adjoint_velocity(self.h, du, dv)
         return du, dv
 
-    def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None):
+    def adjoint(self, n, dL_dgauges, checkpoint_every=100, out=None, scenario=0):
         """Gradient with respect to the current free surface of a loss whose derivative with
-        respect to the gauge eta records of the next n steps is ``dL_dgauges``."""
+        respect to the gauge eta records of the next n steps is ``dL_dgauges`` (of scenario
+        ``scenario`` on a batched grid)."""
         if out is None:
             out = np.empty((self.ny, self.nx), np.float32)
-        cliffs_adjoint_n(self.h, n, checkpoint_every, dL_dgauges, out)
+        cliffs_adjoint_scenario(self.h, scenario, n, checkpoint_every, dL_dgauges, out)
         return out

@@ -1367,12 +1367,17 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     return CLIFFS_OK;
 }
 
-static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                         float* dL_deta0, const float* recorded);
 
 int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                      float* dL_deta0) {
-    return adjoint_core(g, n, checkpoint_every, dL_dgauges, dL_deta0, nullptr);
+    return adjoint_core(g, 0, n, checkpoint_every, dL_dgauges, dL_deta0, nullptr);
+}
+
+int cliffs_adjoint_scenario(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
+                            const float* dL_dgauges, float* dL_deta0) {
+    return adjoint_core(g, scenario, n, checkpoint_every, dL_dgauges, dL_deta0, nullptr);
 }
 
 int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
@@ -1403,7 +1408,7 @@ int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_d
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
     if (g->rec_K <= 0 || g->rec_n < 1) return set_err(CLIFFS_ERR_STATE, "no recorded run");
-    return adjoint_core(g, g->rec_n, g->rec_K, dL_dgauges, dL_deta0, g->rec_ckpt);
+    return adjoint_core(g, 0, g->rec_n, g->rec_K, dL_dgauges, dL_deta0, g->rec_ckpt);
 }
 
 // Adjoint of a y-first step j of the alternating order, X_{j+1} = x-sweep(y-sweep(X_j)),
@@ -1450,14 +1455,18 @@ static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineA
 
 // The adjoint steps of cliffs_adjoint_n; `recorded` holds the checkpoints of a recorded run
 // (X_0 included), else a checkpoint pass from the grid's current state makes them.
-static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
+static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                         float* dL_deta0, const float* recorded) {
     g_err[0] = 0;
     if (!g || !dL_deta0) return set_err(CLIFFS_ERR_ARG, "null argument");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
-    if (g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs batch == 1");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d outside 0..%d", scenario, g->B - 1);
+    if (recorded && g->B != 1) return set_err(CLIFFS_ERR_ARG, "a recorded run needs batch == 1");
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
+    if (!recorded && !g->limit_h.empty() && g->step + n > g->limit_h[scenario])
+        return set_err(CLIFFS_ERR_ARG, "scenario %d stops after %lld steps, before %lld more", scenario,
+                       (long long)g->limit_h[scenario], (long long)n);
     cudaStream_t s = g->stream;
     const int nx = g->nx, ny = g->ny, K = (int)std::min<int64_t>(checkpoint_every, n);
     const long long P = g->plane;                          // row-major plane, floats
@@ -1519,11 +1528,11 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     a.limit = nullptr;
     a.step = 1;
     // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating order)
-    const long long s0 = recorded ? 0 : g->step;           // steps done before X_0
+    const long long s0 = recorded ? 0 : steps_of(g, scenario);   // steps done before X_0
     auto fwd = [&](int from, int to, long long j) -> int {
         a.eta_in = slot(from); a.u_in = slot(from) + P; a.v_in = slot(from) + 2 * P;
         a.eta_out = slot(to); a.u_out = slot(to) + P; a.v_out = slot(to) + 2 * P;
-        a.yfirst = g->cfg.alternate && (j & 1);
+        a.yfirst = g->cfg.alternate && ((s0 + j) & 1);     // the forward's parity: steps since set_initial
         if (g->bnd_any) {                                  // boundary input, as in cliffs_step_n
             const int rci = impose_boundary(g, slot(from), slot(from) + P, slot(from) + 2 * P,
                                             g->t_start + (double)(s0 + j) * g->cfg.dt);
@@ -1535,11 +1544,12 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
     };
     const float* ckpt = recorded ? recorded : g->adj_ckpt;
     // X_0: the grid's current state (or the recorded run's first checkpoint)
-    const int cb = (int)cur_buf(g, 0);
+    const int cb = (int)cur_buf(g, scenario);
+    const size_t so = (size_t)scenario * P;                 // the scenario's plane
     if (!recorded) {
-        CK(cudaMemcpyAsync(slot(0), g->eta[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(slot(0) + P, g->u[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb], sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0), g->eta[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + P, g->u[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
     }
     // checkpoint pass: X_{sK} for every segment s (a recorded run has them already)
     for (long long j = 0; !recorded && j <= (nseg - 1) * K; ++j) {
@@ -1598,7 +1608,7 @@ static int adjoint_core(cliffs_grid* g, int64_t n, int32_t checkpoint_every, con
                 if (rci) return rci;
             }
             const float* seed_j = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * G : nullptr;
-            if (g->cfg.alternate && (j & 1)) {
+            if (g->cfg.alternate && ((s0 + j) & 1)) {
                 int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, g->bnd_any ? false : seeded);
                 if (rc2) return rc2;
             } else {

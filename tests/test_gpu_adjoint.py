@@ -207,9 +207,12 @@ def test_adjoint_checkpoint_spacing_and_state_untouched():
 def test_adjoint_argument_errors():
     w = workloads.ensemble_512(batch=2, nx=64, ny=48, dmin=5, dmax=9)
     g = _start(w)
-    with pytest.raises(CliffsError) as e:
-        g.adjoint(4, None)
-    assert e.value.code == ERR_ARG
+    g.set_durations(w.durations)
+    for scen, n in ((2, 4), (-1, 4), (0, int(w.durations[0]) + 1)):     # no such scenario; past its end
+        with pytest.raises(CliffsError) as e:
+            g.adjoint(n, None, scenario=scen)
+        assert e.value.code == ERR_ARG
+    assert not np.any(g.adjoint(4, None, scenario=1))
     g.close()
     w = workloads.beach_200(64, 48, steps=10)
     g = _start(w)
@@ -292,3 +295,76 @@ def test_adjoint_with_respect_to_initial_velocities():
         worst = max(worst, err)
         assert err <= DOT_RTOL, (k, got, terms.sum())
     P.report("adjoint_dot_velocity", rel_err=worst)
+
+
+def _dot_against_tlm(p, w, grad, seed, state, n, step0=0, k=3, rng=None):
+    """Worst relative error of <grad, delta> against the oracle's tangent model from the
+    GPU state `state` (eta, u, v) over the next n steps."""
+    rng = rng or np.random.default_rng(31)
+    d64 = P.f32(P.oracle_depth(w))
+    yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
+    worst, dots = 0.0, []
+    for i in range(k):
+        cx, cy = rng.uniform(0.3, 0.7) * w.nx, rng.uniform(0.3, 0.7) * w.ny
+        sig = rng.uniform(0.05, 0.12) * min(w.nx, w.ny)
+        delta = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig ** 2))
+        _, gtan, _, _ = oracle.run_tlm(p, w.x, w.y, d64, state[0], delta, u=state[1], v=state[2], nsteps=n,
+                                       step0=step0, gout=w.gout, gauges=w.gauges)
+        terms = seed.astype(np.float64) * gtan
+        got = float((grad * delta).sum())
+        worst = max(worst, abs(got - terms.sum()) / max(np.abs(terms).max(), 1e-12))
+        dots.append((got, terms.sum(), np.abs(terms).max()))
+    return worst, dots
+
+
+def test_batched_scenario_adjoint_equals_a_single_grid_and_the_oracle():
+    """Scenario 1 of a batched grid, 10 steps in: its adjoint equals, bit for bit, the adjoint
+    of a single grid started from the same state, and passes the dot-product test against
+    the oracle's tangent model from that state."""
+    w = workloads.ensemble_512(batch=3, nx=120, ny=100, dmin=60, dmax=90)
+    g = _start(w)
+    g.set_durations(w.durations)
+    g.step(10)
+    state = g.state(1)
+    n = 40
+    rng = np.random.default_rng(37)
+    seed = rng.standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    grad = g.adjoint(n, seed, checkpoint_every=13, scenario=1)
+    others = [g.state(b) for b in (0, 2)]
+    g.close()
+    s1 = CliffsGrid(w.nx, w.ny, w.dt, coords=w.coords, h_min=w.h_min, manning_n2=w.manning_n2, itopo=w.itopo,
+                    dwall=w.dwall, transverse=w.transverse, maxout=w.maxout, gout=w.gout,
+                    gauges=[tuple(q) for q in w.gauges])
+    s1.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    s1.set_initial(*state)
+    single = s1.adjoint(n, seed, checkpoint_every=13)
+    s1.close()
+    assert np.array_equal(grad, single)
+    assert all(np.isfinite(o[0]).all() for o in others)
+    p = oracle.params_from(w)
+    worst, _ = _dot_against_tlm(p, w, grad.astype(np.float64), seed, state, n, rng=rng)
+    P.report("adjoint_dot_batched_scenario", rel_err=worst)
+    assert worst <= DOT_RTOL
+
+
+def test_alternating_adjoint_keeps_the_forward_parity_after_odd_steps():
+    """After 3 steps the next step of the alternating order sweeps y first; the adjoint from
+    there must transpose that order: the dot-product test against the oracle's tangent model
+    started at step index 3 passes, and the same test at the other parity fails (the two
+    splitting orders differ at second order, so that failure is small but far above the
+    right parity's error)."""
+    w = _alternate()
+    g = _start(w, alternate=1)
+    g.step(3)
+    state = g.state()
+    n = 40
+    rng = np.random.default_rng(41)
+    seed = rng.standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    grad = g.adjoint(n, seed, checkpoint_every=17).astype(np.float64)
+    g.close()
+    p = oracle.params_from(w, alternate=1)
+    worst, _ = _dot_against_tlm(p, w, grad, seed, state, n, step0=3, rng=np.random.default_rng(5))
+    P.report("adjoint_dot_alternate_odd_start", rel_err=worst)
+    assert worst <= DOT_RTOL
+    wrong, _ = _dot_against_tlm(p, w, grad, seed, state, n, step0=4, rng=np.random.default_rng(5))
+    assert wrong > DOT_RTOL and wrong > 50 * worst, (wrong, worst)       # measured 2.2e-4 vs 5.3e-7
