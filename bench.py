@@ -64,8 +64,9 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+def profiled_traffic(name, rows_per_warp=None):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source and
+    at this run's tile shape."""
     p = os.path.join(ROOT, "profiles", name + ".json")
     try:
         d = json.load(open(p))
@@ -73,6 +74,8 @@ def profiled_traffic(name):
         return None, None
     if d.get("source_sha") != kernel_source_sha():
         return None, "stale"
+    if d.get("rows_per_warp") and rows_per_warp and d["rows_per_warp"] != rows_per_warp:
+        return None, "profiled at %d rows per warp, this run took %d" % (d["rows_per_warp"], rows_per_warp)
     return d.get("dram_bytes_per_launch"), d.get("note")
 
 
@@ -342,8 +345,12 @@ def run_cuda(args, world, rank, local):
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
     eta0 = w.eta0.astype(np.float32)
     g.set_initial(eta0)
-    tune = g.autotune(3)                  # rows per warp of the fused step, by measurement
-    rows_per_warp = min(tune, key=tune.get) if tune else None
+    if args.rows_per_warp:                # a fixed tile (to profile the configuration a run chose)
+        g.set_rows_per_warp(args.rows_per_warp)
+        rows_per_warp = args.rows_per_warp
+    else:
+        tune = g.autotune(3)              # rows per warp of the fused step, by measurement
+        rows_per_warp = min(tune, key=tune.get) if tune else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -374,7 +381,7 @@ def run_cuda(args, world, rank, local):
     value = world * w.cells * args.steps / (ms_max / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL * w.cells / (ms / args.steps / 1e3) / 1e9
-    traffic, tnote = profiled_traffic("k_step_fused_spherical_2048")
+    traffic, tnote = profiled_traffic("k_step_fused_spherical_2048", rows_per_warp)
 
     # end to end through the public API: pinned host inputs in, host outputs out
     e2e = None
@@ -481,6 +488,8 @@ def main():
     ap.add_argument("--forms-only", choices=["batched", "stress", "adjoint"],
                     help="measure one form only and print it (no headline line)")
     ap.add_argument("--adjoint-steps", type=int, default=None)
+    ap.add_argument("--rows-per-warp", type=int, default=0,
+                    help="fix the fused step's tile instead of autotuning it")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.forms_only:

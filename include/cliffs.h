@@ -250,6 +250,13 @@ int cliffs_adjoint_velocity(cliffs_grid* g, float* dL_du0, float* dL_dv0);
  * Errors: ERR_STATE before set_initial; ERR_NOMEM; ERR_CUDA; ERR_TIMEOUT. */
 int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32_t* ncand);
 
+/* Set the tile shape of the 2D step kernel directly: `rows` output rows per warp (what
+ * cliffs_autotune chooses by measurement), e.g. to repeat a measured configuration. Call it
+ * after cliffs_set_bathy, which chooses a default shape. Results do not depend on the shape.
+ * Errors: ERR_STATE before set_bathy; ERR_ARG (1D grid, rows outside 1..8192); ERR_NOMEM;
+ * ERR_CUDA. */
+int cliffs_set_rows_per_warp(cliffs_grid* g, int32_t rows);
+
 /* Fault injection for tests of the bounded waits (no counterpart in the paper): the next
  * step launch of a 2D grid makes every shared-memory ring slot expect 16 bytes more than
  * its copies deliver, with waits limited to `cycles` clock cycles. Each wait then expires,

@@ -29,7 +29,7 @@ __all__ = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
-    "cliffs_adjoint_scenario", "EXPORTED",
+    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -44,7 +44,7 @@ EXPORTED = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
-    "cliffs_adjoint_scenario",
+    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp",
 ]
 
 
@@ -92,6 +92,7 @@ def lib():
             "cliffs_run_persistent": ([vp, C.c_int64], C.c_int),
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_scenario": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
+            "cliffs_set_rows_per_warp": ([vp, C.c_int32], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
@@ -324,6 +325,10 @@ def cliffs_autotune(g, trials=3):
     return {int(cand[i]): float(us[i]) for i in range(n.value)}
 
 
+def cliffs_set_rows_per_warp(g, rows):
+    _check(lib().cliffs_set_rows_per_warp(g, int(rows)))
+
+
 def cliffs_inject_wait_expiry(g, cycles):
     _check(lib().cliffs_inject_wait_expiry(g, int(cycles)))
 
@@ -453,6 +458,9 @@ class CliffsGrid:
 
     def kernel_time(self, enable=1):
         return cliffs_kernel_time(self.h, enable)
+
+    def set_rows_per_warp(self, rows):
+        cliffs_set_rows_per_warp(self.h, rows)
 
     def autotune(self, trials=3):
         return cliffs_autotune(self.h, trials)

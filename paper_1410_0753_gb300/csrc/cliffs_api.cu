@@ -1667,6 +1667,15 @@ int cliffs_adjoint_velocity(cliffs_grid* g, float* dL_du0, float* dL_dv0) {
     return CLIFFS_OK;
 }
 
+int cliffs_set_rows_per_warp(cliffs_grid* g, int32_t rows) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (!g->have_bathy) return set_err(CLIFFS_ERR_STATE, "set_bathy first (it chooses the geometry)");
+    if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "a 1D grid has no tile shape");
+    if (rows < 1 || rows > 8192) return set_err(CLIFFS_ERR_ARG, "rows per warp %d outside 1..8192", rows);
+    return set_rows_per_warp(g, rows, hard_rows(rows));
+}
+
 int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32_t* ncand) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");

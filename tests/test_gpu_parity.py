@@ -404,20 +404,32 @@ def test_autotuned_tile_shape_gives_identical_results():
     computed by the same arithmetic, so any shape gives the same bits."""
     w = workloads.spherical_coast(300, 260, steps=80)
     runs = []
-    for tune in (False, True):
+    for tune in ("default", "autotune", 1, 7, 300):     # fixed shapes: one row, odd, taller than the grid
         g = CliffsGrid.from_workload(w)
         g.set_bathy(w.x, w.y, w.depth)
         g.set_initial(w.eta0.astype(np.float32))
-        if tune:
+        if tune == "autotune":
             table = g.autotune(2)
             assert len(table) >= 3 and all(t > 0 for t in table.values())
+        elif tune != "default":
+            g.set_rows_per_warp(tune)
         g.step(w.steps)
         runs.append((g.state(), g.gauges(), g.maxwave(), g.boundary(0, 2)))
         g.close()
-    (s0, g0, m0, b0), (s1, g1, m1, b1) = runs
-    for x, y in zip(s0 + m0, s1 + m1):
-        assert np.array_equal(x, y)
-    assert np.array_equal(g0, g1) and np.array_equal(b0, b1)
+    s0, g0, m0, b0 = runs[0]
+    for s1, g1, m1, b1 in runs[1:]:
+        for x, y in zip(s0 + m0, s1 + m1):
+            assert np.array_equal(x, y)
+        assert np.array_equal(g0, g1) and np.array_equal(b0, b1)
+    g1d = CliffsGrid(50, 1, 1.0)
+    with pytest.raises(CliffsError) as e:
+        g1d.set_rows_per_warp(8)                           # before set_bathy
+    assert e.value.code == ERR_STATE
+    g1d.set_bathy(np.arange(50) * 10.0, np.zeros(1), np.full((1, 50), 5.0), False)
+    with pytest.raises(CliffsError) as e:
+        g1d.set_rows_per_warp(8)                           # a 1D grid has no tile
+    assert e.value.code == ERR_ARG
+    g1d.close()
 
 
 def test_state_views_are_zero_copy():
