@@ -216,6 +216,15 @@ int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const 
 int cliffs_adjoint_scenario(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
                             const float* dL_dgauges, float* dL_deta0);
 
+/* cliffs_adjoint_scenario for a loss on the whole gauge records: dL_drecords[r][g][3] holds
+ * dL/d (eta, u, v) at gauge g after r*gout steps (the layout cliffs_read_gauges writes), so
+ * misfits of the recorded velocities differentiate too. Errors: as cliffs_adjoint_scenario. */
+int cliffs_adjoint_records(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
+                           const float* dL_drecords, float* dL_deta0);
+
+/* cliffs_adjoint_recorded with dL/d (eta, u, v) of the records, [nrec][G][3]. */
+int cliffs_adjoint_recorded_records(cliffs_grid* g, const float* dL_drecords, float* dL_deta0);
+
 /* Record the forward run for the adjoint (no counterpart in the paper). With
  * checkpoint_every = K > 0, called right after cliffs_set_initial, the initial state and then
  * every K-th state produced by cliffs_step_n are kept (12 bytes per node each, the store grows

@@ -95,6 +95,9 @@ def _bind(L):
                                         C.c_long, C.c_long, C.c_int, C.c_int, ip, dp, dp, C.c_long, lp,
                                         C.c_double, P(dp), lp, P(dp)]
     L.oracle_run_tlm_forced.restype = C.c_int
+    L.oracle_run_tlm_uv.argtypes = [P(OracleParams), dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                    C.c_long, C.c_long, C.c_int, C.c_int, C.c_int, ip, dp, dp, dp, C.c_long, lp]
+    L.oracle_run_tlm_uv.restype = C.c_int
     return L
 
 
@@ -342,9 +345,10 @@ def run_tlm_forced(p: OracleParams, x, y, depth, eta, deta, boundary, nsteps=0, 
 
 
 def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv=None,
-            nsteps=0, step0=0, record_initial=True, gout=1, gauges=None):
+            nsteps=0, step0=0, record_initial=True, gout=1, gauges=None, uv=False):
     """Tangent-linear run. Returns (gauge values [nrec][G], gauge tangents [nrec][G],
-    final primal state, final tangent state)."""
+    final primal state, final tangent state); with uv=True the gauge tangents are those of
+    (eta, u, v), [nrec][G][3]."""
     L = lib()
     ny, nx = depth.shape
     x = np.ascontiguousarray(x, np.float64)
@@ -363,9 +367,16 @@ def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv
     gval = np.zeros((cap, G))
     gtan = np.zeros((cap, G))
     n = C.c_long(0)
-    rc = L.oracle_run_tlm(C.byref(p), _d(x), _d(y), _d(depth), _d(eta), _d(u), _d(v),
-                          _d(deta), _d(du), _d(dv), int(step0), int(nsteps), int(record_initial),
-                          int(gout), G, _i(gix), _d(gval), _d(gtan), cap, C.byref(n))
+    if uv:
+        guv = np.zeros((cap, G, 2))
+        rc = L.oracle_run_tlm_uv(C.byref(p), _d(x), _d(y), _d(depth), _d(eta), _d(u), _d(v),
+                                 _d(deta), _d(du), _d(dv), int(step0), int(nsteps), int(record_initial),
+                                 int(gout), G, _i(gix), _d(gval), _d(gtan), _d(guv), cap, C.byref(n))
+        gtan = np.concatenate([gtan[:, :, None], guv], axis=2)
+    else:
+        rc = L.oracle_run_tlm(C.byref(p), _d(x), _d(y), _d(depth), _d(eta), _d(u), _d(v),
+                              _d(deta), _d(du), _d(dv), int(step0), int(nsteps), int(record_initial),
+                              int(gout), G, _i(gix), _d(gval), _d(gtan), cap, C.byref(n))
     if rc != 0:
         raise ValueError("oracle_run_tlm failed (%d)" % rc)
     return gval[: n.value], gtan[: n.value], (eta, u, v), (deta, du, dv)

@@ -668,7 +668,8 @@ static int run_tlm_impl(const oracle_params* p, const double* x, const double* y
                         long step0, long nsteps, int record_initial,
                         int gout, int n_gauges, const int* gauge_ixiy,
                         double* gauge_val, double* gauge_tan, long cap, long* nrec,
-                        double t0, const double* const* times, const long* nt, const double* const* vals);
+                        double t0, const double* const* times, const long* nt, const double* const* vals,
+                        double* gauge_tan_uv);
 
 // Tangent-linear run: the primal (eta,u,v) and a tangent (deta,du,dv) advance together;
 // every branch is decided on the primal. Gauge tangents of eta are written to
@@ -679,7 +680,17 @@ int oracle_run_tlm(const oracle_params* p, const double* x, const double* y, con
                    int gout, int n_gauges, const int* gauge_ixiy,
                    double* gauge_val, double* gauge_tan, long cap, long* nrec) {
     return run_tlm_impl(p, x, y, d, eta, u, v, deta, du, dv, step0, nsteps, record_initial, gout, n_gauges,
-                        gauge_ixiy, gauge_val, gauge_tan, cap, nrec, 0.0, nullptr, nullptr, nullptr);
+                        gauge_ixiy, gauge_val, gauge_tan, cap, nrec, 0.0, nullptr, nullptr, nullptr, nullptr);
+}
+
+// oracle_run_tlm that also writes the gauge tangents of u and v to gauge_tan_uv[nrec][G][2].
+int oracle_run_tlm_uv(const oracle_params* p, const double* x, const double* y, const double* d,
+                      double* eta, double* u, double* v, double* deta, double* du, double* dv,
+                      long step0, long nsteps, int record_initial,
+                      int gout, int n_gauges, const int* gauge_ixiy,
+                      double* gauge_val, double* gauge_tan, double* gauge_tan_uv, long cap, long* nrec) {
+    return run_tlm_impl(p, x, y, d, eta, u, v, deta, du, dv, step0, nsteps, record_initial, gout, n_gauges,
+                        gauge_ixiy, gauge_val, gauge_tan, cap, nrec, 0.0, nullptr, nullptr, nullptr, gauge_tan_uv);
 }
 
 // The tangent-linear model of oracle_run_forced: the imposed edge values carry no tangent.
@@ -689,7 +700,7 @@ int oracle_run_tlm_forced(const oracle_params* p, const double* x, const double*
                           double* gauge_val, double* gauge_tan, long cap, long* nrec,
                           double t0, const double* const* times, const long* nt, const double* const* vals) {
     return run_tlm_impl(p, x, y, d, eta, u, v, deta, du, dv, step0, nsteps, 1, gout, n_gauges, gauge_ixiy,
-                        gauge_val, gauge_tan, cap, nrec, t0, times, nt, vals);
+                        gauge_val, gauge_tan, cap, nrec, t0, times, nt, vals, nullptr);
 }
 
 }  // extern "C"
@@ -699,7 +710,8 @@ static int run_tlm_impl(const oracle_params* p, const double* x, const double* y
                         long step0, long nsteps, int record_initial,
                         int gout, int n_gauges, const int* gauge_ixiy,
                         double* gauge_val, double* gauge_tan, long cap, long* nrec,
-                        double t0, const double* const* times, const long* nt, const double* const* vals) {
+                        double t0, const double* const* times, const long* nt, const double* const* vals,
+                        double* gauge_tan_uv) {
     Params P = to_params(p);
     if ((P.nx > 1 && P.nx < 3) || (P.ny > 1 && P.ny < 3)) return -1;
     Grid Gd{P, x, y, d};
@@ -713,6 +725,10 @@ static int run_tlm_impl(const oracle_params* p, const double* x, const double* y
             const size_t c = (size_t)gauge_ixiy[2 * g + 1] * P.nx + gauge_ixiy[2 * g];
             if (gauge_val) gauge_val[n * n_gauges + g] = E[c].v;
             gauge_tan[n * n_gauges + g] = E[c].d;
+            if (gauge_tan_uv) {
+                gauge_tan_uv[2 * (n * n_gauges + g)] = U[c].d;
+                gauge_tan_uv[2 * (n * n_gauges + g) + 1] = V[c].d;
+            }
         }
         ++n;
     };

@@ -29,7 +29,8 @@ __all__ = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
-    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "EXPORTED",
+    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
+    "cliffs_adjoint_recorded_records", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -44,7 +45,8 @@ EXPORTED = [
     "cliffs_inject_wait_expiry", "cliffs_autotune", "cliffs_run_persistent", "cliffs_adjoint_n",
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
-    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp",
+    "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
+    "cliffs_adjoint_recorded_records",
 ]
 
 
@@ -93,6 +95,8 @@ def lib():
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_scenario": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_set_rows_per_warp": ([vp, C.c_int32], C.c_int),
+            "cliffs_adjoint_records": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
+            "cliffs_adjoint_recorded_records": ([vp, vp, vp], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
@@ -227,6 +231,17 @@ def cliffs_adjoint_scenario(g, scenario, n, checkpoint_every, dL_dgauges, out):
     """cliffs_adjoint_n for one scenario of a batched grid."""
     ps, ks = _ptr(dL_dgauges, np.float32)
     _check(lib().cliffs_adjoint_scenario(g, int(scenario), int(n), int(checkpoint_every), ps, _out_ptr(out)))
+
+
+def cliffs_adjoint_records(g, scenario, n, checkpoint_every, dL_drecords, out):
+    """The adjoint for dL/d (eta, u, v) of the gauge records ([n // gout + 1][G][3])."""
+    ps, ks = _ptr(dL_drecords, np.float32)
+    _check(lib().cliffs_adjoint_records(g, int(scenario), int(n), int(checkpoint_every), ps, _out_ptr(out)))
+
+
+def cliffs_adjoint_recorded_records(g, dL_drecords, out):
+    ps, ks = _ptr(dL_drecords, np.float32)
+    _check(lib().cliffs_adjoint_recorded_records(g, ps, _out_ptr(out)))
 
 
 def cliffs_state_ptrs(g, scenario):
@@ -479,7 +494,10 @@ class CliffsGrid:
         """Gradient for the run recorded since the last set_initial (see adjoint)."""
         if out is None:
             out = np.empty((self.ny, self.nx), np.float32)
-        cliffs_adjoint_recorded(self.h, dL_dgauges, out)
+        if dL_dgauges is not None and len(getattr(dL_dgauges, "shape", ())) == 3:   # [nrec][G][3]
+            cliffs_adjoint_recorded_records(self.h, dL_dgauges, out)
+        else:
+            cliffs_adjoint_recorded(self.h, dL_dgauges, out)
         return out
 
     def adjoint_velocity(self):
@@ -495,5 +513,8 @@ class CliffsGrid:
         ``scenario`` on a batched grid)."""
         if out is None:
             out = np.empty((self.ny, self.nx), np.float32)
-        cliffs_adjoint_scenario(self.h, scenario, n, checkpoint_every, dL_dgauges, out)
+        if dL_dgauges is not None and len(getattr(dL_dgauges, "shape", ())) == 3:   # [nrec][G][3]
+            cliffs_adjoint_records(self.h, scenario, n, checkpoint_every, dL_dgauges, out)
+        else:
+            cliffs_adjoint_scenario(self.h, scenario, n, checkpoint_every, dL_dgauges, out)
         return out

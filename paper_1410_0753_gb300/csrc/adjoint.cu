@@ -24,6 +24,7 @@
 // free of the cancellation that p = w + 2c would suffer in FP32. Reciprocals in the
 // coefficients come from the hardware approximation (relative error ~1e-7), as in the forward.
 #include "internal.h"
+#include "adjoint.h"
 #include "sweep.cuh"
 
 namespace cliffs {
@@ -629,10 +630,14 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
     }
     __syncthreads();
     if (DIR == 0 && A.seed) {
-        // gauge-misfit seed of this step: dL/d eta at each gauge node
+        // gauge-misfit seed of this step: dL/d (eta, u, v) at each gauge node
         for (int k = threadIdx.x; k < A.G; k += blockDim.x) {
             const int q = A.gxy[2 * k] - strip * AOUT, ln = A.gxy[2 * k + 1] - l0;
-            if (q >= 0 && q < AOUT && ln >= 0 && ln < ALINES) atomicAdd(&tile[0][q][ln], A.seed[k]);
+            if (q >= 0 && q < AOUT && ln >= 0 && ln < ALINES) {
+                atomicAdd(&tile[0][q][ln], A.seed[3 * k]);           // eta
+                atomicAdd(&tile[1][q][ln], A.seed[3 * k + 1]);       // u, along the rows
+                atomicAdd(&tile[2][q][ln], A.seed[3 * k + 2]);       // v
+            }
         }
         __syncthreads();
     }
@@ -718,9 +723,13 @@ __global__ void __launch_bounds__(256) k_transpose(const float* __restrict__ in,
 }
 
 // lambda.eta[gauge] += seed[gauge] on transposed data
-__global__ void k_adj_seed(float* te, int tpitch, const int* gxy, int G, const float* seed) {
+__global__ void k_adj_seed(float* te, int tpitch, long long tplane, const int* gxy, int G, const float* seed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < G) atomicAdd(te + (long long)gxy[2 * k] * tpitch + gxy[2 * k + 1], seed[k]);
+    if (k >= G) return;
+    const long long o = (long long)gxy[2 * k] * tpitch + gxy[2 * k + 1];
+    atomicAdd(te + o, seed[3 * k]);                          // eta
+    atomicAdd(te + tplane + o, seed[3 * k + 1]);             // u
+    atomicAdd(te + 2 * tplane + o, seed[3 * k + 2]);         // v
 }
 
 // lambda = 0 on the edges whose nodes the boundary input overwrites before a step (mask:
@@ -783,9 +792,10 @@ cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_seed(float* te, int tpitch, const int* gxy, int G, const float* seed, cudaStream_t s) {
+cudaError_t launch_adj_seed(float* te, int tpitch, long long tplane, const int* gxy, int G, const float* seed,
+                            cudaStream_t s) {
     if (G <= 0) return cudaSuccess;
-    k_adj_seed<<<(G + 127) / 128, 128, 0, s>>>(te, tpitch, gxy, G, seed);
+    k_adj_seed<<<(G + 127) / 128, 128, 0, s>>>(te, tpitch, tplane, gxy, G, seed);
     return cudaGetLastError();
 }
 

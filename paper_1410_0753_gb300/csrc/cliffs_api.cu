@@ -20,6 +20,7 @@
 
 #include "cliffs.h"
 #include "internal.h"
+#include "adjoint.h"
 #include "sweep.cuh"
 
 using namespace cliffs;
@@ -1368,7 +1369,7 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
 }
 
 static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
-                        float* dL_deta0, const float* recorded);
+                        float* dL_deta0, const float* recorded, int comps = 1);
 
 int cliffs_adjoint_n(cliffs_grid* g, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
                      float* dL_deta0) {
@@ -1411,6 +1412,18 @@ int cliffs_adjoint_recorded(cliffs_grid* g, const float* dL_dgauges, float* dL_d
     return adjoint_core(g, 0, g->rec_n, g->rec_K, dL_dgauges, dL_deta0, g->rec_ckpt);
 }
 
+int cliffs_adjoint_records(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
+                           const float* dL_drecords, float* dL_deta0) {
+    return adjoint_core(g, scenario, n, checkpoint_every, dL_drecords, dL_deta0, nullptr, 3);
+}
+
+int cliffs_adjoint_recorded_records(cliffs_grid* g, const float* dL_drecords, float* dL_deta0) {
+    g_err[0] = 0;
+    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (g->rec_K <= 0 || g->rec_n < 1) return set_err(CLIFFS_ERR_STATE, "no recorded run");
+    return adjoint_core(g, 0, g->rec_n, g->rec_K, dL_drecords, dL_deta0, g->rec_ckpt, 3);
+}
+
 // Adjoint of a y-first step j of the alternating order, X_{j+1} = x-sweep(y-sweep(X_j)),
 // from lambda_{j+1} (transposed, in the second third of adj_t) to lambda_j in the same place:
 // the y-sweep of X_j is recomputed row-major, the x-sweep adjoint runs over it, then the
@@ -1448,15 +1461,17 @@ static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineA
     for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // lambda_j transposed
         le = launch_transpose(LB + f * P, g->pitch, LT + f * TPL, tp, ny, nx, s);
     if (le == cudaSuccess && seeded && j % g->cfg.gout == 0)
-        le = launch_adj_seed(LT, tp, g->adj_gxy, g->G, g->adj_seed + (j / g->cfg.gout) * g->G, s);
+        le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, g->G, g->adj_seed + (j / g->cfg.gout) * 3 * g->G, s);
     if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
     return CLIFFS_OK;
 }
 
 // The adjoint steps of cliffs_adjoint_n; `recorded` holds the checkpoints of a recorded run
 // (X_0 included), else a checkpoint pass from the grid's current state makes them.
+// comps: dL_dgauges holds dL/d eta at the gauge records ([nrec][G], comps 1) or dL/d (eta,
+// u, v) ([nrec][G][3], comps 3); the seeds are kept as [nrec][G][3] either way.
 static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpoint_every, const float* dL_dgauges,
-                        float* dL_deta0, const float* recorded) {
+                        float* dL_deta0, const float* recorded, int comps) {
     g_err[0] = 0;
     if (!g || !dL_deta0) return set_err(CLIFFS_ERR_ARG, "null argument");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
@@ -1512,12 +1527,19 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     if (G > 0 && dL_dgauges && g->adj_seed_cap < nrec) {
         cudaFree(g->adj_seed);
         g->adj_seed = nullptr;
-        CK(cudaMalloc(&g->adj_seed, sizeof(float) * G * nrec));
+        CK(cudaMalloc(&g->adj_seed, sizeof(float) * 3 * G * nrec));
         g->adj_seed_cap = nrec;
     }
     const bool seeded = G > 0 && dL_dgauges;
-    if (seeded)
-        CK(cudaMemcpyAsync(g->adj_seed, dL_dgauges, sizeof(float) * G * nrec, cudaMemcpyDefault, s));
+    if (seeded) {
+        if (comps == 3) {
+            CK(cudaMemcpyAsync(g->adj_seed, dL_dgauges, sizeof(float) * 3 * G * nrec, cudaMemcpyDefault, s));
+        } else {                                            // eta seeds into every third slot
+            CK(cudaMemsetAsync(g->adj_seed, 0, sizeof(float) * 3 * G * nrec, s));
+            CK(cudaMemcpy2DAsync(g->adj_seed, 3 * sizeof(float), dL_dgauges, sizeof(float), sizeof(float),
+                                 (size_t)G * nrec, cudaMemcpyDefault, s));
+        }
+    }
     float* XT = g->adj_t;                                   // eta', u', v' transposed
     float* LT = g->adj_t + 3 * TPL;                         // adjoint (eta, u, v) transposed
     float* DT = g->adj_t + 6 * TPL;                         // depth transposed
@@ -1567,7 +1589,7 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     // lambda_n: the seed of the last record
     CK(cudaMemsetAsync(LT, 0, sizeof(float) * 3 * TPL, s));
     if (seeded && n % g->cfg.gout == 0) {
-        le = launch_adj_seed(LT, tp, g->adj_gxy, G, g->adj_seed + (n / g->cfg.gout) * G, s);
+        le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, G, g->adj_seed + (n / g->cfg.gout) * 3 * G, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "seed: %s", cudaGetErrorString(le));
     }
     AdjLineArgs Y{};                                        // y-sweep adjoint: lines are columns
@@ -1607,7 +1629,7 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
                                                 g->t_start + (double)(s0 + j) * g->cfg.dt);
                 if (rci) return rci;
             }
-            const float* seed_j = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * G : nullptr;
+            const float* seed_j = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * 3 * G : nullptr;
             if (g->cfg.alternate && ((s0 + j) & 1)) {
                 int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, g->bnd_any ? false : seeded);
                 if (rc2) return rc2;
@@ -1621,7 +1643,7 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
             }
             if (g->bnd_any) {
                 le = launch_adj_zero_edges(LT, tp, nx, ny, input_edges(g), s);
-                if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, g->adj_gxy, G, seed_j, s);
+                if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, G, seed_j, s);
                 if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
             }
         }

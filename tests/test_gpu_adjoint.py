@@ -368,3 +368,77 @@ def test_alternating_adjoint_keeps_the_forward_parity_after_odd_steps():
     assert worst <= DOT_RTOL
     wrong, _ = _dot_against_tlm(p, w, grad, seed, state, n, step0=4, rng=np.random.default_rng(5))
     assert wrong > DOT_RTOL and wrong > 50 * worst, (wrong, worst)       # measured 2.2e-4 vs 5.3e-7
+
+
+def test_adjoint_of_velocity_records_dot_product_against_oracle_tlm():
+    """Seeds on all three recorded fields (eta, u, v) of every gauge: the GPU adjoint against
+    the oracle's tangent model of the same records (its u and v tangents pinned by central
+    differences), on the beach with run-up and on the spherical coast."""
+    for name in ("beach_runup", "spherical_coast"):
+        w = _cases()[name]()
+        n = w.steps
+        g = _start(w)
+        nrec = n // w.gout + 1
+        rng = np.random.default_rng(43)
+        seed = rng.standard_normal((nrec, len(w.gauges), 3)).astype(np.float32)
+        grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
+        du, dv = g.adjoint_velocity()
+        eta_only = g.adjoint(n, np.ascontiguousarray(seed[:, :, 0]), checkpoint_every=37).astype(np.float64)
+        g.close()
+        assert not np.array_equal(grad, eta_only)            # the velocity seeds reach eta0
+        d64 = P.f32(P.oracle_depth(w))
+        p = oracle.params_from(w)
+        yy, xx = np.meshgrid(np.arange(w.ny), np.arange(w.nx), indexing="ij")
+        worst = 0.0
+        for k in range(3):
+            cx, cy = rng.uniform(0.3, 0.7) * w.nx, rng.uniform(0.3, 0.7) * w.ny
+            sig = rng.uniform(0.05, 0.12) * min(w.nx, w.ny)
+            delta = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig ** 2))
+            _, g3, _, _ = oracle.run_tlm(p, w.x, w.y, d64, w.eta0, delta, nsteps=n, gout=w.gout,
+                                         gauges=w.gauges, uv=True)
+            terms = seed.astype(np.float64) * g3
+            got = float((grad * delta).sum())
+            err = abs(got - terms.sum()) / max(np.abs(terms).max(), 1e-12)
+            worst = max(worst, err)
+            assert err <= DOT_RTOL, (name, k, got, terms.sum())
+        # and along an initial-velocity direction (eta0 fixed): dL/du0
+        delta_u = np.exp(-((xx - 0.5 * w.nx) ** 2 + (yy - 0.5 * w.ny) ** 2) / (2 * (0.1 * w.nx) ** 2))
+        z = np.zeros_like(delta_u)
+        _, g3, _, _ = oracle.run_tlm(p, w.x, w.y, d64, w.eta0, z, du=delta_u, nsteps=n, gout=w.gout,
+                                     gauges=w.gauges, uv=True)
+        terms = seed.astype(np.float64) * g3
+        err = abs(float((du.astype(np.float64) * delta_u).sum()) - terms.sum()) / max(np.abs(terms).max(), 1e-12)
+        worst = max(worst, err)
+        assert err <= DOT_RTOL, (name, "u0", err)
+        P.report("adjoint_dot_records_" + name, rel_err=worst)
+
+
+def test_autograd_on_whole_records_matches_finite_differences():
+    """gauge_run(records=True): a loss on the recorded velocities, gradient through the
+    recorded forward and the adjoint against central differences of the GPU forward."""
+    import torch
+    from paper_1410_0753_gb300.autograd import gauge_run
+    w = workloads.inversion_1024(nx=128, ny=112, steps=100)
+    n = w.steps
+    basis = torch.tensor(w.extra["basis"], device="cuda")
+    g = _start(w)
+
+    def loss(theta):
+        rec = gauge_run(torch.einsum("k,kyx->yx", theta, basis), g, n, 25, records=True)
+        return 0.5 * (rec[:, :, 1] ** 2 + 3.0 * rec[:, :, 2] ** 2 + rec[:, :, 0] ** 2).sum(dtype=torch.float64)
+
+    theta = torch.tensor(w.extra["theta0"], device="cuda", requires_grad=True)
+    loss(theta).backward()
+    grad = theta.grad.detach().cpu().numpy().astype(np.float64)
+    assert np.isfinite(grad).all() and np.abs(grad).max() > 0
+    h, worst = 1e-3, 0.0
+    with torch.no_grad():
+        for k in np.argsort(-np.abs(grad))[:6]:
+            e = torch.zeros(64, dtype=theta.dtype, device="cuda")
+            e[k] = h
+            fd = (loss(theta + e).item() - loss(theta - e).item()) / (2 * h)
+            err = abs(fd - grad[k]) / np.abs(grad).max()
+            worst = max(worst, err)
+            assert err <= FD_RTOL, (k, fd, grad[k])
+    P.report("adjoint_fd_records", rel_err=worst)
+    g.close()

@@ -497,6 +497,14 @@ def test_tlm_matches_central_differences():
     assert np.abs(fd - gtan).max() <= 1e-5 * scale, np.abs(fd - gtan).max() / scale
     r0 = oracle.run(p, x, y, d, eta0, nsteps=steps, gout=1, gauges=gauges)
     assert np.array_equal(r0["gauges"][:, :, 0], gval)
+    # the velocity tangents at the gauges against the same differences
+    _, g3, _, _ = oracle.run_tlm(p, x, y, d, eta0, dirn, nsteps=steps, gauges=gauges, uv=True)
+    assert np.array_equal(g3[:, :, 0], gtan)
+    for comp in (1, 2):
+        fdc = (rp["gauges"][:, :, comp] - rm["gauges"][:, :, comp]) / (2 * h)
+        sc = np.abs(g3[:, :, comp]).max()
+        assert sc > 1e-4
+        assert np.abs(fdc - g3[:, :, comp]).max() <= 1e-5 * sc, (comp, np.abs(fdc - g3[:, :, comp]).max() / sc)
 
 
 # ----------------------------------------------------------------------------------------
