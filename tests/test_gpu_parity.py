@@ -1,7 +1,9 @@
 """CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (stated here, derived in the design doc): gauge traces within 1e-4 of the oracle's
-max |eta| per gauge (1e-7 m absolute for traces that stay below 1e-3 m); wet/dry masks equal
+Tolerances: gauge traces within 1e-4 of the oracle's max |eta| per gauge (1e-7 m absolute
+for traces that stay below 1e-3 m), the bound the FP32 step is held to over the runs here
+(each step's FP32 rounding is a few 1e-7 of the state, accumulated over hundreds of steps,
+and the perturbation form keeps the c = sqrt(g h) differences free of cancellation); wet/dry masks equal
 except for cells whose oracle height or flooding margin lies within 1e-5 max(1, |d|) of
 h_min (counted); the depth filter and every branch-free identity (lake at rest, 1D == 2D)
 bit for bit.
