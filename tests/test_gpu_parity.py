@@ -372,7 +372,25 @@ def test_error_paths():
     assert e.value.code == ERR_UNSTABLE
     g.set_initial(np.zeros((20, 20), np.float32))    # the handle stays usable
     g.step(3)
+    # a finite velocity far past any physical one
+    u = np.zeros((20, 20), np.float32)
+    u[5, 5] = 4e5
+    g.set_initial(np.zeros((20, 20), np.float32), u)
+    with pytest.raises(CliffsError) as e:
+        g.step(1)
+    assert e.value.code == ERR_UNSTABLE
     g.close()
+    # the same on the 1D kernels (a line along x, a line along y)
+    for nx, ny in ((20, 1), (1, 20)):
+        g = CliffsGrid(nx, ny, 0.1)
+        g.set_bathy(x[:nx], x[:ny], d[:ny, :nx])
+        w0 = np.zeros((ny, nx), np.float32)
+        w0.flat[7] = np.nan
+        g.set_initial(np.zeros((ny, nx), np.float32), w0 if nx > 1 else None, None if nx > 1 else w0)
+        with pytest.raises(CliffsError) as e:
+            g.step(2)
+        assert e.value.code == ERR_UNSTABLE
+        g.close()
     with pytest.raises(CliffsError) as e:
         CliffsGrid(20, 20, 0.1, gauges=[(25, 3)])
     assert e.value.code == ERR_ARG
