@@ -57,9 +57,9 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name, rows_per_warp=None):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source and
-    at this run's tile shape."""
+def profiled(name, rows_per_warp=None):
+    """The committed ncu summary of a kernel (DRAM bytes and warp-instructions per launch),
+    if it was taken on this source and at this run's tile shape; else (None, why)."""
     p = os.path.join(ROOT, "profiles", name + ".json")
     try:
         d = json.load(open(p))
@@ -69,7 +69,19 @@ def profiled_traffic(name, rows_per_warp=None):
         return None, "stale"
     if d.get("rows_per_warp") and rows_per_warp and d["rows_per_warp"] != rows_per_warp:
         return None, "profiled at %d rows per warp, this run took %d" % (d["rows_per_warp"], rows_per_warp)
-    return d.get("dram_bytes_per_launch"), d.get("note")
+    return d, d.get("note")
+
+
+def issue_roof(prof, cells, value, sm_mhz, sms):
+    """The instruction-issue ceiling of the step kernel: each of an SM's 4 schedulers issues
+    at most one warp-instruction per cycle, so a kernel issuing I warp-instructions per cell
+    cannot exceed 4 * SMs * clock / I cell-updates/s, whatever its bytes."""
+    if not prof or not prof.get("warp_inst_per_launch") or not sm_mhz:
+        return None
+    ipc = prof["warp_inst_per_launch"] / cells
+    peak = 4.0 * sms * sm_mhz * 1e6 / ipc / 1e9
+    return {"warp_inst_per_cell": ipc, "peak": peak, "unit": "Gcell-updates/s", "frac": value / peak,
+            "sms": sms, "sm_mhz": sm_mhz}
 
 
 class Clocks:
@@ -374,7 +386,8 @@ def run_cuda(args, world, rank, local):
     value = world * w.cells * args.steps / (ms_max / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL * w.cells / (ms / args.steps / 1e3) / 1e9
-    traffic, tnote = profiled_traffic("k_step_fused_spherical_2048", rows_per_warp)
+    prof, tnote = profiled("k_step_fused_spherical_2048", rows_per_warp)
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
 
     # end to end through the public API: pinned host inputs in, host outputs out
     e2e = None
@@ -451,7 +464,10 @@ def run_cuda(args, world, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "kernel": "k_step_fused", "bytes_per_cell": BYTES_PER_CELL,
-                         "peak_kind": peak_kind},
+                         "peak_kind": peak_kind,
+                         "issue": issue_roof(prof, w.cells, value / world,
+                                             (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz"),
+                                             torch.cuda.get_device_properties(local).multi_processor_count)},
             "cpu_baseline": cpu,
             "oracle_error": oracle_error,
             "forms": forms,
