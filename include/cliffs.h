@@ -70,8 +70,8 @@ typedef struct cliffs_config {
     int32_t solver;             /* 2 (or 0): eq. (solver2); 1: eq. (solver1) */
     int32_t alternate;          /* 0: x then y every step; 1: y first on the odd steps
                                    (counted from 0 at set_initial), the alternating reading of
-                                   section "Numerics"; cliffs_step_n and the adjoint (the
-                                   persistent run rejects it) */
+                                   section "Numerics"; every stepping path and the
+                                   adjoint take it */
     int32_t maxout;             /* steps between max-wave updates (> 0) */
     int32_t gout;               /* steps between gauge records (> 0) */
     int32_t bndout;             /* steps between boundary-series records (> 0) */
@@ -178,9 +178,11 @@ int cliffs_step_n(cliffs_grid* g, int64_t n);
  * batch of uneven durations keeps every SM busy until the longest ends. The launch is
  * captured once into a CUDA graph (a copy of the step range into a device control block,
  * then the kernel) and replayed by later calls; it is captured again when a launch argument
- * changes (tile shape, record buffers, durations). 2D grids only. The grid barrier waits
- * at most about a second per step before it sets the timeout flag.
- * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 0); ERR_UNSTABLE as for
+ * changes (tile shape, record buffers, durations). 2D grids only; the alternating order and
+ * open edges are taken, boundary input and a recorded run are not (cliffs_step_n). The grid
+ * barrier waits at most about a second per step before it sets the timeout flag.
+ * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 0, boundary input, a recorded
+ * run); ERR_UNSTABLE as for
  * cliffs_step_n; ERR_TIMEOUT when a bounded wait gave up; ERR_CUDA (including a device
  * that cannot launch cooperatively). */
 int cliffs_run_persistent(cliffs_grid* g, int64_t n);

@@ -1265,7 +1265,6 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
-    if (g->cfg.alternate) return set_err(CLIFFS_ERR_ARG, "the persistent run sweeps x then y every step");
     if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "a grid under boundary input runs through cliffs_step_n");
     if (g->rec_K > 0) return set_err(CLIFFS_ERR_ARG, "a recorded run goes through cliffs_step_n");
     if (n == 0) return CLIFFS_OK;
@@ -1308,6 +1307,7 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     b.grec_row = (long long)g->G * 3;
     b.nrec = g->NN ? g->nrec : nullptr;
     b.nrec_row = (long long)g->NN * 3;
+    b.alternate = g->cfg.alternate;
     if (!b.order) {                               // no durations: every scenario, in index order
         std::vector<int> id(g->B);
         for (int i = 0; i < g->B; ++i) id[i] = i;

@@ -35,6 +35,7 @@ namespace cliffs {
 // the same tables for grids with open outer edges (cliffs_step_open.cu)
 const void* fused_kernel_open(int v);
 const void* batch_kernel_open(int v);
+const void* batch_kernel_alt(int v);        // the alternating order (cliffs_step_alt.cu), v + 8 open
 const void* xsweep_kernel_open(int v);
 const void* ysweep_kernel_open(int v);
 
@@ -44,9 +45,10 @@ static const void* fused_kernel(bool sph, bool fric, bool yf, bool s1, bool open
     const int v = (sph ? 1 : 0) + (fric ? 2 : 0) + (yf ? 4 : 0) + (s1 ? 8 : 0);
     return open ? fused_kernel_open(v) : t[v];
 }
-static const void* batch_kernel(bool sph, bool fric, bool s1, bool open) {
-    static const void* const t[8] = {CLIFFS_V2(k_batch, false, false), CLIFFS_V2(k_batch, true, false)};
+static const void* batch_kernel(bool sph, bool fric, bool s1, bool open, bool alt) {
+    static const void* const t[8] = {CLIFFS_V2(k_batch, false, false, false), CLIFFS_V2(k_batch, true, false, false)};
     const int v = (sph ? 1 : 0) + (fric ? 2 : 0) + (s1 ? 4 : 0);
+    if (alt) return batch_kernel_alt(v + (open ? 8 : 0));
     return open ? batch_kernel_open(v) : t[v];
 }
 static const void* xsweep_kernel(bool sph, bool fric, bool s1, bool open) {
@@ -69,8 +71,8 @@ static cudaError_t fused_smem_optin() {
         for (int v = 0; v < 32 && done == cudaSuccess; ++v)
             done = cudaFuncSetAttribute(fused_kernel(v & 1, v & 2, v & 4, v & 8, v & 16),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
-        for (int v = 0; v < 16 && done == cudaSuccess; ++v)
-            done = cudaFuncSetAttribute(batch_kernel(v & 1, v & 2, v & 4, v & 8),
+        for (int v = 0; v < 32 && done == cudaSuccess; ++v)
+            done = cudaFuncSetAttribute(batch_kernel(v & 1, v & 2, v & 4, v & 8, v & 16),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
     }
     return done;
@@ -104,13 +106,13 @@ cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs
     StepArgs aa = a;
     BatchArgs bb = b;
     void* args[] = {&m2, &aa, &bb};
-    return cudaLaunchKernelExC(&cfg, batch_kernel(a.sph, a.dt_gn2 > 0.f, solver1(a), a.open_edges != 0), args);
+    return cudaLaunchKernelExC(&cfg, batch_kernel(a.sph, a.dt_gn2 > 0.f, solver1(a), a.open_edges != 0, b.alternate != 0), args);
 }
 
 int batch_blocks_per_sm(bool sph) {
     if (fused_smem_optin() != cudaSuccess) return 1;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(sph, true, false, false), FUSED_WARPS * 32, FUSED_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(sph, true, false, false, false), FUSED_WARPS * 32, FUSED_SMEM);
     return nb;
 }
 

@@ -14,7 +14,7 @@ const void* fused_kernel_open(int v) {
     return t[v];
 }
 const void* batch_kernel_open(int v) {
-    static const void* const t[8] = {CLIFFS_V2O(k_batch, false, true), CLIFFS_V2O(k_batch, true, true)};
+    static const void* const t[8] = {CLIFFS_V2O(k_batch, false, true, false), CLIFFS_V2O(k_batch, true, true, false)};
     return t[v];
 }
 const void* xsweep_kernel_open(int v) {

@@ -77,6 +77,7 @@ struct BatchArgs {
     long long grec_row;              // floats per record row
     float* nrec;                     // enclosed-grid corner records, row = step / bndout
     long long nrec_row;
+    int alternate;                   // y first on the odd steps (the alternating order)
 };
 
 // launchers (cliffs_step.cu)

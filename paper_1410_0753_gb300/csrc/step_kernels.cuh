@@ -442,7 +442,9 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned nblo
 // (the halves of ctl[3]) alternate by step parity; block 0 clears the one the next step
 // uses while the other is in use. A scenario that has stopped keeps its last state in the
 // buffer of its last step's parity.
-template <bool SPH, bool FRIC, bool S1, bool OPEN>
+// With ALT (the alternating order) the odd-indexed steps (st - 1 odd) sweep y first: a second
+// per-warp worker of the y-first kind shares the warp's ring, barriers and ring count.
+template <bool SPH, bool FRIC, bool S1, bool OPEN, bool ALT>
 __global__ void __launch_bounds__(FUSED_WARPS * 32, 4)
 k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -452,7 +454,13 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
     if (*reinterpret_cast<volatile int*>(a.err) & ERRF_TIMEOUT) return;
     FusedWarp<SPH, FRIC, false, S1, OPEN> W(a);
     W.setup(smem_raw, wib);
+    FusedWarp<SPH, FRIC, true, S1, OPEN> WY(a);
+    if (ALT) {
+        WY.lane = W.lane; WY.K = W.K; WY.ring = W.ring; WY.bar = W.bar; WY.used = W.used; WY.bad = 0;
+    }
     for (long long st = step0 + 1; st <= step_end; ++st) {
+        const bool yf = ALT && (((st - 1) & 1) != 0);
+        if (yf) WY.used = W.used;
         const bool odd = (st & 1) != 0;          // odd steps read buffer 0 and write buffer 1
         const bool mx = st % B.maxout == 0;
         StepOut O{odd ? &MM.m[0] : &MM.m[1], odd ? B.eta[1] : B.eta[0], odd ? B.u[1] : B.u[0],
@@ -468,12 +476,15 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
             if (W.lane == 0) t = atomicAdd(tickets + (odd ? 1 : 0), 1u);
             t = __shfl_sync(FULL, t, 0);
             if (t >= total) break;
-            ok = W.run_item((int)(t % (unsigned)a.nitems), __ldg(B.order + t / (unsigned)a.nitems), O);
+            const int item = (int)(t % (unsigned)a.nitems), scen = __ldg(B.order + t / (unsigned)a.nitems);
+            ok = yf ? WY.run_item(item, scen, O) : W.run_item(item, scen, O);
         }
+        if (yf) W.used = WY.used;
         if (!ok && W.lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
         if (!grid_sync(reinterpret_cast<unsigned long long*>(B.ctl + 2), gridDim.x, a.wait_cycles, a.err)) break;
     }
     W.report();
+    if (ALT) WY.report();
 }
 
 // x-sweep alone: one warp per (row, strip of 56 columns).
