@@ -61,9 +61,10 @@ def test_nesting_chain_is_bit_exact_on_the_gpu():
     ch.close()
 
 
-def test_forced_run_against_the_oracle_on_a_beach():
+@pytest.mark.parametrize("alternate", [0, 1])
+def test_forced_run_against_the_oracle_on_a_beach(alternate):
     """A child straddling the shoreline of a beach, driven by the oracle parent's series:
-    the GPU's forced run against the oracle's forced run."""
+    the GPU's forced run against the oracle's forced run (both sweep orders)."""
     from workloads import Nest
     w = workloads.beach_200(200, 120, steps=400)
     d64 = P.f32(P.oracle_depth(w))
@@ -75,17 +76,19 @@ def test_forced_run_against_the_oracle_on_a_beach():
     series = {e: (times, par["boundary"][0][e]) for e in range(4)}
     sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
     gauges = np.array([(0, 32), (10, 32), (40, 32), (70, 32), (85, 20)], np.int32)   # one on the W input edge
-    pc = oracle.params(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2)
+    pc = oracle.params(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, alternate=alternate)
     o = oracle.run_forced(pc, w.x[i0:i0 + cx], w.y[j0:j0 + cy], d64[sub], w.eta0[sub], series,
                           nsteps=w.steps, gout=1, gauges=gauges)
-    g = CliffsGrid(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, gauges=[tuple(q) for q in gauges])
+    g = CliffsGrid(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, gauges=[tuple(q) for q in gauges],
+                   alternate=alternate)
     g.set_bathy(w.x[i0:i0 + cx], w.y[j0:j0 + cy], d64[sub], False)
     g.set_initial(w.eta0[sub].astype(np.float32))
     for e in range(4):
         g.set_boundary_input(e, times, series[e][1])
     g.step(w.steps)
     rel, absol = P.gauge_errors(g.gauges()[:, :, 0], o["gauges"][:, :, 0])
-    P.report("forced_beach_child", gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0))
+    P.report("forced_beach_child_alt%d" % alternate, gauge_rel_max=rel.max(initial=0.0),
+             gauge_abs_max=absol.max(initial=0.0))
     assert rel.max(initial=0.0) <= P.GAUGE_RTOL and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
     e32 = g.state()[0]
     wet32, wet64, near = P.wet_masks(e32, o["eta"], d64[sub], d64[sub], w.h_min)
@@ -155,10 +158,12 @@ def test_initial_conditions_interpolated_from_a_source_grid():
     assert outside.any() and not e32[outside].any() and not u32[outside].any()
 
 
-def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm():
+@pytest.mark.parametrize("alternate", [0, 1])
+def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm(alternate):
     """The beach child driven by the parent's series: <dL/d eta0, delta> from the GPU adjoint
-    against the oracle's forced tangent model, with gauges on an input edge and inside. Same
-    bound as the unforced dot-product tests (1e-4 of the largest term)."""
+    against the oracle's forced tangent model, with gauges on an input edge and inside, for
+    both sweep orders. Same bound as the unforced dot-product tests (1e-4 of the largest
+    term)."""
     from workloads import Nest
     w = workloads.beach_200(200, 120, steps=300)
     d64 = P.f32(P.oracle_depth(w))
@@ -172,7 +177,8 @@ def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm():
     cxs, cys = w.x[i0:i0 + cx], w.y[j0:j0 + cy]
     gauges = np.array([(0, 32), (3, 40), (40, 32), (70, 20), (85, 32)], np.int32)
     n = w.steps
-    g = CliffsGrid(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, gauges=[tuple(q) for q in gauges])
+    g = CliffsGrid(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, gauges=[tuple(q) for q in gauges],
+                   alternate=alternate)
     g.set_bathy(cxs, cys, d64[sub], False)
     g.set_initial(w.eta0[sub].astype(np.float32))
     for e in range(4):
@@ -181,7 +187,7 @@ def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm():
     seed = rng.standard_normal((n + 1, len(gauges))).astype(np.float32)
     grad = g.adjoint(n, seed, checkpoint_every=37).astype(np.float64)
     assert np.isfinite(grad).all()
-    pc = oracle.params(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2)
+    pc = oracle.params(cx, cy, w.dt, h_min=w.h_min, manning_n2=w.manning_n2, alternate=alternate)
     yy, xx = np.meshgrid(np.arange(cy), np.arange(cx), indexing="ij")
     worst = 0.0
     for k, (gx, gy, sig) in enumerate(((6.0, 30.0, 8.0), (45.0, 25.0, 10.0), (20.0, 40.0, 14.0))):
@@ -197,7 +203,7 @@ def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm():
         err = abs(got - want) / scale
         worst = max(worst, err)
         assert err <= 1e-4, (k, got, want, scale)
-    P.report("adjoint_dot_forced_beach_child", rel_err=worst)
+    P.report("adjoint_dot_forced_beach_child_alt%d" % alternate, rel_err=worst)
     # an edge node under input reaches the loss only through its own record at step 0
     assert grad[32, 0] == pytest.approx(float(seed[0, 0]), rel=1e-6)
     assert not grad[1:31, 0].any() and not grad[:, -1][1:-1].any()
