@@ -202,6 +202,8 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
  * added. dL_dgauges may be NULL (the gradient is then zero). 2D grids; on a batched grid
  * this is scenario 0 (cliffs_adjoint_scenario takes any). With the alternating order the
  * steps keep the forward's parity (steps counted from set_initial).
+ * With checkpoint_every == 1 every state is kept and read in place: no recomputation, at
+ * n states of 12 bytes per node (25 GB for 2000 steps of a 1024^2 grid).
  * Memory: (checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per node,
  * kept for later calls.
  * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 1, checkpoint_every < 1,

@@ -621,6 +621,19 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.open_edges = g->cfg.open_edges;
 }
 
+// dst[3][n] = (a, b, c): the three state planes into one checkpoint in one launch (n a
+// multiple of 4; all pointers 16-byte aligned)
+__global__ void k_copy3(float* __restrict__ dst, const float* __restrict__ a, const float* __restrict__ b,
+                        const float* __restrict__ c, long long n) {
+    const long long n4 = n / 4;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long f = i / n4, k = i - f * n4;
+        const float4* src = reinterpret_cast<const float4*>(f == 0 ? a : f == 1 ? b : c);
+        reinterpret_cast<float4*>(dst)[i] = __ldg(src + k);
+    }
+}
+
 // Keep the current state of a recorded run as checkpoint `idx` (grows the store by doubling).
 int record_checkpoint(cliffs_grid* g, long long idx) {
     const size_t st = sizeof(float) * 3 * g->plane;
@@ -638,9 +651,9 @@ int record_checkpoint(cliffs_grid* g, long long idx) {
     }
     const int cb = (int)(g->step & 1);
     float* dst = g->rec_ckpt + (size_t)3 * g->plane * idx;
-    CK(cudaMemcpyAsync(dst, g->eta[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
-    CK(cudaMemcpyAsync(dst + g->plane, g->u[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
-    CK(cudaMemcpyAsync(dst + 2 * g->plane, g->v[cb], sizeof(float) * g->plane, cudaMemcpyDeviceToDevice, g->stream));
+    k_copy3<<<1216, 256, 0, g->stream>>>(dst, g->eta[cb], g->u[cb], g->v[cb], g->plane);
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "checkpoint copy: %s", cudaGetErrorString(le));
     return CLIFFS_OK;
 }
 
@@ -1614,13 +1627,17 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     Y.open_lo = (g->cfg.open_edges >> 2) & 1; Y.open_hi = (g->cfg.open_edges >> 3) & 1;   // S, N
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
-        CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+        // a one-step segment (every state kept: K = 1) is read where it is stored, with no
+        // copy and no recomputation
+        const float* kept = (j1 - j0 == 1) ? ckpt + 3 * P * sg : nullptr;
+        if (!kept)
+            CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
         for (long long j = j0; j + 1 < j1; ++j) {
             int rc = fwd((int)(j - j0), (int)(j - j0 + 1), j);
             if (rc) return rc;
         }
         for (long long j = j1 - 1; j >= j0; --j) {
-            const float* st = slot((int)(j - j0));
+            const float* st = kept ? kept : slot((int)(j - j0));
             // with boundary input the stored state is imposed again first (the step ran on the
             // imposed state), and the seed goes in after the input edges of lambda_j are zeroed
             if (g->bnd_any) {

@@ -238,9 +238,14 @@ def test_recorded_run_gradient_equals_the_checkpoint_pass_gradient():
     with pytest.raises(CliffsError) as e:
         g.adjoint_recorded(seed)
     assert e.value.code == ERR_STATE
+    assert np.array_equal(g.adjoint(n, seed, checkpoint_every=1), ref)   # every state kept, read in place
     g.adjoint_record(20)
     g.step(50)
     g.step(40)                                   # the record follows the run across calls
+    assert np.array_equal(g.adjoint_recorded(seed), ref)
+    g.set_initial(w.eta0.astype(np.float32))     # a record of every state: no recomputation
+    g.adjoint_record(1)
+    g.step(n)
     assert np.array_equal(g.adjoint_recorded(seed), ref)
     with pytest.raises(CliffsError) as e:
         g.step(2, persistent=True)
@@ -442,3 +447,16 @@ def test_autograd_on_whole_records_matches_finite_differences():
             assert err <= FD_RTOL, (k, fd, grad[k])
     P.report("adjoint_fd_records", rel_err=worst)
     g.close()
+
+
+def test_every_state_kept_with_the_alternating_order():
+    """checkpoint_every = 1 (each state read where it is stored) gives the bits of any other
+    spacing, also with y-first steps."""
+    w = _alternate()
+    g = _start(w, alternate=1)
+    n = 41
+    seed = np.random.default_rng(9).standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    a7 = g.adjoint(n, seed, checkpoint_every=7)
+    a1 = g.adjoint(n, seed, checkpoint_every=1)
+    g.close()
+    assert np.array_equal(a1, a7) and np.abs(a1).max() > 0
