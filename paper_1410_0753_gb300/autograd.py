@@ -48,5 +48,13 @@ class GaugeRun(torch.autograd.Function):
         return out, None, None, None, None
 
 
-def gauge_run(eta0, grid, n, checkpoint_every=100, records=False):
+def gauge_run(eta0, grid, n, checkpoint_every=None, records=False):
+    """Run n steps from eta0 and return the gauge records (see GaugeRun). With
+    checkpoint_every None the run keeps every state when they fit in half the free device
+    memory (the backward then recomputes nothing), else a checkpoint every 100 steps."""
+    if checkpoint_every is None:
+        free, _ = torch.cuda.mem_get_info()
+        pitch = (grid.nx + 31) // 32 * 32
+        need = 12 * pitch * grid.ny * (int(n) + 1)
+        checkpoint_every = 1 if need < free // 2 else 100
     return GaugeRun.apply(eta0, grid, n, checkpoint_every, records)

@@ -267,7 +267,11 @@ def test_recorded_run_gradient_equals_the_checkpoint_pass_gradient():
     g.step(3)
     out.backward(torch.tensor(seed, device="cuda"))
     a2 = eta.grad.detach().cpu().numpy()
-    assert np.array_equal(a1, ref) and np.array_equal(a2, ref)
+    eta.grad = None
+    out = gauge_run(eta, g, n)                   # default: every state kept (it fits), nothing recomputed
+    out.backward(torch.tensor(seed, device="cuda"))
+    a3 = eta.grad.detach().cpu().numpy()
+    assert np.array_equal(a1, ref) and np.array_equal(a2, ref) and np.array_equal(a3, ref)
     g.close()
 
 
