@@ -68,7 +68,10 @@ def profiled(name, rows_per_warp=None):
     if d.get("source_sha") != kernel_source_sha():
         return None, "stale"
     if d.get("rows_per_warp") and rows_per_warp and d["rows_per_warp"] != rows_per_warp:
-        return None, "profiled at %d rows per warp, this run took %d" % (d["rows_per_warp"], rows_per_warp)
+        t = d.get("tiles", {}).get(str(rows_per_warp))
+        if not t:
+            return None, "profiled at %d rows per warp, this run took %d" % (d["rows_per_warp"], rows_per_warp)
+        d = dict(d, rows_per_warp=rows_per_warp, **t)
     return d, d.get("note")
 
 
