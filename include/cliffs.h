@@ -148,8 +148,8 @@ int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
  * values at the current model time, linearly interpolated between records (the first or last
  * record outside their span), edges in the order W, E, S, N (S and N own the corners); an
  * edge without input stays a reflecting wall. nt = 0 removes the edge's input. batch == 1
- * only; a grid with input runs through cliffs_step_n (not the persistent run); the adjoint
- * takes the input as fixed (the imposed edge values carry no sensitivity). Errors: ERR_ARG (edge, sizes, times not increasing, batch > 1). */
+ * only; cliffs_step_n and the persistent run take it; the adjoint takes the input as fixed
+ * (the imposed edge values carry no sensitivity). Errors: ERR_ARG (edge, sizes, times not increasing, batch > 1). */
 int cliffs_set_boundary_input(cliffs_grid* g, int edge, const double* times, int64_t nt, const double* vals);
 
 /* Model clock under boundary input (parameter-file fields 5, cuke, and 13). The run starts at
@@ -178,11 +178,13 @@ int cliffs_step_n(cliffs_grid* g, int64_t n);
  * batch of uneven durations keeps every SM busy until the longest ends. The launch is
  * captured once into a CUDA graph (a copy of the step range into a device control block,
  * then the kernel) and replayed by later calls; it is captured again when a launch argument
- * changes (tile shape, record buffers, durations). 2D grids only; the alternating order and
- * open edges are taken, boundary input and a recorded run are not (cliffs_step_n). The grid
- * barrier waits at most about a second per step before it sets the timeout flag.
- * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 0, boundary input, a recorded
- * run); ERR_UNSTABLE as for
+ * changes (tile shape, record buffers, durations). 2D grids only; the alternating order, open
+ * edges and boundary input are taken (the input is imposed by the kernel before each step
+ * from the interpolation cliffs_step_n would use, computed on the host; the run stops where
+ * cliffs_step_n would stop), a recorded run is not (cliffs_step_n). The grid barrier waits
+ * at most about a second per step before it sets the timeout flag.
+ * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 0, a recorded run);
+ * ERR_UNSTABLE as for
  * cliffs_step_n; ERR_TIMEOUT when a bounded wait gave up; ERR_CUDA (including a device
  * that cannot launch cooperatively). */
 int cliffs_run_persistent(cliffs_grid* g, int64_t n);

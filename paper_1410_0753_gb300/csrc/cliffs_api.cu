@@ -207,22 +207,7 @@ struct BndStep {
 __global__ void k_bnd(float* eta, float* u, float* v, int pitch, int nx, int ny, BndStep b) {
     const int e = blockIdx.y;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!b.vals[e] || q >= b.np[e]) return;
-    if (e < 2 && ((q == 0 && b.vals[2]) || (q == ny - 1 && b.vals[3])) && nx > 1 && ny > 1) return;
-    const int ix = (e == 0) ? 0 : (e == 1) ? nx - 1 : q;
-    const int iy = (e == 2) ? 0 : (e == 3) ? ny - 1 : q;
-    const int np = b.np[e];
-    const double* r0 = b.vals[e] + b.k[e] * 3 * np;
-    const double w = b.w[e];
-    double val[3];
-    for (int f = 0; f < 3; ++f) {
-        const double a = r0[f * np + q];
-        val[f] = (w > 0.0) ? (1.0 - w) * a + w * r0[(3 + f) * np + q] : a;
-    }
-    const size_t o = (size_t)iy * pitch + ix;
-    u[o] = (float)val[0];
-    v[o] = (float)val[1];
-    eta[o] = (float)val[2];
+    bnd_apply(eta, u, v, pitch, nx, ny, e, q, b.vals, b.np, b.k[e], b.w[e]);
 }
 
 // Bilinear interpolation of a source field [sny][snx] onto the master nodes: per master
@@ -345,6 +330,8 @@ struct cliffs_grid {
                                              // and an intermediate adjoint (3 transposed planes)
     std::vector<double> bnd_t[4];
     double* bnd_v[4] = {nullptr, nullptr, nullptr, nullptr};
+    BndRow* bnd_rows = nullptr;              // per-step interpolation table of a persistent run
+    long long bnd_rows_cap = 0;
     bool bnd_any = false;
     double t_start = 0.0;
     bool bnd_stop = false;
@@ -658,9 +645,10 @@ int record_checkpoint(cliffs_grid* g, long long idx) {
 }
 
 // Boundary input at model time t into the edge nodes of a state (batch 1).
-int impose_boundary(cliffs_grid* g, float* eta, float* u, float* v, double t) {
-    BndStep b{};
-    int npmax = 0;
+// The record and weight of every edge's input at model time t (the first or last record
+// outside their span).
+static BndRow bnd_row(const cliffs_grid* g, double t) {
+    BndRow r{};
     for (int e = 0; e < 4; ++e) {
         const std::vector<double>& T = g->bnd_t[e];
         if (T.empty()) continue;
@@ -672,10 +660,34 @@ int impose_boundary(cliffs_grid* g, float* eta, float* u, float* v, double t) {
             i = (long long)(std::upper_bound(T.begin(), T.end(), t) - T.begin()) - 1;
             w = (t - T[i]) / (T[i + 1] - T[i]);
         }
+        r.k[e] = i;
+        r.w[e] = w;
+    }
+    return r;
+}
+
+// Model time of the state after `step` steps, and the end of the shortest record.
+static double bnd_time(const cliffs_grid* g, long long step) { return g->t_start + (double)step * g->cfg.dt; }
+static double bnd_end(const cliffs_grid* g) {
+    double t_end = 1e300;
+    for (int e = 0; e < 4; ++e)
+        if (!g->bnd_t[e].empty()) t_end = std::min(t_end, g->bnd_t[e].back());
+    return t_end;
+}
+static bool bnd_stops(const cliffs_grid* g, double t, double t_end) {
+    return g->bnd_stop && t + g->cfg.dt > t_end * (1.0 + 1e-12) + 1e-9 * g->cfg.dt;
+}
+
+int impose_boundary(cliffs_grid* g, float* eta, float* u, float* v, double t) {
+    BndStep b{};
+    int npmax = 0;
+    const BndRow r = bnd_row(g, t);
+    for (int e = 0; e < 4; ++e) {
+        if (g->bnd_t[e].empty()) continue;
         b.vals[e] = g->bnd_v[e];
         b.np[e] = e < 2 ? g->ny : g->nx;
-        b.k[e] = i;
-        b.w[e] = w;
+        b.k[e] = r.k[e];
+        b.w[e] = r.w[e];
         npmax = std::max(npmax, b.np[e]);
     }
     k_bnd<<<dim3((npmax + 127) / 128, 4), 128, 0, g->stream>>>(eta, u, v, g->pitch, g->nx, g->ny, b);
@@ -705,6 +717,7 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
     cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
     for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
+    cudaFree(g->bnd_rows);
     cudaFree(g->rec_ckpt);
     cudaFree(g->adj_alt);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -1211,16 +1224,13 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
     if (rc) return rc;
     cudaStream_t s = g->stream;
     StepArgs a;
-    double t_end = 1e300;
-    if (g->bnd_any)
-        for (int e = 0; e < 4; ++e)
-            if (!g->bnd_t[e].empty()) t_end = std::min(t_end, g->bnd_t[e].back());
+    const double t_end = g->bnd_any ? bnd_end(g) : 1e300;
     for (long long k = 0; k < n; ++k) {
         const long long st = g->step + 1;
         const int in = (int)(g->step & 1), out = 1 - in;
         if (g->bnd_any) {
-            const double t = g->t_start + (double)g->step * g->cfg.dt;
-            if (g->bnd_stop && t + g->cfg.dt > t_end * (1.0 + 1e-12) + 1e-9 * g->cfg.dt) break;
+            const double t = bnd_time(g, g->step);
+            if (bnd_stops(g, t, t_end)) break;
             rc = impose_boundary(g, g->eta[in], g->u[in], g->v[in], t);
             if (rc) return rc;
         }
@@ -1278,8 +1288,13 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (n < 0) return set_err(CLIFFS_ERR_ARG, "negative step count");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the persistent run needs a 2D grid");
-    if (g->bnd_any) return set_err(CLIFFS_ERR_ARG, "a grid under boundary input runs through cliffs_step_n");
     if (g->rec_K > 0) return set_err(CLIFFS_ERR_ARG, "a recorded run goes through cliffs_step_n");
+    if (g->bnd_any) {                             // the steps cliffs_step_n would take
+        const double t_end = bnd_end(g);
+        long long m = 0;
+        while (m < n && !bnd_stops(g, bnd_time(g, g->step + m), t_end)) ++m;
+        n = m;
+    }
     if (n == 0) return CLIFFS_OK;
     const long long last = g->step + n;
     int rc = grow_records(g, last / g->cfg.gout + 1, last / g->cfg.bndout + 1);
@@ -1321,6 +1336,26 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
     b.nrec = g->NN ? g->nrec : nullptr;
     b.nrec_row = (long long)g->NN * 3;
     b.alternate = g->cfg.alternate;
+    if (g->bnd_any) {
+        // the interpolation of every step of this run, computed as cliffs_step_n does
+        if (g->bnd_rows_cap < n) {
+            cudaFree(g->bnd_rows);
+            g->bnd_rows = nullptr;
+            const long long cap = std::max<long long>(n, 2 * g->bnd_rows_cap);
+            CK(cudaMalloc(&g->bnd_rows, sizeof(BndRow) * cap));
+            g->bnd_rows_cap = cap;
+        }
+        std::vector<BndRow> rows(n);
+        for (long long j = 0; j < n; ++j) rows[j] = bnd_row(g, bnd_time(g, g->step + j));
+        CK(cudaMemcpyAsync(g->bnd_rows, rows.data(), sizeof(BndRow) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        b.bnd = 1;
+        b.bnd_rows = g->bnd_rows;
+        for (int e = 0; e < 4; ++e) {
+            b.bv[e] = g->bnd_t[e].empty() ? nullptr : g->bnd_v[e];
+            b.bnp[e] = e < 2 ? g->ny : g->nx;
+        }
+    }
     if (!b.order) {                               // no durations: every scenario, in index order
         std::vector<int> id(g->B);
         for (int i = 0; i < g->B; ++i) id[i] = i;

@@ -64,6 +64,12 @@ struct StepMaps2 {
 // graph serves every call: ctl[0] = steps done before the launch, ctl[1] = steps done after
 // it, ctl[2] = grid barrier (arrival count in the low 32 bits, generation in the high 32),
 // ctl[3] = work-item ticket counters for even (low 32 bits) and odd (high 32) steps.
+// Interpolation of one step's boundary input per edge: record k and weight w toward k + 1.
+struct BndRow {
+    long long k[4];
+    double w[4];
+};
+
 struct BatchArgs {
     long long* ctl;
     const int* order;                // scenarios by decreasing step limit
@@ -78,7 +84,36 @@ struct BatchArgs {
     float* nrec;                     // enclosed-grid corner records, row = step / bndout
     long long nrec_row;
     int alternate;                   // y first on the odd steps (the alternating order)
+    // boundary input (batch 1): before step step0 + 1 + j the edge nodes of its input take
+    // record k, weight w of bnd_rows[j] (computed on the host as cliffs_step_n does)
+    int bnd;
+    const BndRow* bnd_rows;
+    const double* bv[4];             // records [nt][3][np] per edge, or null
+    int bnp[4];                      // nodes per edge
 };
+
+// Edge node q of edge e (0 W, 1 E, 2 S, 3 N) takes its input (u, v, eta) from record k with
+// weight w toward k + 1 (the interpolation in FP64, non-fused, then rounded to FP32). S and
+// N own the corners when they carry input. Shared by the per-step kernel and the persistent
+// one, so both give the same bits.
+__device__ __forceinline__ void bnd_apply(float* eta, float* u, float* v, int pitch, int nx, int ny, int e, int q,
+                                          const double* const* vals, const int* np, long long k, double w) {
+    if (!vals[e] || q >= np[e]) return;
+    if (e < 2 && ((q == 0 && vals[2]) || (q == ny - 1 && vals[3])) && nx > 1 && ny > 1) return;
+    const int ix = (e == 0) ? 0 : (e == 1) ? nx - 1 : q;
+    const int iy = (e == 2) ? 0 : (e == 3) ? ny - 1 : q;
+    const int n = np[e];
+    const double* r0 = vals[e] + k * 3 * n;
+    double val[3];
+    for (int f = 0; f < 3; ++f) {
+        const double a = r0[f * n + q];
+        val[f] = (w > 0.0) ? __dadd_rn(__dmul_rn(__dsub_rn(1.0, w), a), __dmul_rn(w, r0[(3 + f) * n + q])) : a;
+    }
+    const size_t o = (size_t)iy * pitch + ix;
+    u[o] = (float)val[0];
+    v[o] = (float)val[1];
+    eta[o] = (float)val[2];
+}
 
 // launchers (cliffs_step.cu)
 cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s);

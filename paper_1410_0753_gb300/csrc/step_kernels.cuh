@@ -461,6 +461,21 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
     for (long long st = step0 + 1; st <= step_end; ++st) {
         const bool yf = ALT && (((st - 1) & 1) != 0);
         if (yf) WY.used = W.used;
+        if (B.bnd) {
+            // boundary input: the edge nodes of this step's input take the input at its model
+            // time, then every block waits so that no TMA load reads an edge before it is set
+            const BndRow& R = B.bnd_rows[st - step0 - 1];
+            float* ei = (st & 1) ? B.eta[0] : B.eta[1];
+            float* ui = (st & 1) ? B.u[0] : B.u[1];
+            float* vi = (st & 1) ? B.v[0] : B.v[1];
+            const int per = 2 * a.ny + 2 * a.nx;
+            for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < per; idx += gridDim.x * blockDim.x) {
+                const int e = idx < a.ny ? 0 : idx < 2 * a.ny ? 1 : idx < 2 * a.ny + a.nx ? 2 : 3;
+                const int q = e == 0 ? idx : e == 1 ? idx - a.ny : e == 2 ? idx - 2 * a.ny : idx - 2 * a.ny - a.nx;
+                bnd_apply(ei, ui, vi, a.pitch, a.nx, a.ny, e, q, B.bv, B.bnp, R.k[e], R.w[e]);
+            }
+            if (!grid_sync(reinterpret_cast<unsigned long long*>(B.ctl + 2), gridDim.x, a.wait_cycles, a.err)) break;
+        }
         const bool odd = (st & 1) != 0;          // odd steps read buffer 0 and write buffer 1
         const bool mx = st % B.maxout == 0;
         StepOut O{odd ? &MM.m[0] : &MM.m[1], odd ? B.eta[1] : B.eta[0], odd ? B.u[1] : B.u[0],

@@ -55,9 +55,6 @@ def test_nesting_chain_is_bit_exact_on_the_gpu():
     ce, cu, cv = ch.state()
     for a, b in ((ce, pe), (cu, pu), (cv, pv)):
         assert np.array_equal(a[1:-1, 1:-1], b[sub][1:-1, 1:-1])
-    with pytest.raises(CliffsError) as e:
-        ch.step(2, persistent=True)
-    assert e.value.code == ERR_ARG
     ch.close()
 
 
@@ -208,3 +205,39 @@ def test_adjoint_under_boundary_input_dot_product_against_oracle_tlm(alternate):
     assert grad[32, 0] == pytest.approx(float(seed[0, 0]), rel=1e-6)
     assert not grad[1:31, 0].any() and not grad[:, -1][1:-1].any()
     g.close()
+
+
+@pytest.mark.parametrize("alternate", [0, 1])
+def test_persistent_run_under_boundary_input_equals_per_step(alternate):
+    """The persistent run imposes the input itself before each step (its blocks write the
+    edges, then meet at a grid barrier) from the host's interpolation table: state, maxima and
+    records equal the per-step path bit for bit, across calls, with the cuke start and the
+    stop at the end of the records."""
+    from workloads import Nest
+    x, y, d, eta0 = _open_water()
+    dt, steps = 1.5, 60
+    i0, j0, cx, cy = 41, 33, 70, 64
+    nest = Nest(x[i0], y[j0], 100.0, 100.0, cx, cy)
+    par = CliffsGrid(len(x), len(y), dt, manning_n2=6.25e-4, nests=[nest], bndout=1)
+    par.set_bathy(x, y, d, False)
+    par.set_initial(eta0.astype(np.float32))
+    par.step(steps)
+    series = [par.boundary(0, e) for e in range(4)]
+    par.close()
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    times = 10.0 + dt * np.arange(steps + 1) * 0.8         # records every 1.2 s: interpolated
+    runs = []
+    for pers in (False, True):
+        ch = CliffsGrid(cx, cy, dt, manning_n2=6.25e-4, gauges=[(0, 20), (5, 30), (35, 32)], alternate=alternate)
+        ch.set_bathy(x[i0:i0 + cx], y[j0:j0 + cy], d[sub], False)
+        ch.set_initial(eta0[sub].astype(np.float32))
+        for e in range(4):
+            ch.set_boundary_input(e, times, series[e])
+        ch.set_boundary_clock(1e-4, stop_at_end=True)
+        ch.step(17, persistent=pers)
+        ch.step(1000, persistent=pers)                     # stops at the end of the records
+        runs.append((ch.steps_done, ch.state() + ch.maxwave() + (ch.gauges(),)))
+        ch.close()
+    assert runs[0][0] == runs[1][0] and 17 < runs[0][0] < 1000
+    for p, q in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(p, q)
