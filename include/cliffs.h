@@ -231,14 +231,23 @@ int cliffs_adjoint_records(cliffs_grid* g, int32_t scenario, int64_t n, int32_t 
 /* cliffs_adjoint_recorded with dL/d (eta, u, v) of the records, [nrec][G][3]. */
 int cliffs_adjoint_recorded_records(cliffs_grid* g, const float* dL_drecords, float* dL_deta0);
 
+/* cliffs_adjoint_recorded for scenario `scenario` of a recorded batched run, with
+ * components 1 (dL/d eta of the records, [nrec][G]) or 3 (dL/d (eta, u, v), [nrec][G][3]).
+ * The scenario must have run every recorded step (its duration at least the record's
+ * length). Errors: ERR_STATE without a record; ERR_ARG (scenario outside 0..batch-1, a
+ * scenario that stopped earlier, components not 1 or 3); as cliffs_adjoint_n. */
+int cliffs_adjoint_recorded_scenario(cliffs_grid* g, int32_t scenario, int32_t components, const float* dL,
+                                     float* dL_deta0);
+
 /* Record the forward run for the adjoint (no counterpart in the paper). With
  * checkpoint_every = K > 0, called right after cliffs_set_initial, the initial state and then
- * every K-th state produced by cliffs_step_n are kept (12 bytes per node each, the store grows
- * as the run does), so that cliffs_adjoint_recorded needs no checkpoint pass of its own. A
- * later cliffs_set_initial starts a new record with the same spacing; K = 0 stops recording
- * and frees the store. A recording grid runs through cliffs_step_n only (the persistent run
- * rejects it). Errors: ERR_STATE before set_initial or after steps since it; ERR_ARG (K < 0,
- * 1D grid, batch > 1). */
+ * every K-th state produced by cliffs_step_n are kept (12 bytes per node and scenario each,
+ * the store grows as the run does), so that cliffs_adjoint_recorded needs no checkpoint pass
+ * of its own. A later cliffs_set_initial starts a new record with the same spacing; K = 0
+ * stops recording and frees the store. A recording grid runs through cliffs_step_n only (the
+ * persistent run rejects it). On a batched grid every scenario is recorded
+ * (cliffs_adjoint_recorded_scenario). Errors: ERR_STATE before set_initial or after steps
+ * since it; ERR_ARG (K < 0, 1D grid). */
 int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every);
 
 /* cliffs_adjoint_n for the run recorded since the last cliffs_set_initial: n = the steps

@@ -30,7 +30,7 @@ __all__ = [
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
-    "cliffs_adjoint_recorded_records", "EXPORTED",
+    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -46,7 +46,7 @@ EXPORTED = [
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
-    "cliffs_adjoint_recorded_records",
+    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario",
 ]
 
 
@@ -97,6 +97,7 @@ def lib():
             "cliffs_set_rows_per_warp": ([vp, C.c_int32], C.c_int),
             "cliffs_adjoint_records": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_recorded_records": ([vp, vp, vp], C.c_int),
+            "cliffs_adjoint_recorded_scenario": ([vp, C.c_int32, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
@@ -242,6 +243,11 @@ def cliffs_adjoint_records(g, scenario, n, checkpoint_every, dL_drecords, out):
 def cliffs_adjoint_recorded_records(g, dL_drecords, out):
     ps, ks = _ptr(dL_drecords, np.float32)
     _check(lib().cliffs_adjoint_recorded_records(g, ps, _out_ptr(out)))
+
+
+def cliffs_adjoint_recorded_scenario(g, scenario, components, dL, out):
+    ps, ks = _ptr(dL, np.float32)
+    _check(lib().cliffs_adjoint_recorded_scenario(g, int(scenario), int(components), ps, _out_ptr(out)))
 
 
 def cliffs_state_ptrs(g, scenario):
@@ -490,14 +496,12 @@ class CliffsGrid:
         """Keep checkpoints of the run from the current initial state (0 stops recording)."""
         cliffs_adjoint_record(self.h, checkpoint_every)
 
-    def adjoint_recorded(self, dL_dgauges, out=None):
+    def adjoint_recorded(self, dL_dgauges, out=None, scenario=0):
         """Gradient for the run recorded since the last set_initial (see adjoint)."""
         if out is None:
             out = np.empty((self.ny, self.nx), np.float32)
-        if dL_dgauges is not None and len(getattr(dL_dgauges, "shape", ())) == 3:   # [nrec][G][3]
-            cliffs_adjoint_recorded_records(self.h, dL_dgauges, out)
-        else:
-            cliffs_adjoint_recorded(self.h, dL_dgauges, out)
+        comps = 3 if dL_dgauges is not None and len(getattr(dL_dgauges, "shape", ())) == 3 else 1
+        cliffs_adjoint_recorded_scenario(self.h, scenario, comps, dL_dgauges, out)
         return out
 
     def adjoint_velocity(self):

@@ -623,7 +623,7 @@ __global__ void k_copy3(float* __restrict__ dst, const float* __restrict__ a, co
 
 // Keep the current state of a recorded run as checkpoint `idx` (grows the store by doubling).
 int record_checkpoint(cliffs_grid* g, long long idx) {
-    const size_t st = sizeof(float) * 3 * g->plane;
+    const size_t st = sizeof(float) * 3 * g->B * g->plane;         // [3][batch][plane]
     if (idx >= g->rec_cap) {
         const long long cap = std::max<long long>(idx + 1, 2 * g->rec_cap);
         float* nb = nullptr;
@@ -637,8 +637,8 @@ int record_checkpoint(cliffs_grid* g, long long idx) {
         g->rec_cap = cap;
     }
     const int cb = (int)(g->step & 1);
-    float* dst = g->rec_ckpt + (size_t)3 * g->plane * idx;
-    k_copy3<<<1216, 256, 0, g->stream>>>(dst, g->eta[cb], g->u[cb], g->v[cb], g->plane);
+    float* dst = g->rec_ckpt + (size_t)3 * g->B * g->plane * idx;
+    k_copy3<<<1216, 256, 0, g->stream>>>(dst, g->eta[cb], g->u[cb], g->v[cb], (long long)g->B * g->plane);
     const cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "checkpoint copy: %s", cudaGetErrorString(le));
     return CLIFFS_OK;
@@ -1435,14 +1435,15 @@ int cliffs_adjoint_record(cliffs_grid* g, int32_t checkpoint_every) {
     if (checkpoint_every < 0) return set_err(CLIFFS_ERR_ARG, "checkpoint_every must be >= 0");
     if (checkpoint_every == 0) {
         cudaFree(g->rec_ckpt);
-    cudaFree(g->adj_alt);
+        cudaFree(g->adj_alt);
+        g->adj_alt = nullptr;
         g->rec_ckpt = nullptr;
         g->rec_cap = 0;
         g->rec_K = 0;
         g->rec_n = 0;
         return CLIFFS_OK;
     }
-    if (g->kind != 0 || g->B != 1) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid with batch == 1");
+    if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->step != 0) return set_err(CLIFFS_ERR_STATE, "record from the initial state (no steps since set_initial)");
     g->rec_K = checkpoint_every;
@@ -1466,10 +1467,16 @@ int cliffs_adjoint_records(cliffs_grid* g, int32_t scenario, int64_t n, int32_t 
 }
 
 int cliffs_adjoint_recorded_records(cliffs_grid* g, const float* dL_drecords, float* dL_deta0) {
+    return cliffs_adjoint_recorded_scenario(g, 0, 3, dL_drecords, dL_deta0);
+}
+
+int cliffs_adjoint_recorded_scenario(cliffs_grid* g, int32_t scenario, int32_t components, const float* dL,
+                                     float* dL_deta0) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (components != 1 && components != 3) return set_err(CLIFFS_ERR_ARG, "components must be 1 or 3");
     if (g->rec_K <= 0 || g->rec_n < 1) return set_err(CLIFFS_ERR_STATE, "no recorded run");
-    return adjoint_core(g, 0, g->rec_n, g->rec_K, dL_drecords, dL_deta0, g->rec_ckpt, 3);
+    return adjoint_core(g, scenario, g->rec_n, g->rec_K, dL, dL_deta0, g->rec_ckpt, components);
 }
 
 // Adjoint of a y-first step j of the alternating order, X_{j+1} = x-sweep(y-sweep(X_j)),
@@ -1525,7 +1532,9 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
     if (g->kind != 0) return set_err(CLIFFS_ERR_ARG, "the adjoint needs a 2D grid");
     if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d outside 0..%d", scenario, g->B - 1);
-    if (recorded && g->B != 1) return set_err(CLIFFS_ERR_ARG, "a recorded run needs batch == 1");
+    if (recorded && !g->limit_h.empty() && g->limit_h[scenario] < n)
+        return set_err(CLIFFS_ERR_ARG, "scenario %d stopped after %lld of the %lld recorded steps", scenario,
+                       (long long)g->limit_h[scenario], (long long)n);
     if (n < 1 || checkpoint_every < 1) return set_err(CLIFFS_ERR_ARG, "need n >= 1 and checkpoint_every >= 1");
     if (!recorded && !g->limit_h.empty() && g->step + n > g->limit_h[scenario])
         return set_err(CLIFFS_ERR_ARG, "scenario %d stops after %lld steps, before %lld more", scenario,
@@ -1613,6 +1622,9 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
         return CLIFFS_OK;
     };
     const float* ckpt = recorded ? recorded : g->adj_ckpt;
+    const long long cfield = recorded ? (long long)g->B * P : P;      // floats between fields
+    const long long cstride = 3 * cfield;                             // floats between checkpoints
+    const long long coff = recorded ? (long long)scenario * P : 0;    // the scenario's plane
     // X_0: the grid's current state (or the recorded run's first checkpoint)
     const int cb = (int)cur_buf(g, scenario);
     const size_t so = (size_t)scenario * P;                 // the scenario's plane
@@ -1664,9 +1676,12 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
         const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
         // a one-step segment (every state kept: K = 1) is read where it is stored, with no
         // copy and no recomputation
-        const float* kept = (j1 - j0 == 1) ? ckpt + 3 * P * sg : nullptr;
+        // a checkpoint holds [3][batch][plane] (recorded) or [3][plane]: this scenario's fields
+        const float* c0 = ckpt + cstride * sg + coff;
+        const float* kept = (j1 - j0 == 1 && cfield == P) ? c0 : nullptr;
         if (!kept)
-            CK(cudaMemcpyAsync(slot(0), ckpt + 3 * P * sg, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+            for (int f = 0; f < 3; ++f)
+                CK(cudaMemcpyAsync(slot(0) + f * P, c0 + f * cfield, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
         for (long long j = j0; j + 1 < j1; ++j) {
             int rc = fwd((int)(j - j0), (int)(j - j0 + 1), j);
             if (rc) return rc;

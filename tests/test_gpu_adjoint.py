@@ -464,3 +464,39 @@ def test_every_state_kept_with_the_alternating_order():
     a1 = g.adjoint(n, seed, checkpoint_every=1)
     g.close()
     assert np.array_equal(a1, a7) and np.abs(a1).max() > 0
+
+
+def test_recorded_batched_run_per_scenario():
+    """A recorded batched forward keeps every scenario's states; the recorded adjoint of a
+    scenario equals its checkpoint-pass adjoint from the same initial state bit for bit (with
+    a checkpoint every 7 steps and with every state kept), for eta and for whole-record
+    seeds; a scenario that stopped before the end of the record is refused."""
+    w = workloads.ensemble_512(batch=3, nx=96, ny=80, dmin=30, dmax=50)
+    n = 30
+    rng = np.random.default_rng(47)
+    seed = rng.standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
+    seed3 = rng.standard_normal((n // w.gout + 1, len(w.gauges), 3)).astype(np.float32)
+    g = _start(w)
+    g.set_durations(w.durations)
+    refs = {b: (g.adjoint(n, seed, checkpoint_every=7, scenario=b), g.adjoint(n, seed3, checkpoint_every=7, scenario=b))
+            for b in (0, 2)}
+    for K in (7, 1):
+        g.set_initial(w.eta0.astype(np.float32))
+        g.adjoint_record(K)
+        g.step(n)
+        for b in (0, 2):
+            assert np.array_equal(g.adjoint_recorded(seed, scenario=b), refs[b][0])
+            assert np.array_equal(g.adjoint_recorded(seed3, scenario=b), refs[b][1])
+    g.adjoint_record(0)
+    g.close()
+    short = w.durations.copy()
+    short[1] = n - 5
+    g = _start(w)
+    g.set_durations(short)
+    g.adjoint_record(5)
+    g.step(n)
+    with pytest.raises(CliffsError) as e:
+        g.adjoint_recorded(seed, scenario=1)
+    assert e.value.code == ERR_ARG
+    assert np.array_equal(g.adjoint_recorded(seed, scenario=0), refs[0][0])
+    g.close()
