@@ -10,14 +10,18 @@ through ctypes:
 * ``depth_filter``  - the depth-jump filter (eqs. dstab, newdw, newdc)
 * ``sweep_line``    - one 1D sweep of one line with the record of steps (a)-(e)
 * ``run``           - time steps with max-wave, gauges and enclosed-grid boundary series
-* ``run_tlm``       - the tangent-linear model of ``run`` (branches frozen on the primal)
+* ``run_tlm``       - the tangent-linear model of ``run`` (branches frozen on the primal), with
+  the gauge tangents of eta or of (eta, u, v)
 * ``run_forced``    - ``run`` under boundary input on the domain edges
+* ``run_tlm_forced`` - the tangent-linear model under boundary input
 * ``interp_initial`` - initial conditions from a source grid onto the master grid
+``params(..., open_edges=...)`` makes outer edges open (radiating) instead of walls.
 
 Parity status of each part (what pins it) is listed in the tests under ``tests/test_oracle_*``.
-The spherical metric (reading 7) is pinned only by its Cartesian limit and by propagation
-speed in longitude; beyond that its parity is unpinned (the paper defers the spherical
-equations to another reference).
+The spherical metric (reading 7) is pinned by its Cartesian limit at the equator, the
+propagation speed in longitude and the area-weighted volume with the continuity term; the
+metric momentum terms, which the paper leaves to another reference, are not modelled, and
+that part of its parity is unpinned.
 """
 from __future__ import annotations
 

@@ -16,7 +16,9 @@
 //   * the depth-jump filter of section "Numerical stability", eqs. (dstab), (newdw),
 //     (newdc);
 //   * the outputs of section "Running Options": max-wave (field maxout), gauges
-//     (gout), and boundary series for enclosed grids (bndout).
+//     (gout), and boundary series for enclosed grids (bndout);
+//   * boundary input on the domain edges and open (radiating) outer edges, both readings
+//     where the paper gives no condition (stated where they are computed).
 // Where the paper is silent, the readings are listed at the top of each function.
 //
 // Two algebraic forms of the same update are provided: form 0 is the literal one
