@@ -109,7 +109,8 @@ int cliffs_grid_create(const cliffs_config* cfg, cliffs_grid** out);
 int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const double* depth,
                      int apply_filter, double alpha, double min_depth);
 
-/* Read back the FP64 depth in use (after the filter and any quake deformation), [ny][nx]. */
+/* Read back the FP64 depth in use (after the filter and any quake deformation), [ny][nx]
+ * (host or device array). Errors: ERR_ARG (NULL argument); ERR_STATE before set_bathy. */
 int cliffs_read_depth(cliffs_grid* g, double* depth);
 
 /* Set the initial state of one scenario (scenario in [0, batch)) or of all (scenario = -1,
@@ -136,7 +137,9 @@ int cliffs_set_initial_interp(cliffs_grid* g, int scenario, const double* sx, in
                               int32_t sny, const float* eta, const float* u, const float* v, int quake);
 
 /* Per-scenario step limits for a batched grid: scenario b stops after steps[b] steps
- * (its state, max-wave and records then stay as they were). Default: unlimited. */
+ * (its state, max-wave and records then stay as they were). steps[batch] is copied (host or
+ * device); NULL removes the limits. Default: unlimited. Errors: ERR_ARG (no grid, a
+ * negative duration). */
 int cliffs_set_durations(cliffs_grid* g, const int64_t* steps);
 
 /* Boundary input (section "Running Options", "The input to the computations": one series
@@ -228,7 +231,8 @@ int cliffs_adjoint_scenario(cliffs_grid* g, int32_t scenario, int64_t n, int32_t
 int cliffs_adjoint_records(cliffs_grid* g, int32_t scenario, int64_t n, int32_t checkpoint_every,
                            const float* dL_drecords, float* dL_deta0);
 
-/* cliffs_adjoint_recorded with dL/d (eta, u, v) of the records, [nrec][G][3]. */
+/* cliffs_adjoint_recorded with dL/d (eta, u, v) of the records, [nrec][G][3].
+ * Errors: as cliffs_adjoint_recorded. */
 int cliffs_adjoint_recorded_records(cliffs_grid* g, const float* dL_drecords, float* dL_deta0);
 
 /* cliffs_adjoint_recorded for scenario `scenario` of a recorded batched run, with
@@ -291,27 +295,32 @@ int cliffs_set_rows_per_warp(cliffs_grid* g, int32_t rows);
  * or hang is involved. Errors: ERR_ARG (no grid, cycles <= 0, 1D grid). */
 int cliffs_inject_wait_expiry(cliffs_grid* g, int64_t cycles);
 
-/* Steps completed since set_initial (for a batched grid, by the longest scenario). */
+/* Steps completed since set_initial (for a batched grid, by the longest scenario).
+ * Errors: ERR_ARG (NULL argument). */
 int cliffs_steps_done(cliffs_grid* g, int64_t* steps);
 
 /* Gauge records of one scenario (section "Running Options", the _gages output): writes
- * out[nrec][n_gauges][3] as (eta, u, v) at steps 0, gout, 2 gout, ... and sets *nrec.
- * With out == NULL only *nrec is set. */
+ * out[nrec][n_gauges][3] as (eta, u, v) at steps 0, gout, 2 gout, ... (host or device) and
+ * sets *nrec. With out == NULL only *nrec is set. Errors: ERR_ARG (NULL grid or nrec, a
+ * scenario outside 0..batch-1). */
 int cliffs_read_gauges(cliffs_grid* g, int scenario, float* out, int64_t* nrec);
 
 /* Max-wave of one scenario (the _maxwave output): maximal eta and maximal current
  * sqrt(u^2 + v^2) over wet nodes at the steps multiple of maxout and at the current
- * (last) step, [ny][nx] each; never-wet nodes hold -FLT_MAX and 0. Either pointer may be
- * NULL. */
+ * (last) step, [ny][nx] each (host or device); never-wet nodes hold -FLT_MAX and 0. Either
+ * pointer may be NULL. Errors: ERR_ARG (no grid, scenario out of range); ERR_STATE before
+ * set_initial. */
 int cliffs_read_maxwave(cliffs_grid* g, int scenario, float* eta_max, float* speed_max);
 
 /* Boundary series for one edge of one enclosed grid (the _west/_east/_south/_north
  * outputs): vals[nt][3][np] as (u, v, eta) in FP64 at steps 0, bndout, 2 bndout, ..., with
  * np = nest ny (west, east) or nx (south, north), the master state interpolated bilinearly
- * in the master grid's index space. With vals == NULL only *nt is set. */
+ * in the master grid's index space. With vals == NULL only *nt is set. Errors: ERR_ARG
+ * (NULL grid or nt, nest or edge out of range). */
 int cliffs_read_boundary(cliffs_grid* g, int nest, int edge, double* vals, int64_t* nt);
 
-/* Current state of one scenario, [ny][nx] each; any pointer may be NULL. */
+/* Current state of one scenario, [ny][nx] each (host or device); any pointer may be NULL.
+ * Errors: ERR_ARG (no grid, scenario out of range). */
 int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float* v);
 
 /* The current state of one scenario as library-owned device memory, for zero-copy views
@@ -326,7 +335,7 @@ int cliffs_state_ptrs(cliffs_grid* g, int scenario, float** eta, float** u, floa
 /* Kernel timing: enable != 0 records CUDA events around every sweep kernel launch (on the
  * grid's stream) from now on; *ms and *launches (either may be NULL) receive the total
  * device time and count of those launches since timing was enabled or last reset; the call
- * synchronises. enable < 0 resets the totals. */
+ * synchronises. enable < 0 resets the totals. Errors: ERR_ARG (no grid); ERR_CUDA. */
 int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches);
 
 /* The depth-jump filter of cliffs_set_bathy for callers that cannot allocate device
