@@ -241,3 +241,40 @@ def test_persistent_run_under_boundary_input_equals_per_step(alternate):
     assert runs[0][0] == runs[1][0] and 17 < runs[0][0] < 1000
     for p, q in zip(runs[0][1], runs[1][1]):
         assert np.array_equal(p, q)
+
+
+def test_input_edges_with_open_edges_against_the_oracle():
+    """Input on the west and east edges, the south and north edges open: the GPU's forced run
+    against the oracle's (the open ghosts act on the edges without input)."""
+    from workloads import Nest
+    x, y, d, eta0 = _open_water()
+    dt, steps = 1.5, 80
+    i0, j0, cx, cy = 41, 33, 70, 64
+    nest = Nest(x[i0], y[j0], 100.0, 100.0, cx, cy)
+    par = CliffsGrid(len(x), len(y), dt, manning_n2=6.25e-4, nests=[nest], bndout=1)
+    par.set_bathy(x, y, d, False)
+    par.set_initial(eta0.astype(np.float32))
+    par.step(steps)
+    series = {e: (dt * np.arange(steps + 1), par.boundary(0, e).astype(np.float64)) for e in (0, 1)}
+    par.close()
+    sub = (slice(j0, j0 + cy), slice(i0, i0 + cx))
+    gauges = np.array([(0, 20), (35, 0), (35, 63), (30, 30)], np.int32)
+    d64 = d[sub].astype(np.float64)
+    pc = oracle.params(cx, cy, dt, manning_n2=6.25e-4, open_edges=12)
+    o = oracle.run_forced(pc, x[i0:i0 + cx], y[j0:j0 + cy], d64, eta0[sub], series, nsteps=steps, gout=1,
+                          gauges=gauges)
+    g = CliffsGrid(cx, cy, dt, manning_n2=6.25e-4, open_edges=12, gauges=[tuple(q) for q in gauges])
+    g.set_bathy(x[i0:i0 + cx], y[j0:j0 + cy], d[sub], False)
+    g.set_initial(eta0[sub].astype(np.float32))
+    for e in (0, 1):
+        g.set_boundary_input(e, series[e][0], series[e][1])
+    g.step(steps)
+    rel, absol = P.gauge_errors(g.gauges()[:, :, 0], o["gauges"][:, :, 0])
+    P.report("forced_with_open_edges", gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0))
+    assert rel.max(initial=0.0) <= P.GAUGE_RTOL and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
+    assert np.abs(g.state()[0] - o["eta"]).max() <= 1e-4 * np.abs(eta0).max()
+    # the open edges matter: with walls there the run differs
+    w = oracle.run_forced(oracle.params(cx, cy, dt, manning_n2=6.25e-4), x[i0:i0 + cx], y[j0:j0 + cy], d64,
+                          eta0[sub], series, nsteps=steps)
+    assert np.abs(w["eta"] - o["eta"]).max() > 1e-3
+    g.close()
