@@ -262,9 +262,14 @@ def _form_batched(torch, stream, workloads, CliffsGrid):
     g1.close()
     v_b = useful / (ms_b / 1e3) / 1e9
     v_1 = w.cells * n1 / (ms_1 / 1e3) / 1e9
+    # per useful cell-update: eta, u and v read and written (FP32); the one depth plane is
+    # shared by every live scenario, so it adds 4 B / batch
+    bpc = 24.0 + 4.0 / w.batch
+    peaks, _ = measured_peaks()
     return {
         "workload": w.name, "scenarios": int(w.batch), "durations": [int(w.durations.min()), int(w.durations.max())],
         "value": v_b, "unit": UNIT, "ms": ms_b, "launches": 1,
+        "bytes_per_cell": bpc, "achieved_gbs": v_b * bpc, "frac": v_b * bpc / peaks["hbm_gbs"],
         "rows_per_warp": min(tune, key=tune.get) if tune else None,
         "single_scenario_forward": {"value": v_1, "unit": UNIT, "steps": n1,
                                     "note": "one scenario, one launch per step, same grid"},
