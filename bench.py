@@ -221,7 +221,7 @@ def _event_ms(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_forms(torch, stream, only=None, adjoint_steps=None):
+def measure_forms(torch, stream, only=None, adjoint_steps=None, ensemble=None):
     """The batched ensemble (256 scenarios of uneven duration on one 512 x 512 bathymetry, one
     persistent graph-captured launch) and the adjoint (1024 x 1024, 2000 steps, checkpoint
     every 100), each reported against the plain single-scenario forward on this GPU."""
@@ -230,7 +230,7 @@ def measure_forms(torch, stream, only=None, adjoint_steps=None):
     out = {}
     s = stream.cuda_stream
     if only in (None, "batched"):
-        out["batched"] = _form_batched(torch, stream, workloads, CliffsGrid)
+        out["batched"] = _form_batched(torch, stream, workloads, CliffsGrid, ensemble)
     if only in (None, "stress"):
         out["stress"] = _form_stress(torch, stream, workloads, CliffsGrid)
     if only in (None, "adjoint"):
@@ -238,9 +238,12 @@ def measure_forms(torch, stream, only=None, adjoint_steps=None):
     return out
 
 
-def _form_batched(torch, stream, workloads, CliffsGrid):
+def _form_batched(torch, stream, workloads, CliffsGrid, ensemble=None):
+    # ensemble = (scenarios, shortest, longest duration) shrinks the 256-scenario ensemble to
+    # a case small enough for a profiler capture
     s = stream.cuda_stream
-    w = workloads.ensemble_512()
+    w = workloads.ensemble_512() if ensemble is None else \
+        workloads.ensemble_512(batch=ensemble[0], dmin=ensemble[1], dmax=ensemble[2])
     g = CliffsGrid.from_workload(w, stream=s)
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
     eta0 = w.eta0.astype(np.float32)
@@ -521,6 +524,8 @@ def main():
     ap.add_argument("--forms-only", choices=["batched", "stress", "adjoint"],
                     help="measure one form only and print it (no headline line)")
     ap.add_argument("--adjoint-steps", type=int, default=None)
+    ap.add_argument("--ensemble", default=None, metavar="B,DMIN,DMAX",
+                    help="batched form on B scenarios of DMIN..DMAX steps instead of 256 of 500..4000")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fix the fused step's tile instead of autotuning it")
     args = ap.parse_args()
@@ -529,8 +534,9 @@ def main():
         import torch
         from paper_1410_0753_gb300 import _build
         _build.build()
+        ens = tuple(int(t) for t in args.ensemble.split(",")) if args.ensemble else None
         print(json.dumps({"forms": measure_forms(torch, torch.cuda.current_stream(), args.forms_only,
-                                                 args.adjoint_steps)}), flush=True)
+                                                 args.adjoint_steps, ens)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
