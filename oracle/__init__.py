@@ -111,11 +111,18 @@ def threads(n: int = 0) -> int:
 
 
 def _d(a):
-    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+    # the C side reads every array in row-major order
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
 def _i(a):
-    return a.ctypes.data_as(C.POINTER(C.c_int)) if a is not None else None
+    if a is None:
+        return None
+    assert a.dtype.itemsize == 4 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_int))
 
 
 def params(nx, ny, dt, coords=1, h_min=0.01, manning_n2=0.0, itopo=1, dwall=0.0, transverse=1,
@@ -144,9 +151,9 @@ def sweep_line(p: OracleParams, ds, d, eta, w, t, src=None):
     n = len(d)
     ds = np.ascontiguousarray(ds, np.float64)
     d = np.ascontiguousarray(d, np.float64)
-    eta = np.array(eta, np.float64)
-    w = np.array(w, np.float64)
-    t = np.array(t, np.float64)
+    eta = np.array(eta, np.float64, order="C")
+    w = np.array(w, np.float64, order="C")
+    t = np.array(t, np.float64, order="C")
     src = None if src is None else np.ascontiguousarray(src, np.float64)
     r = {k: np.zeros(n, np.int32) for k in ("wet0", "wet1", "src")}
     r.update({k: np.zeros(n) for k in ("eta_b", "w_b", "t_b", "eta_d", "w_d", "t_d")})
@@ -190,9 +197,9 @@ def run(p: OracleParams, x, y, depth, eta, u=None, v=None, nsteps=0, step0=0,
     x = np.ascontiguousarray(x, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
-    eta = np.array(eta, np.float64).reshape(ny, nx)
-    u = np.zeros_like(eta) if u is None else np.array(u, np.float64).reshape(ny, nx)
-    v = np.zeros_like(eta) if v is None else np.array(v, np.float64).reshape(ny, nx)
+    eta = np.array(eta, np.float64, order="C").reshape(ny, nx)
+    u = np.zeros_like(eta) if u is None else np.array(u, np.float64, order="C").reshape(ny, nx)
+    v = np.zeros_like(eta) if v is None else np.array(v, np.float64, order="C").reshape(ny, nx)
     nrec_cap = (nsteps + 1) if max_records is None else max_records
     eta_max = speed_max = None
     if maxout > 0:
@@ -248,9 +255,9 @@ def run_forced(p: OracleParams, x, y, depth, eta, boundary, u=None, v=None, nste
     x = np.ascontiguousarray(x, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
-    eta = np.array(eta, np.float64).reshape(ny, nx)
-    u = np.zeros_like(eta) if u is None else np.array(u, np.float64).reshape(ny, nx)
-    v = np.zeros_like(eta) if v is None else np.array(v, np.float64).reshape(ny, nx)
+    eta = np.array(eta, np.float64, order="C").reshape(ny, nx)
+    u = np.zeros_like(eta) if u is None else np.array(u, np.float64, order="C").reshape(ny, nx)
+    v = np.zeros_like(eta) if v is None else np.array(v, np.float64, order="C").reshape(ny, nx)
     keep = []
     tp = (C.POINTER(C.c_double) * 4)()
     vp = (C.POINTER(C.c_double) * 4)()
@@ -320,8 +327,8 @@ def run_tlm_forced(p: OracleParams, x, y, depth, eta, deta, boundary, nsteps=0, 
     x = np.ascontiguousarray(x, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
-    eta = np.array(eta, np.float64).reshape(ny, nx)
-    deta = np.array(deta, np.float64).reshape(ny, nx)
+    eta = np.array(eta, np.float64, order="C").reshape(ny, nx)
+    deta = np.array(deta, np.float64, order="C").reshape(ny, nx)
     z = [np.zeros_like(eta) for _ in range(4)]
     keep = []
     tp = (C.POINTER(C.c_double) * 4)()
@@ -358,13 +365,13 @@ def run_tlm(p: OracleParams, x, y, depth, eta, deta, u=None, v=None, du=None, dv
     x = np.ascontiguousarray(x, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
-    eta = np.array(eta, np.float64).reshape(ny, nx)
-    deta = np.array(deta, np.float64).reshape(ny, nx)
+    eta = np.array(eta, np.float64, order="C").reshape(ny, nx)
+    deta = np.array(deta, np.float64, order="C").reshape(ny, nx)
     z = np.zeros_like(eta)
-    u = z.copy() if u is None else np.array(u, np.float64).reshape(ny, nx)
-    v = z.copy() if v is None else np.array(v, np.float64).reshape(ny, nx)
-    du = z.copy() if du is None else np.array(du, np.float64).reshape(ny, nx)
-    dv = z.copy() if dv is None else np.array(dv, np.float64).reshape(ny, nx)
+    u = z.copy() if u is None else np.array(u, np.float64, order="C").reshape(ny, nx)
+    v = z.copy() if v is None else np.array(v, np.float64, order="C").reshape(ny, nx)
+    du = z.copy() if du is None else np.array(du, np.float64, order="C").reshape(ny, nx)
+    dv = z.copy() if dv is None else np.array(dv, np.float64, order="C").reshape(ny, nx)
     gix = np.ascontiguousarray(np.asarray(gauges, np.int32).reshape(-1))
     G = len(gix) // 2
     cap = nsteps + 1

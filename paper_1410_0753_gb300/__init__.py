@@ -173,8 +173,7 @@ def cliffs_set_bathy(g, x, y, depth, apply_filter=1, alpha=2.0, min_depth=0.1):
 
 
 def cliffs_read_depth(g, out):
-    _check(lib().cliffs_read_depth(g, C.c_void_p(out.ctypes.data) if isinstance(out, np.ndarray)
-                                   else C.c_void_p(out.data_ptr())))
+    _check(lib().cliffs_read_depth(g, _out_ptr(out)))
 
 
 def cliffs_set_initial(g, scenario, eta, u=None, v=None, quake=0):

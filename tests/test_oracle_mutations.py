@@ -91,6 +91,26 @@ MUTATIONS = [
      "const T q = right ? T(-2.0 * c0) : C.w - 2.0 * c;",
      "const T q = right ? T(2.0 * c0) : C.w - 2.0 * c;",
      ["test_open_edges_keep_a_lake_at_rest", "test_open_edge_lets_a_simple_wave_leave"]),
+    ("eq. (solver1) flux over one interval instead of two",
+     "Fp = dt * Q_literal(lpR, lpL, pR, pL, R.d, L.d, dsL + dsR);",
+     "Fp = dt * Q_literal(lpR, lpL, pR, pL, R.d, L.d, dsR);",
+     ["test_dalembert_speed_and_second_order", "test_literal_and_perturbation_forms_agree"]),
+    ("eq. (solver1) speed difference without the depth term",
+     "T dcRL = g * ((R.eta - L.eta) + (R.d - L.d)) / (cR + cL);",
+     "T dcRL = g * (R.eta - L.eta) / (cR + cL);",
+     ["test_literal_and_perturbation_forms_agree"]),
+    ("alternating splitting never swaps the order",
+     "const bool yfirst = Gd.P.alternate && (k & 1);", "const bool yfirst = false;",
+     ["test_alternating_sweeps_take_y_first_on_odd_steps"]),
+    ("alternating splitting swaps on even steps",
+     "const bool yfirst = Gd.P.alternate && (k & 1);", "const bool yfirst = Gd.P.alternate && !(k & 1);",
+     ["test_alternating_sweeps_take_y_first_on_odd_steps"]),
+    ("boundary input held at the earlier record",
+     "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
+     ["test_boundary_input_is_linear_between_records"]),
+    ("boundary input weights reversed",
+     "w = (t - times[k]) / (times[k + 1] - times[k]);", "w = (times[k + 1] - t) / (times[k + 1] - times[k]);",
+     ["test_boundary_input_is_linear_between_records"]),
 ]
 
 

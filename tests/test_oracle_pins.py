@@ -90,12 +90,13 @@ def lake_bathy(nx=40, ny=30):
 def test_lake_at_rest(itopo):
     x, y, d = lake_bathy()
     assert (d < 0).any() and (d > 0).any()
-    for form, tol in ((0, 1e-9), (1, 0.0)):
-        p = oracle.params(d.shape[1], d.shape[0], 2.0, h_min=0.01, manning_n2=6.25e-4,
-                          itopo=itopo, dwall=1.0, form=form)
-        r = oracle.run(p, x, y, d, np.zeros_like(d), nsteps=1000)
-        for k in ("eta", "u", "v"):
-            assert np.abs(r[k]).max() <= tol, (form, k, np.abs(r[k]).max())
+    for solver in (2, 1):
+        for form, tol in ((0, 1e-9), (1, 0.0)):
+            p = oracle.params(d.shape[1], d.shape[0], 2.0, h_min=0.01, manning_n2=6.25e-4,
+                              itopo=itopo, dwall=1.0, form=form, solver=solver)
+            r = oracle.run(p, x, y, d, np.zeros_like(d), nsteps=1000)
+            for k in ("eta", "u", "v"):
+                assert np.abs(r[k]).max() <= tol, (solver, form, k, np.abs(r[k]).max())
 
 
 # ----------------------------------------------------------------------------------------
@@ -103,7 +104,7 @@ def test_lake_at_rest(itopo):
 # into two halves moving at +-sqrt(gH) (d'Alembert). The scheme is second order in space
 # (section "Difference Scheme": "second-order accurate in space for a uniform grid").
 
-def dalembert_error(dx):
+def dalembert_error(dx, solver=2):
     H, sigma, A = 10.0, 150.0, 1e-3
     L = 6000.0
     n = int(round(L / dx)) + 1
@@ -115,18 +116,45 @@ def dalembert_error(dx):
     t = steps * dt
     x0 = 3000.0
     eta0 = A * np.exp(-(x - x0) ** 2 / (2 * sigma ** 2))
-    p = oracle.params(n, 1, dt, manning_n2=0.0, h_min=0.01)
+    p = oracle.params(n, 1, dt, manning_n2=0.0, h_min=0.01, solver=solver)
     r = oracle.run(p, x, np.zeros(1), np.full((1, n), H), eta0[None, :], nsteps=steps)
     exact = 0.5 * A * (np.exp(-(x - x0 - c * t) ** 2 / (2 * sigma ** 2)) +
                        np.exp(-(x - x0 + c * t) ** 2 / (2 * sigma ** 2)))
     return np.abs(r["eta"][0] - exact).max() / A
 
 
-def test_dalembert_speed_and_second_order():
-    e10 = dalembert_error(10.0)           # sigma / dx = 15
-    e20 = dalembert_error(20.0)           # sigma / dx = 7.5
+@pytest.mark.parametrize("solver", [2, 1])
+def test_dalembert_speed_and_second_order(solver):
+    e10 = dalembert_error(10.0, solver)   # sigma / dx = 15
+    e20 = dalembert_error(20.0, solver)   # sigma / dx = 7.5
     assert e10 < 0.01, e10
     assert e20 / e10 > 3.0, (e20, e10)
+
+
+# ----------------------------------------------------------------------------------------
+# eq. (eqQ) in the Riemann invariants r = w +- 2c, and the same flux rewritten in
+# perturbation variables: with c^2 = g (eta + d),
+#   1/2 (lam_a + lam_b)(r_a - r_b) - g (d_a - d_b)
+#     = 1/2 (lam_a + lam_b)(w_a - w_b) +- (w_a + w_b)(c_a - c_b) + g (eta_a - eta_b),
+# c_a - c_b = g ((eta_a - eta_b) + (d_a - d_b)) / (c_a + c_b). The oracle computes both; on a
+# moving flow over an uneven bottom they must agree to rounding, under either solver.
+
+@pytest.mark.parametrize("solver", [2, 1])
+def test_literal_and_perturbation_forms_agree(solver):
+    rng = np.random.default_rng(17)
+    n = 80
+    x = np.concatenate([[0.0], np.cumsum(rng.uniform(40.0, 60.0, n - 1))])
+    d = 12.0 + 8.0 * np.sin(x / 300.0) + 3.0 * rng.random(n)
+    eta = 0.8 * np.exp(-(x - x[30]) ** 2 / (2 * 200.0 ** 2))
+    u = 0.4 * np.sin(x / 170.0)
+    out = []
+    for form in (0, 1):
+        p = oracle.params(n, 1, 1.0, h_min=0.01, manning_n2=6.25e-4, solver=solver, form=form)
+        out.append(oracle.run(p, x, np.zeros(1), d[None, :], eta[None, :], u[None, :], nsteps=60))
+    for f in ("eta", "u"):
+        ref = np.abs(out[0][f]).max()
+        assert np.abs(out[0][f] - out[1][f]).max() <= 1e-10 * ref, f
+    assert np.abs(out[1]["eta"] - eta).max() > 0.1                 # the flow did move
 
 
 # ----------------------------------------------------------------------------------------
@@ -811,3 +839,85 @@ def test_runup_workload_takes_the_printed_parameter_file():
         assert w.dt == t["dt"][0] and w.steps == t["steps"][0]
         assert w.extra["slope"] == t["slope"][0] and math.isclose(w.extra["H"] / w.extra["d"], H)
         assert not w.nests and not len(w.gauges)
+
+
+# ----------------------------------------------------------------------------------------
+# Section "Numerics", eqs. (eq2A), (eq2B): the step is the x-problem followed by the
+# y-problem; with alternating splitting the odd steps take them in the other order. The
+# y-sweep of a grid is the x-sweep of its transpose (x <-> y, u <-> v), so a step in the
+# order y then x equals the plain step of the transposed grid, transposed back. That fixes
+# what two alternating steps must give without using the alternating code.
+
+def _shore_problem(nx=14, ny=11, seed=31):
+    rng = np.random.default_rng(seed)
+    x = np.concatenate([[0.0], np.cumsum(rng.uniform(80.0, 120.0, nx - 1))])
+    y = np.concatenate([[0.0], np.cumsum(rng.uniform(80.0, 120.0, ny - 1))])
+    X, Y = np.meshgrid(x, y)
+    d = 15.0 + 45.0 * rng.random((ny, nx))
+    d[:3, :4] = -0.4                                               # a low beach in one corner
+    eta = 1.2 * np.exp(-((X - x[4]) ** 2 + (Y - y[4]) ** 2) / (2 * 260.0 ** 2))
+    eta[d < 0] = -d[d < 0]                                         # dry: h = 0
+    u = 0.1 * rng.standard_normal((ny, nx))
+    v = 0.1 * rng.standard_normal((ny, nx))
+    u[d < 0] = v[d < 0] = 0.0
+    return x, y, d, eta, u, v
+
+
+def _y_then_x(kw, x, y, d, eta, u, v):
+    ny, nx = d.shape
+    r = oracle.run(oracle.params(ny, nx, 1.0, **kw), y, x, d.T, eta.T, v.T, u.T, nsteps=1)
+    return r["eta"].T, r["v"].T, r["u"].T
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_alternating_sweeps_take_y_first_on_odd_steps(form):
+    x, y, d, eta, u, v = _shore_problem()
+    ny, nx = d.shape
+    kw = dict(h_min=0.01, manning_n2=6.25e-4, form=form)
+    alt = oracle.run(oracle.params(nx, ny, 1.0, alternate=1, **kw), x, y, d, eta, u, v, nsteps=2)
+    one = oracle.run(oracle.params(nx, ny, 1.0, **kw), x, y, d, eta, u, v, nsteps=1)   # step 0: x, y
+    e2, u2, v2 = _y_then_x(kw, x, y, d, one["eta"], one["u"], one["v"])               # step 1: y, x
+    for f, ref in (("eta", e2), ("u", u2), ("v", v2)):
+        assert np.abs(alt[f] - ref).max() <= 1e-12 * (1.0 + np.abs(ref).max()), f
+    # an odd first step is y then x
+    odd = oracle.run(oracle.params(nx, ny, 1.0, alternate=1, **kw), x, y, d, eta, u, v, nsteps=1, step0=1)
+    e1, _, _ = _y_then_x(kw, x, y, d, eta, u, v)
+    assert np.abs(odd["eta"] - e1).max() <= 1e-12 * (1.0 + np.abs(e1).max())
+    # the orders differ by far more than the tolerance on this problem
+    plain = oracle.run(oracle.params(nx, ny, 1.0, **kw), x, y, d, eta, u, v, nsteps=2)
+    assert np.abs(plain["eta"] - alt["eta"]).max() > 1e-6
+    assert np.abs(one["eta"] - e1).max() > 1e-6
+
+
+# ----------------------------------------------------------------------------------------
+# Section "Running Options", the input to the computations: boundary input is a time series
+# at the edge nodes. Between records the input is the straight line through the two records
+# (before the first and after the last it holds that record), so imposing a series at a time
+# between records equals imposing the constant series of the interpolated value.
+
+def test_boundary_input_is_linear_between_records():
+    x, y, d, eta0, p, _ = _open_water_parent(nx=12, ny=10)
+    rng = np.random.default_rng(5)
+    ny = d.shape[0]
+    a = 0.3 * rng.standard_normal((3, ny))
+    b = 0.3 * rng.standard_normal((3, ny))
+    series = {0: (np.array([0.0, 4.0]), np.stack([a, b]))}
+
+    def forced(bnd, t0, nsteps=1, **state):
+        return oracle.run_forced(p, x, y, d, state.get("eta", eta0), bnd, u=state.get("u"),
+                                 v=state.get("v"), nsteps=nsteps, t0=t0, step0=state.get("step0", 0))
+
+    for t0, val in ((1.0, 0.75 * a + 0.25 * b), (3.0, 0.25 * a + 0.75 * b),
+                    (-2.0, a), (9.0, b)):
+        got = forced(series, t0)
+        ref = forced({0: (np.array([0.0]), val[None])}, 0.0)
+        for f in ("eta", "u", "v"):
+            assert np.array_equal(got[f], ref[f]), (t0, f)
+    # the model clock advances by dt per step: two steps from t = 1 equal one step at t = 1
+    # and one at t = 1 + dt (1.5 s) = 2.5 s, each against its interpolated constant input
+    two = forced(series, 1.0, nsteps=2)
+    first = forced({0: (np.array([0.0]), (0.75 * a + 0.25 * b)[None])}, 0.0)
+    second = forced({0: (np.array([0.0]), (0.375 * a + 0.625 * b)[None])}, 0.0,
+                    eta=first["eta"], u=first["u"], v=first["v"], step0=1)
+    for f in ("eta", "u", "v"):
+        assert np.array_equal(two[f], second[f]), f
