@@ -3,11 +3,15 @@
 Each case plants one mistake in a temporary copy of ``oracle/cliffs_oracle.cpp`` (a dropped
 term, a wrong sign, a wrong index or factor), builds it with the host compiler, points the
 oracle module at it, and requires at least one pin of ``test_oracle_pins`` to fail. The
-committed oracle is never modified.
+oracle's Python-level functions (quake initialisation, initial-condition interpolation) get
+the same treatment on a mutated copy of their source. The committed oracle is never
+modified.
 """
+import inspect
 import os
 import subprocess
 import tempfile
+import textwrap
 
 import pytest
 
@@ -105,6 +109,9 @@ MUTATIONS = [
     ("alternating splitting swaps on even steps",
      "const bool yfirst = Gd.P.alternate && (k & 1);", "const bool yfirst = Gd.P.alternate && !(k & 1);",
      ["test_alternating_sweeps_take_y_first_on_odd_steps"]),
+    ("eq. (newdc) over alpha instead of alpha^2",
+     "nd = (lw ? line[j - 1] : line[j + 1]) / a2;", "nd = (lw ? line[j - 1] : line[j + 1]) / alpha;",
+     ["test_depth_filter_by_hand"]),
     ("boundary input held at the earlier record",
      "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
      ["test_boundary_input_is_linear_between_records"]),
@@ -157,4 +164,39 @@ def test_pins_catch_planted_mistake(case, tmp_path):
                 caught.append((pname, kw))
     finally:
         oracle.swap_library(None)
+    assert caught, "no pin caught: %s" % name
+
+
+# Mistakes in the oracle's Python-level functions: (name, function, exact text, replacement,
+# pins expected to notice). The mutated function replaces the module's for the pins' calls.
+PY_MUTATIONS = [
+    ("initial-condition weight measured from the far node", "interp_initial",
+     "return k, (xp - c[k]) / (c[k + 1] - c[k])", "return k, (c[k + 1] - xp) / (c[k + 1] - c[k])",
+     ["test_initial_condition_interpolation_exact_for_linear_fields_and_zero_outside"]),
+    ("quake lowers the floor", "quake_init",
+     "return depth - zeta, np.where(wet, zeta, 0.0)", "return depth + zeta, np.where(wet, zeta, 0.0)",
+     ["test_quake_lifts_the_floor_and_the_water_column_with_it"]),
+    ("quake lifts the surface on dry nodes too", "quake_init",
+     "return depth - zeta, np.where(wet, zeta, 0.0)", "return depth - zeta, zeta.copy()",
+     ["test_quake_lifts_the_floor_and_the_water_column_with_it"]),
+    ("quake ignores walls", "quake_init",
+     "wet = (depth >= h_min) & ((itopo != 0) | (depth >= dwall))", "wet = depth >= h_min",
+     ["test_quake_lifts_the_floor_and_the_water_column_with_it"]),
+]
+
+
+@pytest.mark.parametrize("case", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_pins_catch_planted_mistake_in_python(case, monkeypatch):
+    name, fname, old, new, targets = case
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fname)))
+    assert src.count(old) == 1, "mutation anchor must occur exactly once: %r" % old
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant %s>" % fname, "exec"), ns)
+    monkeypatch.setattr(oracle, fname, ns[fname])
+    caught = []
+    for pname, fn, kw in _pin_functions(targets):
+        try:
+            fn(**kw)
+        except (AssertionError, ValueError, FloatingPointError):
+            caught.append((pname, kw))
     assert caught, "no pin caught: %s" % name

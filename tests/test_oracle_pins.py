@@ -921,3 +921,30 @@ def test_boundary_input_is_linear_between_records():
                     eta=first["eta"], u=first["u"], v=first["v"], step0=1)
     for f in ("eta", "u", "v"):
         assert np.array_equal(two[f], second[f]), f
+
+
+# ----------------------------------------------------------------------------------------
+# Section "Running Options", field quake: with quake = 1 the initial deformation zeta is
+# applied to the sea floor. The floor rises by zeta everywhere; over wet nodes the water
+# column rises with it (its height is unchanged, the surface stands at zeta); dry nodes and,
+# with itopo = 0, walls keep a flat surface.
+
+def test_quake_lifts_the_floor_and_the_water_column_with_it():
+    rng = np.random.default_rng(23)
+    d = rng.uniform(-20.0, 80.0, (30, 40))
+    d[0, :5] = [0.0, 0.005, 0.01, 0.02, 3.0]                       # around h_min and a wall
+    zeta = rng.uniform(-1.5, 2.5, d.shape)
+    for itopo, dwall in ((1, 0.0), (0, 5.0)):
+        dn, eta = oracle.quake_init(d, zeta, 0.01, itopo=itopo, dwall=dwall)
+        assert np.allclose(dn + zeta, d, rtol=0.0, atol=1e-12)
+        wet = (d >= 0.01) if itopo else (d >= 5.0)
+        assert np.array_equal(eta[wet], zeta[wet])
+        assert not eta[~wet].any()
+        assert np.allclose((eta + dn)[wet], d[wet], rtol=0.0, atol=1e-12)
+    # by hand: nodes 50 m, 5 mm (below h_min), land and a 2 m node, h_min = 1 cm
+    d4 = np.array([[50.0, 0.005, -3.0, 2.0]])
+    z4 = np.array([[1.0, 0.5, 0.25, -0.5]])
+    dn, eta = oracle.quake_init(d4, z4, 0.01, itopo=1)
+    assert dn.tolist() == [[49.0, -0.495, -3.25, 2.5]] and eta.tolist() == [[1.0, 0.0, 0.0, -0.5]]
+    dn, eta = oracle.quake_init(d4, z4, 0.01, itopo=0, dwall=5.0)  # the 2 m node is a wall
+    assert eta.tolist() == [[1.0, 0.0, 0.0, 0.0]]
