@@ -112,6 +112,12 @@ MUTATIONS = [
     ("eq. (newdc) over alpha instead of alpha^2",
      "nd = (lw ? line[j - 1] : line[j + 1]) / a2;", "nd = (lw ? line[j - 1] : line[j + 1]) / alpha;",
      ["test_depth_filter_by_hand"]),
+    ("gauges recorded every step whatever gout",
+     "O->gout > 0 && k % O->gout == 0", "O->gout > 0",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("max-wave taken every step whatever maxout",
+     "O->maxout > 0 && k % O->maxout == 0", "O->maxout > 0",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
     ("boundary input held at the earlier record",
      "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
      ["test_boundary_input_is_linear_between_records"]),

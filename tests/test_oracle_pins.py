@@ -499,6 +499,13 @@ def test_gauges_maxwave_and_bilinear_boundary():
     for k, (ix, iy) in enumerate(gauges):
         assert r["eta_max"][iy, ix] == g[:, k, 0].max()
     assert r["boundary"][0][0].shape[0] == 11                      # steps 0, 3, ..., 30
+    # cadences: gauges every 4 steps are every 4th record of the run above; max-wave every 5
+    # steps is the maximum over steps 0, 5, ..., 30 (the gauges are wet throughout)
+    r4 = oracle.run(p, x, y, d, eta0, nsteps=30, gout=4, gauges=gauges, maxout=5)
+    assert np.array_equal(r4["gauges"], g[::4])
+    for k, (ix, iy) in enumerate(gauges):
+        assert r4["eta_max"][iy, ix] == g[::5, k, 0].max()
+    assert (r4["eta_max"] <= r["eta_max"]).all() and (r4["eta_max"] < r["eta_max"]).any()
 
 
 # ----------------------------------------------------------------------------------------
