@@ -117,7 +117,8 @@ int cliffs_read_depth(cliffs_grid* g, double* depth);
  * then eta/u/v hold [batch][ny][nx]) (section "Running Options", "input to the
  * computations"): free surface eta (m) and velocities u, v (m/s; NULL means zero). With
  * quake = 1 eta is a sea-floor deformation zeta (parameter-file field 12): the depth becomes
- * d - zeta and the free surface zeta on nodes that were wet (d >= h_min); quake needs
+ * d - zeta and the free surface zeta on nodes that were wet (d >= h_min, and with itopo = 0
+ * d >= dwall), 0 on the others; quake needs
  * batch == 1. Resets the step counter and the records, initialises max-wave from this state
  * and records step 0 (gauges, boundary series).
  * Errors: ERR_STATE before set_bathy; ERR_ARG; ERR_CUDA. */

@@ -231,15 +231,21 @@ def test_spherical_coast_small_with_nests():
 
 # ---------------------------------------------------------------------------- quake, batch
 
-def test_quake_initial_condition():
+@pytest.mark.parametrize("itopo,dwall", [(1, 0.0), (0, 45.0)])
+def test_quake_initial_condition(itopo, dwall):
     w = workloads.beach_200(120, 90, steps=150)
+    w.itopo, w.dwall = itopo, dwall                          # with itopo = 0: the slope is walls
     d64 = P.oracle_depth(w)
     zeta = w.eta0.astype(np.float32)
     g = CliffsGrid.from_workload(w)
     g.set_bathy(w.x, w.y, w.depth)
     g.set_initial(zeta, quake=1)
-    dq, eq = oracle.quake_init(d64, zeta.astype(np.float64), w.h_min)
+    dq, eq = oracle.quake_init(d64, zeta.astype(np.float64), w.h_min, itopo=itopo, dwall=dwall)
     assert np.array_equal(g.depth(), dq)
+    assert np.array_equal(g.state()[0], eq.astype(np.float32))
+    if not itopo:                                            # some walls carry a deformation
+        walls = (d64 >= w.h_min) & (d64 < dwall)
+        assert walls.any() and np.abs(zeta[walls]).max() > 0
     g.step(w.steps)
     o = oracle.run(oracle.params_from(w), w.x, w.y, P.f32(dq), eq, nsteps=w.steps, gout=1,
                    gauges=w.gauges)
