@@ -408,8 +408,21 @@ def test_depth_filter_postconditions():
             wet = c > 0
             assert np.all(~(wet & (l > 0)) | (l <= a2 * c * (1 + 1e-12)))
             assert np.all(~(wet & (r > 0)) | (r <= a2 * c * (1 + 1e-12)))
+            # eqs. (rr), (rstab), (fcond): with alpha = 3 - 2 eps, dstab gives 1 + r >= eps on
+            # both sides of every wet node between wet neighbours, hence f > 0
+            eps = (3.0 - alpha) / 2.0
+            both = wet & (l > 0) & (r > 0)
+            sc, sl, sr = np.sqrt(c[both]), np.sqrt(l[both]), np.sqrt(r[both])
+            assert np.all(1 + (sc - sl) / (2 * sc) >= eps - 1e-12)
+            assert np.all(1 + (sc - sr) / (2 * sc) >= eps - 1e-12)
+            assert np.all(6 * sc > sl + sr)
+            assert both.sum() > 1000
         again, n2 = oracle.depth_filter(out, alpha=alpha)
         assert n2 == 1 and np.array_equal(again, out)  # idempotent
+    # the unfiltered map breaks eq. (fcond) somewhere, so the check above has teeth
+    c, l, r = d[:, 1:-1], d[:, :-2], d[:, 2:]
+    both = (c > 0) & (l > 0) & (r > 0)
+    assert np.any(6 * np.sqrt(c[both]) <= np.sqrt(l[both]) + np.sqrt(r[both]))
     smooth = np.full((20, 20), 30.0) + np.arange(20)[None, :]
     out, n = oracle.depth_filter(smooth)
     assert n == 1 and np.array_equal(out, smooth)   # untouched where dstab holds
