@@ -97,7 +97,7 @@ def _sensitivity(p, w, d64, eta0, n, u0=None, v0=None):
     return float((np.abs(g1 - g0).max(axis=0) / np.maximum(np.abs(g0).max(axis=0), 1e-3)).max())
 
 
-def _judge(name, w, got, o, d64, amp, sens):
+def _assess(name, w, got, o, d64, amp, sens):
     """A run whose own FP64 solution amplifies the perturbation at most tenfold is held to the
     stated tolerances (_check); one that amplifies it more is held to three times its own
     sensitivity on the gauges, and its masks and fields are reported (next to the shoreline
@@ -124,14 +124,14 @@ def test_inversion_1024_full_horizon():
     g = P.gpu_run(w, w.steps)
     o = P.oracle_run(w, w.steps, d64)
     sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
-    _judge("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max(), sens)
+    _assess("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max(), sens)
     g["grid"].close()
 
 
 def test_ensemble_scenarios_full_durations():
     """Three scenarios of the ensemble (the longest, the shortest and the median duration)
     run to their own durations in one persistent launch, each against its own oracle run and
-    judged by its own conditioning (run-up on the ensemble's beach makes some scenarios
+    assessed against its own conditioning (run-up on the ensemble's beach makes some scenarios
     ill-conditioned)."""
     w = workloads.ensemble_512()
     d64 = P.f32(P.oracle_depth(w))
@@ -150,7 +150,7 @@ def test_ensemble_scenarios_full_durations():
         got = dict(eta=e, gauges=g.gauges(b)[: n // w.gout + 1], eta_max=em)
         o = oracle.run(p, w.x, w.y, d64, w.eta0[b], nsteps=n, maxout=w.maxout, gout=w.gout, gauges=w.gauges)
         sens = _sensitivity(p, w, d64, w.eta0[b], n)
-        _judge("horizon_ensemble_scenario_%d" % b, dataclasses.replace(w, steps=n), got, o, d64,
+        _assess("horizon_ensemble_scenario_%d" % b, dataclasses.replace(w, steps=n), got, o, d64,
                np.abs(w.eta0[b]).max(), sens)
     g.close()
 
@@ -162,5 +162,5 @@ def test_spherical_coast_2048_full_horizon():
     g = P.gpu_run(w, w.steps)
     o = P.oracle_run(w, w.steps, d64)
     sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
-    _judge("horizon_spherical_2048", w, g, o, d64, np.abs(w.eta0).max(), sens)
+    _assess("horizon_spherical_2048", w, g, o, d64, np.abs(w.eta0).max(), sens)
     g["grid"].close()
