@@ -332,6 +332,17 @@ int cliffs_read_state(cliffs_grid* g, int scenario, float* eta, float* u, float*
  * pointer may be NULL. Errors: ERR_ARG (scenario out of range). */
 int cliffs_state_ptrs(cliffs_grid* g, int scenario, float** eta, float** u, float** v, int64_t* pitch);
 
+/* Diagnostics of the current state of one scenario (a monitor beside the status codes; the
+ * paper's program logs to a text file instead, section "Running Options"). Over wet nodes
+ * (eta + d >= h_min, and with itopo = 0 d >= dwall, the max-wave test) out[4] (host)
+ * receives: out[0] the displaced volume sum eta * A (m^3; A the node's area from its control
+ * widths, half the distance to each neighbour and the full spacing at an end node, in
+ * geographic metrics R^2 cos(phi) dlambda dphi; a one-node axis counts 1 m), out[1] the
+ * number of wet nodes, out[2] max |eta| (m), out[3] the maximum speed sqrt(u^2 + v^2)
+ * (m/s). The call synchronises. Errors: ERR_ARG (NULL argument, scenario out of range);
+ * ERR_STATE before set_initial; ERR_CUDA. */
+int cliffs_diagnostics(cliffs_grid* g, int scenario, double* out);
+
 
 /* Kernel timing: enable != 0 records CUDA events around every sweep kernel launch (on the
  * grid's stream) from now on; *ms and *launches (either may be NULL) receive the total

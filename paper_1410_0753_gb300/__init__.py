@@ -30,7 +30,8 @@ __all__ = [
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
-    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "EXPORTED",
+    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "cliffs_diagnostics",
+    "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -46,7 +47,7 @@ EXPORTED = [
     "cliffs_set_boundary_input", "cliffs_set_boundary_clock", "cliffs_set_initial_interp",
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
-    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario",
+    "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "cliffs_diagnostics",
 ]
 
 
@@ -98,6 +99,7 @@ def lib():
             "cliffs_adjoint_records": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_recorded_records": ([vp, vp, vp], C.c_int),
             "cliffs_adjoint_recorded_scenario": ([vp, C.c_int32, C.c_int32, vp, vp], C.c_int),
+            "cliffs_diagnostics": ([vp, C.c_int, vp], C.c_int),
             "cliffs_adjoint_record": ([vp, C.c_int32], C.c_int),
             "cliffs_state_ptrs": ([vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(C.c_int64)], C.c_int),
@@ -247,6 +249,13 @@ def cliffs_adjoint_recorded_records(g, dL_drecords, out):
 def cliffs_adjoint_recorded_scenario(g, scenario, components, dL, out):
     ps, ks = _ptr(dL, np.float32)
     _check(lib().cliffs_adjoint_recorded_scenario(g, int(scenario), int(components), ps, _out_ptr(out)))
+
+
+def cliffs_diagnostics(g, scenario=0):
+    """(volume m^3, wet nodes, max |eta| m, max speed m/s) of the current state over wet nodes."""
+    out = np.zeros(4, np.float64)
+    _check(lib().cliffs_diagnostics(g, int(scenario), C.c_void_p(out.ctypes.data)))
+    return dict(volume=float(out[0]), wet=int(out[1]), eta_abs_max=float(out[2]), speed_max=float(out[3]))
 
 
 def cliffs_state_ptrs(g, scenario):
@@ -446,6 +455,9 @@ class CliffsGrid:
         if n and self.n_gauges:
             cliffs_read_gauges(self.h, scenario, out)
         return out
+
+    def diagnostics(self, scenario=0):
+        return cliffs_diagnostics(self.h, scenario)
 
     def maxwave(self, scenario=0):
         e = np.empty((self.ny, self.nx), np.float32)

@@ -138,6 +138,49 @@ __global__ void k_max_init(const float* eta, const float* u, const float* v, con
     (void)ny;
 }
 
+// Diagnostics of one state plane (a monitor, not a step of the method): over wet nodes (the
+// max-wave test), the displaced volume sum eta * wx_i * wy_j, the node count, max |eta| and
+// max speed. FP64 sums per block, then one atomic per block; the maxima are non-negative
+// floats, so their bit patterns order like unsigned integers.
+__global__ void k_diag(const float* eta, const float* u, const float* v, const float* d32,
+                       const double* wx, const double* wy, int nx, int ny, int pitch, float hmin,
+                       float dwall, double* acc, unsigned* mx) {
+    double vol = 0.0, cnt = 0.0;
+    float me = 0.f, ms = 0.f;
+    const long long N = (long long)nx * ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / nx), c = (int)(i % nx);
+        const long long o = (long long)r * pitch + c;
+        const float e = eta[o], dd = d32[o];
+        if (!((dd >= dwall) && (e + dd >= hmin))) continue;
+        vol += (double)e * wx[c] * wy[r];
+        cnt += 1.0;
+        me = fmaxf(me, fabsf(e));
+        ms = fmaxf(ms, sqrtf(u[o] * u[o] + v[o] * v[o]));
+    }
+    __shared__ double sv[8], sc[8];
+    __shared__ float se[8], ss[8];
+    for (int k = 16; k > 0; k >>= 1) {
+        vol += __shfl_down_sync(0xffffffffu, vol, k);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, k);
+        me = fmaxf(me, __shfl_down_sync(0xffffffffu, me, k));
+        ms = fmaxf(ms, __shfl_down_sync(0xffffffffu, ms, k));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sv[w] = vol; sc[w] = cnt; se[w] = me; ss[w] = ms; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            vol += sv[k]; cnt += sc[k]; me = fmaxf(me, se[k]); ms = fmaxf(ms, ss[k]);
+        }
+        atomicAdd(&acc[0], vol);
+        atomicAdd(&acc[1], cnt);
+        atomicMax(&mx[0], __float_as_uint(me));
+        atomicMax(&mx[1], __float_as_uint(ms));
+    }
+}
+
 // step-0 record of the gauges / enclosed-grid nodes of scenarios [b0, b0 + nb)
 __global__ void k_record0(const float* eta, const float* u, const float* v, int pitch,
                           long long plane, const int4* items, int nitems, float* rec_g,
@@ -1942,6 +1985,63 @@ int cliffs_state_ptrs(cliffs_grid* g, int scenario, float** eta, float** u, floa
     if (u) *u = g->u[cb] + o;
     if (v) *v = g->v[cb] + o;
     if (pitch) *pitch = g->pitch;
+    return CLIFFS_OK;
+}
+
+// Node control widths along one axis: half the distance to each neighbour, the full spacing
+// at an end node (the wall stands half a spacing beyond it), 1 on a one-node axis.
+static void control_widths(const std::vector<double>& c, std::vector<double>& w) {
+    const size_t n = c.size();
+    w.assign(n, 1.0);
+    if (n < 2) return;
+    w[0] = c[1] - c[0];
+    w[n - 1] = c[n - 1] - c[n - 2];
+    for (size_t i = 1; i + 1 < n; ++i) w[i] = 0.5 * (c[i + 1] - c[i - 1]);
+}
+
+int cliffs_diagnostics(cliffs_grid* g, int scenario, double* out) {
+    g_err[0] = 0;
+    if (!g || !out) return set_err(CLIFFS_ERR_ARG, "null argument");
+    if (scenario < 0 || scenario >= g->B) return set_err(CLIFFS_ERR_ARG, "scenario %d out of range", scenario);
+    if (!g->have_init) return set_err(CLIFFS_ERR_STATE, "set_initial first");
+    const int nx = g->nx, ny = g->ny;
+    std::vector<double> wx, wy;
+    control_widths(g->hx, wx);
+    control_widths(g->hy, wy);
+    if (g->cfg.coords != 1) {                    // lon/lat in degrees: R^2 cos(phi) dlambda dphi
+        for (int i = 0; i < nx; ++i) wx[i] *= R_SPHERE * DEGR;
+        for (int j = 0; j < ny; ++j) wy[j] *= R_SPHERE * DEGR * std::cos(g->hy[j] * DEGR);
+    }
+    std::vector<double> host(nx + ny + 2, 0.0);
+    std::copy(wx.begin(), wx.end(), host.begin());
+    std::copy(wy.begin(), wy.end(), host.begin() + nx);
+    int rc = ensure_tmp(g, sizeof(double) * host.size() + 2 * sizeof(unsigned));
+    if (rc) return rc;
+    double* dw = (double*)g->tmp;
+    unsigned* mx = (unsigned*)(dw + host.size());
+    CK(cudaMemcpyAsync(dw, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), g->stream));
+    const int cb = (int)cur_buf(g, scenario);
+    const size_t o = (size_t)scenario * g->plane;
+    const long long N = (long long)nx * ny;
+    const unsigned blocks = std::min<unsigned>(nblk(N), 1024u);
+    k_diag<<<blocks, 256, 0, g->stream>>>(g->eta[cb] + o, g->u[cb] + o, g->v[cb] + o, g->d32, dw, dw + nx,
+                                          nx, ny, g->pitch, (float)g->cfg.h_min,
+                                          g->cfg.itopo ? -3.402823466e38f : (float)g->cfg.dwall,
+                                          dw + nx + ny, mx);
+    CK(cudaGetLastError());
+    double acc[2];
+    unsigned m[2];
+    CK(cudaMemcpyAsync(acc, dw + nx + ny, sizeof(acc), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(m, mx, sizeof(m), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    float me, ms;
+    std::memcpy(&me, &m[0], sizeof(float));
+    std::memcpy(&ms, &m[1], sizeof(float));
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = me;
+    out[3] = ms;
     return CLIFFS_OK;
 }
 

@@ -294,6 +294,48 @@ def test_exact_resume_from_the_read_state(alternate):
         g.close()
 
 
+def _control_widths(c):
+    c = np.asarray(c, np.float64)
+    if len(c) < 2:
+        return np.ones(len(c))
+    w = np.empty(len(c))
+    w[0], w[-1] = c[1] - c[0], c[-1] - c[-2]
+    w[1:-1] = 0.5 * (c[2:] - c[:-2])
+    return w
+
+
+@pytest.mark.parametrize("name", ["beach", "spherical"])
+def test_diagnostics_against_their_definition_and_the_oracle(name):
+    w = workloads.beach_200(steps=60) if name == "beach" else workloads.spherical_coast(96, 80, steps=60)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    g.step(w.steps)
+    dg = g.diagnostics()
+    e, u, v = g.state()
+    d64 = g.depth()
+    d32 = d64.astype(np.float32)
+    wall = -np.float32(3.402823466e38) if w.itopo else np.float32(w.dwall)
+    wet = (d32 >= wall) & (e + d32 >= np.float32(w.h_min))
+    wx, wy = _control_widths(w.x), _control_widths(w.y)
+    if w.coords != 1:
+        R, deg = 6371000.0, np.pi / 180.0
+        wx = wx * R * deg
+        wy = wy * R * deg * np.cos(np.asarray(w.y, np.float64) * deg)
+    A = wy[:, None] * wx[None, :]
+    ea = e.astype(np.float64) * A
+    assert abs(dg["volume"] - ea[wet].sum()) <= 1e-9 * np.abs(ea[wet]).sum()
+    assert dg["wet"] == wet.sum() and 0 < dg["wet"] < w.nx * w.ny
+    assert dg["eta_abs_max"] == np.abs(e[wet]).max()
+    assert np.isclose(dg["speed_max"], np.sqrt(u * u + v * v)[wet].max(), rtol=1e-6, atol=0.0)
+    # the same volume over the FP64 oracle's state after the same steps
+    o = oracle.run(oracle.params_from(w), w.x, w.y, P.oracle_depth(w), w.eta0, nsteps=w.steps)
+    wo = (o["eta"] + P.oracle_depth(w) >= w.h_min)
+    vo = (o["eta"] * A)[wo].sum()
+    assert abs(dg["volume"] - vo) <= 1e-4 * np.abs(o["eta"] * A)[wo].sum()
+    g.close()
+
+
 def test_batch_with_durations_matches_single_runs():
     w = workloads.ensemble_512(batch=5, nx=96, ny=80, dmin=20, dmax=120)
     g = P.gpu_run(w, int(w.durations.max()) + 5)
