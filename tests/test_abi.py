@@ -79,3 +79,50 @@ def test_loading_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pk, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         pk.lib()
+
+
+# Argument checks that return before any CUDA call (host logic; nothing is launched).
+BAD_GRIDS = [
+    (dict(nx=0, ny=10), "need nx, ny >= 1"),
+    (dict(nx=10, ny=0), "need nx, ny >= 1"),
+    (dict(nx=1, ny=1), "not both 1"),
+    (dict(nx=2, ny=10), "at least 3 nodes"),
+    (dict(nx=10, ny=2), "at least 3 nodes"),
+    (dict(batch=0), "batch"),
+    (dict(h_min=0.0), "h_min"),
+    (dict(dt=0.0), "dt"),
+    (dict(manning_n2=-1e-4), "manning_n2"),
+    (dict(maxout=0), "maxout"),
+    (dict(gout=0), "maxout, gout and bndout"),
+    (dict(solver=3), "solver"),
+    (dict(open_edges=16), "open_edges"),
+    (dict(alternate=2), "alternate"),
+    (dict(gauges=[(10, 3)]), "outside the 10 x 8 grid"),
+    (dict(gauges=[(3, -1)]), "outside the 10 x 8 grid"),
+    (dict(nx=10, ny=1, nests=[pk.cliffs_nest(0.0, 0.0, 1.0, 1.0, 3, 3)]), "2D master grid"),
+    (dict(batch=2, nests=[pk.cliffs_nest(0.0, 0.0, 1.0, 1.0, 3, 3)]), "batch == 1"),
+    (dict(nests=[pk.cliffs_nest(0.0, 0.0, 1.0, 1.0, 1, 3)]), "nest 0"),
+]
+
+
+@pytest.mark.parametrize("kw,msg", BAD_GRIDS, ids=[m for _, m in BAD_GRIDS])
+def test_grid_create_rejects_bad_arguments_on_the_host(built, kw, msg):
+    kw = dict(kw)
+    nx, ny, dt = kw.pop("nx", 10), kw.pop("ny", 8), kw.pop("dt", 1.0)
+    with pytest.raises(pk.CliffsError) as e:
+        pk.CliffsGrid(nx, ny, dt, **kw)
+    assert e.value.code == pk.ERR_ARG
+    assert msg in str(e.value) and msg in pk.cliffs_last_error()
+
+
+def test_null_handles_are_argument_errors(built):
+    out = (C.c_double * 4)()
+    L = pk.lib()
+    for rc in (L.cliffs_step_n(None, 1), L.cliffs_run_persistent(None, 1),
+               L.cliffs_read_state(None, 0, None, None, None),
+               L.cliffs_read_maxwave(None, 0, None, None),
+               L.cliffs_diagnostics(None, 0, out), L.cliffs_set_durations(None, None),
+               L.cliffs_adjoint_n(None, 1, 1, None, None), L.cliffs_grid_create(None, None)):
+        assert rc == pk.ERR_ARG
+    assert "null" in pk.cliffs_last_error()
+    pk.lib().cliffs_destroy(None)                       # destroying nothing is a no-op

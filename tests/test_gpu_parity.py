@@ -485,6 +485,29 @@ def test_error_paths():
     assert e.value.code == ERR_ARG
 
 
+def test_zero_and_negative_step_counts():
+    """n = 0 steps is a no-op (no launch, no record); a negative count is an argument error
+    that leaves the grid as it was."""
+    w = workloads.beach_200(120, 90, steps=10)
+    g = CliffsGrid.from_workload(w)
+    g.set_bathy(w.x, w.y, w.depth)
+    g.set_initial(w.eta0.astype(np.float32))
+    g.step(3)
+    before = g.state(), g.gauges(), g.steps_done
+    g.step(0)
+    with pytest.raises(CliffsError) as e:
+        g.step(-1)
+    assert e.value.code == ERR_ARG
+    with pytest.raises(CliffsError) as e:
+        g.set_initial(w.eta0.astype(np.float32), scenario=1)    # batch 1: no scenario 1
+    assert e.value.code == ERR_ARG
+    after = g.state(), g.gauges(), g.steps_done
+    for a, b in zip(before[0], after[0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(before[1], after[1]) and before[2] == after[2] == 3
+    g.close()
+
+
 def test_bounded_wait_expiry_reports_timeout_and_recovers():
     """A ring wait that can never complete (injected: the slots expect bytes no copy
     delivers) expires after its cycle limit; the step reports CLIFFS_ERR_TIMEOUT, the later
