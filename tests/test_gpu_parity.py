@@ -351,6 +351,10 @@ def test_batch_with_durations_matches_single_runs():
         gb, g1 = grid.gauges(b), single.gauges()
         assert gb.shape == g1.shape == (int(w.durations[b]) + 1, 16, 3)
         assert np.array_equal(gb, g1)
+        # diagnostics of a scenario read its own state plane (block sums add in any order)
+        db, d1 = grid.diagnostics(b), single.diagnostics()
+        assert math.isclose(db["volume"], d1["volume"], rel_tol=1e-12, abs_tol=1e-6)
+        assert (db["wet"], db["eta_abs_max"], db["speed_max"]) == (d1["wet"], d1["eta_abs_max"], d1["speed_max"])
         single.close()
     b = 2
     d64 = P.oracle_depth(w)
