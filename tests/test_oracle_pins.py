@@ -968,3 +968,38 @@ def test_quake_lifts_the_floor_and_the_water_column_with_it():
     assert dn.tolist() == [[49.0, -0.495, -3.25, 2.5]] and eta.tolist() == [[1.0, 0.0, 0.0, -0.5]]
     dn, eta = oracle.quake_init(d4, z4, 0.01, itopo=0, dwall=5.0)  # the 2 m node is a wall
     assert eta.tolist() == [[1.0, 0.0, 0.0, 0.0]]
+
+
+# ----------------------------------------------------------------------------------------
+# The lines of a sweep are independent (eqs. eq2A, eq2B), so the oracle's threads over them
+# cannot change a bit of the result; and the seeded inputs are the same on every call.
+
+def test_oracle_threads_do_not_change_results():
+    w = workloads.spherical_coast(96, 80, steps=40)
+    d = oracle.depth_filter(w.depth, w.filter_alpha, w.filter_min_depth)[0]
+    p = oracle.params_from(w)
+    kw = dict(nsteps=w.steps, maxout=1, gout=1, gauges=w.gauges, bndout=1, nests=w.nests)
+    n0 = oracle.threads()
+    try:
+        oracle.threads(1)
+        one = oracle.run(p, w.x, w.y, d, w.eta0, **kw)
+        oracle.threads(max(2, os.cpu_count() or 2))
+        many = oracle.run(p, w.x, w.y, d, w.eta0, **kw)
+    finally:
+        oracle.threads(n0)
+    for k in ("eta", "u", "v", "eta_max", "speed_max", "gauges"):
+        assert np.array_equal(one[k], many[k]), k
+    for a, b in zip(one["boundary"][0], many["boundary"][0]):
+        assert np.array_equal(a, b)
+
+
+def test_seeded_inputs_repeat():
+    for make in (lambda: workloads.spherical_coast(64, 48, steps=5),
+                 lambda: workloads.ensemble_512(batch=3, nx=40, ny=32),
+                 lambda: workloads.inversion_1024(64, 48, steps=5),
+                 lambda: workloads.shelf_islands(128, 96, steps=5),
+                 lambda: workloads.beach_200(40, 30, steps=5)):
+        a, b = make(), make()
+        for f in ("x", "y", "depth", "eta0"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+        assert np.array_equal(a.gauges, b.gauges)
