@@ -118,6 +118,9 @@ MUTATIONS = [
     ("max-wave taken every step whatever maxout",
      "O->maxout > 0 && k % O->maxout == 0", "O->maxout > 0",
      ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("max-wave without the fold of the final state",
+     "    if (fold_final && eta_max) {", "    if (false && eta_max) {",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
     ("boundary input held at the earlier record",
      "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
      ["test_boundary_input_is_linear_between_records"]),

@@ -519,6 +519,11 @@ def test_gauges_maxwave_and_bilinear_boundary():
     for k, (ix, iy) in enumerate(gauges):
         assert r4["eta_max"][iy, ix] == g[::5, k, 0].max()
     assert (r4["eta_max"] <= r["eta_max"]).all() and (r4["eta_max"] < r["eta_max"]).any()
+    # every 7 steps: steps 0, 7, ..., 28, and the final state (step 30) folded in at the end
+    r7 = oracle.run(p, x, y, d, eta0, nsteps=30, gout=1, gauges=gauges, maxout=7)
+    for k, (ix, iy) in enumerate(gauges):
+        assert r7["eta_max"][iy, ix] == g[[0, 7, 14, 21, 28, 30], k, 0].max()
+    assert any(g[30, k, 0] > g[[0, 7, 14, 21, 28], k, 0].max() for k in range(len(gauges)))
 
 
 # ----------------------------------------------------------------------------------------
