@@ -121,6 +121,14 @@ MUTATIONS = [
     ("max-wave without the fold of the final state",
      "    if (fold_final && eta_max) {", "    if (false && eta_max) {",
      ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("gauge records with u and v swapped",
+     "r[3 * g + 0] = val(eta[c]); r[3 * g + 1] = val(u[c]); r[3 * g + 2] = val(v[c]);",
+     "r[3 * g + 0] = val(eta[c]); r[3 * g + 1] = val(v[c]); r[3 * g + 2] = val(u[c]);",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("boundary series with u and v swapped",
+     "r[3 * p + 0] = bil(u); r[3 * p + 1] = bil(v); r[3 * p + 2] = bil(eta);",
+     "r[3 * p + 0] = bil(v); r[3 * p + 1] = bil(u); r[3 * p + 2] = bil(eta);",
+     ["test_gauges_maxwave_and_bilinear_boundary"]),
     ("boundary input held at the earlier record",
      "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
      ["test_boundary_input_is_linear_between_records"]),

@@ -524,6 +524,14 @@ def test_gauges_maxwave_and_bilinear_boundary():
     for k, (ix, iy) in enumerate(gauges):
         assert r7["eta_max"][iy, ix] == g[[0, 7, 14, 21, 28, 30], k, 0].max()
     assert any(g[30, k, 0] > g[[0, 7, 14, 21, 28], k, 0].max() for k in range(len(gauges)))
+    # record slots: a wave uniform in y moves u only (v stays exactly 0), so gauges hold
+    # (eta, u, v) and boundary series (u, v, eta) in that order
+    ex = 0.3 * np.exp(-(X - 1500) ** 2 / (2 * 300.0 ** 2))
+    rx = oracle.run(p, x, y, d, ex, nsteps=20, gout=1, gauges=gauges, bndout=1, nests=nests)
+    gx = rx["gauges"]
+    assert np.abs(gx[1:, :, 1]).max() > 1e-6 and not gx[:, :, 2].any()
+    Wx = rx["boundary"][0][0]
+    assert np.abs(Wx[1:, 0]).max() > 1e-6 and not Wx[:, 1].any()
 
 
 # ----------------------------------------------------------------------------------------
