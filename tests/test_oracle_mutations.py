@@ -129,6 +129,12 @@ MUTATIONS = [
      "r[3 * p + 0] = bil(u); r[3 * p + 1] = bil(v); r[3 * p + 2] = bil(eta);",
      "r[3 * p + 0] = bil(v); r[3 * p + 1] = bil(u); r[3 * p + 2] = bil(eta);",
      ["test_gauges_maxwave_and_bilinear_boundary"]),
+    ("second-order coefficient over twice the right spacing",
+     "const double k2 = dt * dt / (dsL + dsR);", "const double k2 = dt * dt / (2.0 * dsR);",
+     ["test_pulse_closed_form_on_unequal_spacing"]),
+    ("left flux of p over the right spacing",
+     "T QpL = Q_literal(lpC, lpL, pC, pL, C.d, L.d, dsL);", "T QpL = Q_literal(lpC, lpL, pC, pL, C.d, L.d, dsR);",
+     ["test_pulse_closed_form_on_unequal_spacing"]),
     ("boundary input held at the earlier record",
      "val[f] = (1.0 - w) * a + w * b;", "val[f] = a;",
      ["test_boundary_input_is_linear_between_records"]),

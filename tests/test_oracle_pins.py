@@ -1016,3 +1016,36 @@ def test_seeded_inputs_repeat():
         for f in ("x", "y", "depth", "eta0"):
             assert np.array_equal(getattr(a, f), getattr(b, f)), f
         assert np.array_equal(a.gauges, b.gauges)
+
+
+# ----------------------------------------------------------------------------------------
+# Section "Numerical stability", the one-step pulse response, on unequal spacings: eq.
+# (solver2) applied to a pulse (eta_j, u_j) at node j of a flat basin of depth H, spacings
+# dsL to the left and dsR to the right, gives to second order in the pulse
+#   eta_j' = (1 - b) eta_j - (H dt / 2) s u_j,   u_j' = (1 - b) u_j - (g dt / 2) s eta_j,
+# b = g H dt^2 / (dsL dsR) (the second-order term, k2 = dt^2 / (dsL + dsR)) and
+# s = 1/dsL - 1/dsR (the averaged first-order fluxes); eq. (solver1)'s first-order flux spans
+# the two neighbours at rest, so s = 0 there. With dsL = dsR this is eq. (eq:uet), f = 1.
+
+def unequal_pulse_residual(eps, solver, form, dsL=80.0, dsR=130.0):
+    H, dt, j, n = 30.0, 1.0, 4, 9
+    ds = np.array([100.0, 90.0, 110.0, dsL, dsR, 95.0, 105.0, 100.0])
+    eta = np.zeros(n); u = np.zeros(n)
+    eta[j], u[j] = eps, 0.4 * eps
+    p = line_params(n, dt, manning_n2=0.0, solver=solver, form=form, h_min=0.01)
+    r = oracle.sweep_line(p, ds, np.full(n, H), eta, u, np.zeros(n))
+    b = G * H * dt ** 2 / (dsL * dsR)
+    s = (1 / dsL - 1 / dsR) if solver == 2 else 0.0
+    eta_exp = (1 - b) * eta[j] - 0.5 * H * dt * s * u[j]
+    u_exp = (1 - b) * u[j] - 0.5 * G * dt * s * eta[j]
+    return abs(r["eta"][j] - eta_exp), abs(r["w"][j] - u_exp), abs(eta_exp - eta[j])
+
+
+@pytest.mark.parametrize("solver", [2, 1])
+@pytest.mark.parametrize("form", [0, 1])
+def test_pulse_closed_form_on_unequal_spacing(solver, form):
+    re1, ru1, shift = unequal_pulse_residual(1e-4, solver, form)
+    re2, ru2, _ = unequal_pulse_residual(5e-5, solver, form)
+    for a, b in ((re1, re2), (ru1, ru2)):
+        assert a < 1e-9 and 3.3 < a / b < 4.7, (a, b)
+    assert shift > 1e3 * re1
