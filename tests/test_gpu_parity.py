@@ -8,6 +8,7 @@ except for cells whose oracle height or flooding margin lies within 1e-5 max(1, 
 h_min (counted); the depth filter and every branch-free identity (lake at rest, 1D == 2D)
 bit for bit.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -224,6 +225,30 @@ def test_spherical_coast_small_with_nests():
     wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
     P.report("spherical_300x260", boundary_eta_rel=worst, mask_mismatch=int((wet32 != wet64).sum()),
              mask_mismatch_not_near=int(((wet32 != wet64) & ~near).sum()))
+    assert worst <= 1e-4
+    assert ((wet32 != wet64) & ~near).sum() == 0
+    g["grid"].close()
+
+
+def test_spherical_coast_high_latitude():
+    """The same coast moved to 55-57 N, where cos(phi) is 0.57 instead of 0.94, with its
+    enclosed grids and a time step shortened for the narrower cells (Courant 0.8)."""
+    w = workloads.spherical_coast(200, 160, steps=300)
+    w.y = np.asarray(w.y, np.float64) + 35.0
+    w.nests = [dataclasses.replace(n, y0=n.y0 + 35.0) for n in w.nests]
+    w.dt = 0.6 * w.dt
+    d64 = P.oracle_depth(w)
+    g = P.gpu_run(w, w.steps)
+    o = P.oracle_run(w, w.steps, P.f32(d64))
+    assert_gauges("spherical_high_latitude", g["gauges"], o["gauges"])
+    worst = 0.0
+    for m in range(len(w.nests)):
+        for e in range(4):
+            b32, b64 = g["boundary"][m][e], o["boundary"][m][e]
+            scale = max(np.abs(b64[:, 2]).max(), 1e-3)
+            worst = max(worst, np.abs(b32[:, 2] - b64[:, 2]).max() / scale)
+    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
+    P.report("spherical_high_latitude", boundary_eta_rel=worst, mask_mismatch=int((wet32 != wet64).sum()))
     assert worst <= 1e-4
     assert ((wet32 != wet64) & ~near).sum() == 0
     g["grid"].close()
