@@ -351,25 +351,29 @@ int cliffs_diagnostics(cliffs_grid* g, int scenario, double* out);
 int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches);
 
 /* The depth-jump filter of cliffs_set_bathy for callers that cannot allocate device
- * memory. The paper has no counterpart of this entry point; it serves code that must not
- * call cudaMalloc or cudaFree: code running while a CUDA stream is being captured (the
- * allocation calls are not permitted then), hosts that hand out all device memory from
- * their own pool and forbid hidden allocations, and callers that cannot afford the
- * device-wide synchronisation cudaFree implies. It allocates nothing: its scratch (a second
- * FP64 Jacobi buffer and a flag) is one static device array of CLIFFS_NOALLOC_MAX_CELLS
- * doubles (8 MiB) that every GPU loading the library holds until the process exits.
+ * memory. The paper has no counterpart of this entry point. It serves callers that must not
+ * call cudaMalloc or cudaFree: applications whose own memory pool owns the whole device and
+ * forbids allocations behind its back (a hidden allocation can fail, or fragment the pool),
+ * and callers that cannot afford cudaFree's device-wide synchronisation, which stalls every
+ * stream on the device. It allocates nothing: its scratch (a second FP64 Jacobi buffer and
+ * a flag) is one static device array of CLIFFS_NOALLOC_MAX_CELLS doubles (8 MiB) that every
+ * GPU loading the library holds until the process exits.
  *   depth   [ny][nx] FP64 input depth, positive down (host or device memory)
- *   out     [ny][nx] FP64 filtered depth, DEVICE memory owned by the caller (may equal depth
- *           when depth is device memory; must not overlap it otherwise)
+ *   out     [ny][nx] FP64 filtered depth, DEVICE (or managed) memory owned by the caller;
+ *           it may be the same array as depth, but may not partly overlap it
  *   alpha, min_depth  as in cliffs_set_bathy; stream: cudaStream_t or NULL
  *   passes  receives the passes made (-1: stopped at the 100-pass cap); may be NULL
- * The result is bit-identical to the filter cliffs_set_bathy applies. nx * ny larger than
- * CLIFFS_NOALLOC_MAX_CELLS returns CLIFFS_ERR_ARG with the limit in cliffs_last_error().
+ * The result is bit-identical to the filter cliffs_set_bathy applies (both launch the same
+ * per-node code). Errors: CLIFFS_ERR_ARG, with nothing launched, for a NULL pointer, an
+ * empty grid, alpha outside (1, 3), an out that is not device memory, arrays that partly
+ * overlap, or nx * ny larger than CLIFFS_NOALLOC_MAX_CELLS (the limit is in
+ * cliffs_last_error()); CLIFFS_ERR_CUDA for a failed runtime call.
  * The first call on each device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture. Every call on a device shares the one array and leaves its last contents there
- * (the flag is cleared before each pass): calls that overlap on the GPU (other streams or
- * threads) race and give wrong results. The call synchronises the stream once per pass. */
+ * (cudaGetSymbolAddress) with that device current and keeps it; make that first call before
+ * any stream capture. The kept address does not survive cudaDeviceReset. Every call on a
+ * device shares the one array and leaves its last contents there (the flag is cleared
+ * before each pass): calls that overlap on the GPU (other streams or threads) race and give
+ * wrong results. The call synchronises the stream once per pass to read the flag. */
 #define CLIFFS_NOALLOC_MAX_CELLS (1 << 20)
 int cliffs_depth_filter_noalloc(const double* depth, double* out, int32_t nx, int32_t ny,
                                 double alpha, double min_depth, void* stream, int32_t* passes);

@@ -334,10 +334,24 @@ def cliffs_kernel_time(g, enable):
 
 def cliffs_depth_filter_noalloc(depth, out, nx, ny, alpha=2.0, min_depth=0.1, stream=None) -> int:
     """Depth filter into caller-owned device memory ``out`` with no device allocation (see
-    include/cliffs.h). Returns the passes made."""
+    include/cliffs.h). ``out`` must be a contiguous CUDA float64 tensor of nx * ny elements;
+    ``depth`` may be host (NumPy) or device data. An in-place call (``out`` is ``depth``)
+    needs ``depth`` to be that same contiguous CUDA float64 tensor: a converted copy would be
+    filtered instead of the caller's array. Returns the passes made."""
+    import torch
+    n_cells = int(nx) * int(ny)
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.numel() == n_cells):
+        raise CliffsError(ERR_ARG, "out must be a contiguous CUDA float64 tensor of nx * ny = %d "
+                                   "elements" % n_cells)
+    if isinstance(depth, torch.Tensor) and depth.data_ptr() == out.data_ptr():
+        if not (depth.is_cuda and depth.dtype == torch.float64 and depth.is_contiguous()):
+            raise CliffsError(ERR_ARG, "an in-place call needs depth to be out itself")
+    elif (depth.numel() if isinstance(depth, torch.Tensor) else np.size(depth)) != n_cells:
+        raise CliffsError(ERR_ARG, "depth must have nx * ny = %d elements" % n_cells)
     pd, kd = _ptr(depth, np.float64)
     n = C.c_int32()
-    _check(lib().cliffs_depth_filter_noalloc(pd, _out_ptr(out), int(nx), int(ny), float(alpha),
+    _check(lib().cliffs_depth_filter_noalloc(pd, C.c_void_p(out.data_ptr()), int(nx), int(ny), float(alpha),
                                              float(min_depth), C.c_void_p(stream) if stream else None,
                                              C.byref(n)))
     return n.value

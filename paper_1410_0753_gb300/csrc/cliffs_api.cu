@@ -53,34 +53,14 @@ const double DEGR = 3.14159265358979323846 / 180.0;
 // depth-jump filter, section "Numerical stability": eqs. (dstab), (newdw), (newdc)
 __global__ void k_filter_minraise(double* d, long long n, double min_depth) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n && d[i] > 0.0 && d[i] < min_depth) d[i] = min_depth;
+    if (i < n) filter_minraise_node(d, i, min_depth);
 }
 
 // One Jacobi pass along rows (dir 0) or columns (dir 1).
 __global__ void k_filter_pass(const double* in, double* out, int nx, int ny, int dir, double a2,
                               int* changed) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)nx * ny) return;
-    const int r = (int)(i / nx), c = (int)(i % nx);
-    const int n = dir == 0 ? nx : ny, j = dir == 0 ? c : r;
-    const long long st = dir == 0 ? 1 : nx;
-    const double dj = in[i];
-    double nd = dj;
-    if (n >= 3 && dj > 0.0) {
-        const bool lw = j > 0 && in[i - st] > 0.0;
-        const bool rw = j < n - 1 && in[i + st] > 0.0;
-        const bool viol = (lw && in[i - st] > a2 * dj) || (rw && in[i + st] > a2 * dj);
-        if (viol) {
-            if (lw && rw) {
-                const double s = sqrt(in[i - st]) + sqrt(in[i + st]);
-                nd = s * s / 4.0;
-            } else {
-                nd = (lw ? in[i - st] : in[i + st]) / a2;
-            }
-        }
-    }
-    out[i] = nd;
-    if (nd != dj) *changed = 1;
+    if (i < (long long)nx * ny) filter_pass_node(in, out, i, nx, ny, dir, a2, changed);
 }
 
 __global__ void k_depth_to_f32(const double* d64, float* d32, int nx, int ny, int pitch) {

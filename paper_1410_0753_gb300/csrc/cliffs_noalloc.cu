@@ -23,35 +23,25 @@ std::mutex g_mu;
 constexpr int MAX_DEVICES = 64;
 double* g_dev_ptr[MAX_DEVICES] = {nullptr};
 
+// The same per-node code as cliffs_set_bathy's filter kernels (internal.h).
 __global__ void k_na_minraise(double* d, long long n, double min_depth) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n && d[i] > 0.0 && d[i] < min_depth) d[i] = min_depth;
+    if (i < n) cliffs::filter_minraise_node(d, i, min_depth);
 }
 
 __global__ void k_na_pass(const double* in, double* out, int nx, int ny, int dir, double a2,
                           int* changed) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)nx * ny) return;
-    const int r = (int)(i / nx), c = (int)(i % nx);
-    const int n = dir == 0 ? nx : ny, j = dir == 0 ? c : r;
-    const long long st = dir == 0 ? 1 : nx;
-    const double dj = in[i];
-    double nd = dj;
-    if (n >= 3 && dj > 0.0) {
-        const bool lw = j > 0 && in[i - st] > 0.0;
-        const bool rw = j < n - 1 && in[i + st] > 0.0;
-        const bool viol = (lw && in[i - st] > a2 * dj) || (rw && in[i + st] > a2 * dj);
-        if (viol) {
-            if (lw && rw) {
-                const double s = sqrt(in[i - st]) + sqrt(in[i + st]);
-                nd = s * s / 4.0;
-            } else {
-                nd = (lw ? in[i - st] : in[i + st]) / a2;
-            }
-        }
-    }
-    out[i] = nd;
-    if (nd != dj) *changed = 1;
+    if (i < (long long)nx * ny) cliffs::filter_pass_node(in, out, i, nx, ny, dir, a2, changed);
+}
+
+// Memory type of a pointer as the runtime sees it (cudaMemoryTypeUnregistered for plain
+// host memory it does not know).
+cudaError_t mem_type(const void* p, cudaMemoryType* t) {
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    *t = at.type;
+    return e;
 }
 
 int fail(int code, const char* what, cudaError_t e) {
@@ -87,10 +77,27 @@ int cliffs_depth_filter_noalloc(const double* depth, double* out, int32_t nx, in
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(CLIFFS_ERR_CUDA, "cudaGetDevice", e);
+    // out is written by kernels: it must be device (or managed) memory, and the input may
+    // share it only as a whole (in place)
+    cudaMemoryType to, ti;
+    e = mem_type(out, &to);
+    if (e != cudaSuccess) return fail(CLIFFS_ERR_CUDA, "cudaPointerGetAttributes(out)", e);
+    if (to != cudaMemoryTypeDevice && to != cudaMemoryTypeManaged)
+        return reject("out must be device memory (cudaMalloc'd or managed)");
+    e = mem_type(depth, &ti);
+    if (e != cudaSuccess) return fail(CLIFFS_ERR_CUDA, "cudaPointerGetAttributes(depth)", e);
+    if (out != depth && (ti == cudaMemoryTypeDevice || ti == cudaMemoryTypeManaged)) {
+        const char* a = reinterpret_cast<const char*>(depth);
+        const char* b = reinterpret_cast<const char*>(out);
+        const size_t bytes = sizeof(double) * (size_t)N;
+        if (a < b + bytes && b < a + bytes) return reject("depth and out overlap without being the same array");
+    }
     if (dev < 0 || dev >= MAX_DEVICES) return reject("device index beyond the 64 this entry point tracks");
     double* base;
     {
-        // set-up once per device, with that device current: the array's device address
+        // set-up once per device, with that device current: the array's device address. The
+        // address is kept for the life of the process; it does not survive cudaDeviceReset
+        // (the module is loaded again afterwards), so do not call this entry point after one.
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_dev_ptr[dev]) {
             void* p = nullptr;

@@ -47,6 +47,40 @@ constexpr int MET_PAD = 8;
 constexpr int TMA_BOX_COLS = 64;   // columns of one TMA box (a warp's window)
 constexpr int TMA_BOX_ROWS = 2;    // rows of one TMA box (one ring slot)
 
+// Depth-jump filter (section "Numerical stability", eqs. (dstab), (newdw), (newdc)), one
+// node per thread; shared by cliffs_set_bathy and cliffs_depth_filter_noalloc so that both
+// launch the same code. Wet nodes (0 < d < min_depth) are first raised to min_depth.
+__device__ __forceinline__ void filter_minraise_node(double* d, long long i, double min_depth) {
+    if (d[i] > 0.0 && d[i] < min_depth) d[i] = min_depth;
+}
+// One Jacobi pass along rows (dir 0) or columns (dir 1) at node i of an nx x ny grid: where a
+// wet neighbour is deeper than alpha^2 d_j, d_j becomes the square of the mean square root of
+// its two neighbours (open water) or the coastal neighbour's depth over alpha^2; land
+// (d <= 0) and lines shorter than 3 nodes stay. Sets *changed when the node changed.
+__device__ __forceinline__ void filter_pass_node(const double* in, double* out, long long i, int nx, int ny,
+                                                 int dir, double a2, int* changed) {
+    const int r = (int)(i / nx), c = (int)(i % nx);
+    const int n = dir == 0 ? nx : ny, j = dir == 0 ? c : r;
+    const long long st = dir == 0 ? 1 : nx;
+    const double dj = in[i];
+    double nd = dj;
+    if (n >= 3 && dj > 0.0) {
+        const bool lw = j > 0 && in[i - st] > 0.0;
+        const bool rw = j < n - 1 && in[i + st] > 0.0;
+        const bool viol = (lw && in[i - st] > a2 * dj) || (rw && in[i + st] > a2 * dj);
+        if (viol) {
+            if (lw && rw) {
+                const double s = sqrt(in[i - st]) + sqrt(in[i + st]);
+                nd = s * s / 4.0;
+            } else {
+                nd = (lw ? in[i - st] : in[i + st]) / a2;
+            }
+        }
+    }
+    out[i] = nd;
+    if (nd != dj) *changed = 1;
+}
+
 // message returned by cliffs_last_error() on the calling thread (cliffs_api.cu)
 void set_last_error(const char* msg);
 

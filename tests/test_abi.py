@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1410_0753_gb300 as pk
@@ -126,3 +127,22 @@ def test_null_handles_are_argument_errors(built):
         assert rc == pk.ERR_ARG
     assert "null" in pk.cliffs_last_error()
     pk.lib().cliffs_destroy(None)                       # destroying nothing is a no-op
+
+
+def test_noalloc_filter_wrapper_refuses_bad_outputs_on_the_host(built):
+    """The allocation-free filter's binding refuses outputs it cannot write (host memory, a
+    CPU tensor, the wrong type or size) before calling into the library; the C entry point's
+    own NULL and size checks run without touching a GPU."""
+    import torch
+    d = np.full((6, 5), 10.0)
+    for out in (np.zeros((6, 5)), torch.zeros((6, 5), dtype=torch.float64),
+                torch.zeros((6, 5), dtype=torch.float32)):
+        with pytest.raises(pk.CliffsError) as e:
+            pk.cliffs_depth_filter_noalloc(d, out, 5, 6)
+        assert e.value.code == pk.ERR_ARG and "CUDA float64" in str(e.value)
+    L = pk.lib()
+    assert L.cliffs_depth_filter_noalloc(None, None, 5, 6, 2.0, 0.1, None, None) == pk.ERR_ARG
+    buf = (C.c_double * 30)()
+    assert L.cliffs_depth_filter_noalloc(buf, buf, 0, 6, 2.0, 0.1, None, None) == pk.ERR_ARG
+    assert L.cliffs_depth_filter_noalloc(buf, buf, 2048, 2048, 2.0, 0.1, None, None) == pk.ERR_ARG
+    assert "at most 1048576" in pk.cliffs_last_error()

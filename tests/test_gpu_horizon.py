@@ -67,15 +67,6 @@ def _check(name, w, g, o, d64, amp):
     assert np.all(dm[wet_ever] <= 1e-4 * amp + 1e-2 * jm[wet_ever])
 
 
-def test_inversion_1024_full_horizon():
-    w = workloads.inversion_1024()
-    d64 = P.oracle_depth(w)
-    g = P.gpu_run(w, w.steps)
-    o = P.oracle_run(w, w.steps, P.f32(d64))
-    _check("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max())
-    g["grid"].close()
-
-
 EPS = 1e-5
 
 

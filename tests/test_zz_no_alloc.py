@@ -1,14 +1,15 @@
 """The allocation-free depth filter, cliffs_depth_filter_noalloc, on the GPU.
 
-Some callers of this library cannot allocate device memory at the moment they call it: code
-running while a CUDA stream is being captured (cudaMalloc and cudaFree are not allowed
-then), hosts whose own pool owns the whole device and forbids hidden allocations, and callers
-that cannot afford the device-wide synchronisation of cudaFree. For them the library filters
-bathymetry into memory the caller owns, using a fixed static scratch array instead of
+Some callers of this library cannot allocate device memory when they call it: applications
+whose own memory pool owns the whole device and forbids allocations behind its back, and
+callers that cannot afford the device-wide synchronisation of cudaFree. For them the library
+filters bathymetry into memory the caller owns, using a fixed static scratch array instead of
 allocating. Its result must equal the allocating path's (cliffs_set_bathy) bit for bit, the
 tolerance every depth-filter test here uses, on consecutive calls that reuse the one scratch
-array.
+array. Arguments it cannot use are refused before anything is launched.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -69,3 +70,35 @@ def test_noalloc_filter_rejects_grids_beyond_its_scratch():
     with pytest.raises(CliffsError) as e:
         pk.cliffs_depth_filter_noalloc(dev, dev, n, n, 2.0, 0.1)
     assert e.value.code == ERR_ARG and "at most 1048576" in str(e.value)
+
+
+def test_noalloc_filter_refuses_unusable_outputs_before_launching():
+    """The C entry point itself refuses a host output and partly overlapping arrays (checked
+    with the runtime's pointer attributes, before any launch); the Python wrapper refuses
+    outputs of the wrong kind, type or size, and an in-place call on a converted copy."""
+    import torch
+    _build.build()
+    d = spiky(13, 40, 50)
+    ny, nx = d.shape
+    L = pk.lib()
+    host_out = np.zeros_like(d)
+    rc = L.cliffs_depth_filter_noalloc(C.c_void_p(d.ctypes.data), C.c_void_p(host_out.ctypes.data), nx, ny,
+                                       2.0, 0.1, None, None)
+    assert rc == ERR_ARG and "device memory" in pk.cliffs_last_error()
+    assert np.all(host_out == 0.0)
+    buf = torch.zeros(2 * d.size, dtype=torch.float64, device="cuda")
+    rc = L.cliffs_depth_filter_noalloc(C.c_void_p(buf.data_ptr()), C.c_void_p(buf.data_ptr() + 8 * 100), nx, ny,
+                                       2.0, 0.1, None, None)
+    assert rc == ERR_ARG and "overlap" in pk.cliffs_last_error()
+    assert torch.count_nonzero(buf).item() == 0
+    bad_outs = [host_out, torch.zeros(d.shape, dtype=torch.float32, device="cuda"),
+                torch.zeros((ny, nx + 1), dtype=torch.float64, device="cuda"),
+                torch.zeros((nx, ny), dtype=torch.float64, device="cuda").t(),
+                torch.zeros(d.shape, dtype=torch.float64)]
+    for out in bad_outs:
+        with pytest.raises(CliffsError) as e:
+            pk.cliffs_depth_filter_noalloc(d, out, nx, ny)
+        assert e.value.code == ERR_ARG
+    f32 = torch.from_numpy(d.astype(np.float32)).cuda()
+    with pytest.raises(CliffsError):
+        pk.cliffs_depth_filter_noalloc(f32, f32, nx, ny)
