@@ -137,8 +137,8 @@ __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, s
         if (eA || eB || sA || sB) {
             if (eA) em.x = E.x;
             if (eB) em.y = E.y;
-            if (sA) sm.x = fmaxf(sm.x, s2.x * rsqrt_approx(fmaxf(s2.x, 1e-30f)));
-            if (sB) sm.y = fmaxf(sm.y, s2.y * rsqrt_approx(fmaxf(s2.y, 1e-30f)));
+            if (sA) sm.x = fmaxf(sm.x, sqrt_pos(s2.x));
+            if (sB) sm.y = fmaxf(sm.y, sqrt_pos(s2.y));
             if (vb) {
                 *reinterpret_cast<float2*>(O.emax + o) = em;
                 *reinterpret_cast<float2*>(O.smax + o) = sm;

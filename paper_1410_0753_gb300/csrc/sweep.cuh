@@ -53,6 +53,8 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, v2(-1.f), a); }
 
+#ifndef CLIFFS_IEEE_MATH
+// Hardware approximations (MUFU): one instruction each.
 __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -71,15 +73,35 @@ __device__ __forceinline__ float pow_m43(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
     return r;
 }
+// sqrt(x) for x >= 0 (x = 0 gives 0 through the 1e-30 floor)
+__device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrt_approx(fmaxf(x, 1e-30f)); }
+__device__ __forceinline__ float div_pos(float a, float b) { return a * rcp_approx(b); }
+#else
+// Build option CLIFFS_IEEE_MATH: correctly rounded square root, reciprocal and quotient
+// (IEEE round-to-nearest) in place of the hardware approximations.
+__device__ __forceinline__ float rsqrt_approx(float x) { return __frsqrt_rn(x); }
+__device__ __forceinline__ float rcp_approx(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float pow_m43(float x) { return __frcp_rn(__fmul_rn(x, cbrtf(x))); }
+__device__ __forceinline__ float sqrt_pos(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ float div_pos(float a, float b) { return __fdiv_rn(a, b); }
+#endif
 
 // c = sqrt(g h) of both nodes (h > 0 for wet nodes; dry nodes give NaN and are not used)
 __device__ __forceinline__ float2 wave_speed2(float2 h) {
     const float2 gh = mul2(v2(GRAV), h);
+#ifndef CLIFFS_IEEE_MATH
     return mul2(gh, make_float2(rsqrt_approx(gh.x), rsqrt_approx(gh.y)));
+#else
+    return make_float2(__fsqrt_rn(gh.x), __fsqrt_rn(gh.y));
+#endif
 }
 __device__ __forceinline__ float wave_speed(float h) {
     const float gh = GRAV * h;
+#ifndef CLIFFS_IEEE_MATH
     return gh * rsqrt_approx(gh);
+#else
+    return __fsqrt_rn(gh);
+#endif
 }
 
 __device__ __forceinline__ bool wet_mark(float eta, float d, const SweepConst& K) {
@@ -96,7 +118,11 @@ __device__ __forceinline__ Flux2 iface2(float2 ea, float2 wa, float2 ta, float2 
     const float2 deta = sub2(eb, ea);
     const float2 sc = add2(cb, ca);
     const float2 num = mul2(v2(GRAV), add2(deta, sub2(db, da)));
+#ifndef CLIFFS_IEEE_MATH
     const float2 dc = mul2(num, make_float2(rcp_approx(sc.x), rcp_approx(sc.y)));
+#else
+    const float2 dc = make_float2(__fdiv_rn(num.x, sc.x), __fdiv_rn(num.y, sc.y));
+#endif
     const float2 sw = add2(wb, wa);
     const float2 hdw = mul2(v2(0.5f), sub2(wb, wa));
     const float2 y = mul2(sw, dc);
@@ -131,7 +157,7 @@ __device__ __forceinline__ void open_ghost(float e, float w, float d, float c, b
                                            float& eg, float& wg, float& cg) {
     const bool deep = d > 0.f;
     const float c0 = deep ? wave_speed(d) : 0.f;
-    const float delta = deep ? GRAV * e * rcp_approx(c + c0) : c;
+    const float delta = deep ? div_pos(GRAV * e, c + c0) : c;
     const float s = right ? 1.f : -1.f;
     wg = fmaf(0.5f, w, s * delta);
     float gam = fmaf(s * 0.25f, w, -0.5f * delta);           // c_g - c
@@ -176,8 +202,7 @@ __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float
     if (FRIC) {
         const float2 h = add2(e, d);
         const float2 s2 = fma2(w, w, mul2(t, t));
-        const float2 s = mul2(s2, make_float2(rsqrt_approx(fmaxf(s2.x, 1e-30f)),
-                                              rsqrt_approx(fmaxf(s2.y, 1e-30f))));
+        const float2 s = make_float2(sqrt_pos(s2.x), sqrt_pos(s2.y));
         float2 adt = mul2(mul2(mul2(v2(K.dt_gn2), w), s), make_float2(pow_m43(h.x), pow_m43(h.y)));
         if (fabsf(adt.x) > fabsf(w.x)) adt.x = w.x;
         if (fabsf(adt.y) > fabsf(w.y)) adt.y = w.y;
