@@ -1,5 +1,5 @@
 """The bench's reference arm on the CPU: it times the FP64 oracle on the host cores and
-prints one JSON line with the same metric, unit and workload naming as the CUDA arm. Under
+prints one JSON line with the same metric, unit and config (workload, cells) as the CUDA arm. Under
 a multi-rank launch rank 0 alone runs it; the other ranks exit 0 without work."""
 import json
 import os
@@ -26,7 +26,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
     assert d["dtype"] == "f64" and d["data"] == "synthetic"
-    assert d["config"]["workload"] == "spherical_coast_256x192"
+    import workloads
+    # the CUDA arm prints the same config dict for the same workload
+    assert d["config"] == bench.bench_config(workloads.shelf_islands(256, 192), 1)
+    assert d["config"]["workload"] == "shelf_islands_256x192" and d["config"]["cells"] == 256 * 192
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,

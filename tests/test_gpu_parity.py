@@ -452,6 +452,17 @@ def test_full_size_shelf_islands_8192_windows():
     assert worst <= 1e-4
 
 
+def test_full_size_shelf_islands_8192_windows_300_steps():
+    """The stress grid in the bench's launch configuration over 300 steps: blocks on both
+    fronts of the split N-wave, each against an oracle window holding its whole domain of
+    dependence (912 nodes each way)."""
+    w = workloads.shelf_islands(8192, 8192, steps=300)
+    c = int(round(40.0e3 / 50.0))
+    shift = int(np.sqrt(9.81 * 200.0) * w.dt * 300 / 50.0)
+    worst, _ = window_check(w, 300, [(4096, c + shift), (2000, c - shift)], "shelf_8192_windows_300")
+    assert worst <= 1e-4
+
+
 def test_full_size_shelf_islands_8192_island_windows():
     w = workloads.shelf_islands(8192, 8192, steps=60)
     land = w.depth < 0
