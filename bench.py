@@ -58,8 +58,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "step_kernels.cuh", "cliffs_step.cu", "internal.h", "sweep_wide.cuh",
-              "cliffs_step_wide.cu"):
+    for f in ("sweep.cuh", "step_kernels.cuh", "cliffs_step.cu", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1410_0753_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -576,7 +575,6 @@ def run_cuda(args, world, rank, local):
     stream = torch.cuda.current_stream()
     g = CliffsGrid.from_workload(w, stream=stream.cuda_stream, gauges=[], nests=[])
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
-    g.set_step_kernel(args.step_kernel)
     eta0 = w.eta0.astype(np.float32)
     g.set_initial(eta0)
     dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
@@ -613,8 +611,7 @@ def run_cuda(args, world, rank, local):
     value = world * w.cells * args.steps / (ms_max / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL * w.cells / (ms / args.steps / 1e3) / 1e9
-    prof, tnote = profiled(("k_step_wide" if args.step_kernel == 0 else "k_step_fused") + "_shelf_8192",
-                           rows_per_warp)
+    prof, tnote = profiled("k_step_fused_shelf_8192", rows_per_warp)
     traffic = prof.get("dram_bytes_per_launch") if prof else None
 
     # end to end through the public API over the workload's horizon: eta0 from pinned host
@@ -662,11 +659,9 @@ def run_cuda(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": bench_config(w, world),
             "rows_per_warp": rows_per_warp,
-            "step_kernel": "k_step_wide" if args.step_kernel == 0 else "k_step_fused",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": "k_step_wide" if args.step_kernel == 0 else "k_step_fused",
-                         "bytes_per_cell": BYTES_PER_CELL,
+                         "kernel": "k_step_fused", "bytes_per_cell": BYTES_PER_CELL,
                          "peak_kind": peak_kind,
                          "issue": issue_roof(prof, w.cells, value / world,
                                              (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz"), sms)},
@@ -704,8 +699,6 @@ def main():
                     help="batched form on B scenarios of DMIN..DMAX steps instead of 256 of 500..4000")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fix the fused step's tile instead of autotuning it")
-    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1],
-                    help="0: the wide step kernel (default), 1: the two-node step kernel")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.forms_only:

@@ -350,15 +350,6 @@ int cliffs_diagnostics(cliffs_grid* g, int scenario, double* out);
  * synchronises. enable < 0 resets the totals. Errors: ERR_ARG (no grid); ERR_CUDA. */
 int cliffs_kernel_time(cliffs_grid* g, int enable, double* ms, int64_t* launches);
 
-/* Which fused step kernel takes a 2D grid's steps (no counterpart in the paper; both compute
- * the split step of section "Numerics" and give the same bits). kind 0 (the default): the
- * wide kernel (four nodes per lane, 120 output columns per warp) for the steps it covers -
- * eq. (solver2), reflecting outer edges, swept x first - and the two-node kernel for the
- * rest; kind 1: the two-node kernel for every step. The tile shape is kept; call
- * cliffs_autotune again to re-tune it for the other kernel. Errors: ERR_ARG (no grid, kind
- * not 0 or 1). */
-int cliffs_set_step_kernel(cliffs_grid* g, int32_t kind);
-
 /* The depth-jump filter of cliffs_set_bathy for callers that cannot allocate device
  * memory. The paper has no counterpart of this entry point. It serves callers that must not
  * call cudaMalloc or cudaFree: applications whose own memory pool owns the whole device and

@@ -31,7 +31,7 @@ __all__ = [
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
     "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "cliffs_diagnostics",
-    "cliffs_set_step_kernel", "EXPORTED",
+    "EXPORTED",
 ]
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -48,7 +48,6 @@ EXPORTED = [
     "cliffs_adjoint_record", "cliffs_adjoint_recorded", "cliffs_state_ptrs", "cliffs_adjoint_velocity",
     "cliffs_adjoint_scenario", "cliffs_set_rows_per_warp", "cliffs_adjoint_records",
     "cliffs_adjoint_recorded_records", "cliffs_adjoint_recorded_scenario", "cliffs_diagnostics",
-    "cliffs_set_step_kernel",
 ]
 
 
@@ -97,7 +96,6 @@ def lib():
             "cliffs_adjoint_n": ([vp, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_scenario": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_set_rows_per_warp": ([vp, C.c_int32], C.c_int),
-            "cliffs_set_step_kernel": ([vp, C.c_int32], C.c_int),
             "cliffs_adjoint_records": ([vp, C.c_int32, C.c_int64, C.c_int32, vp, vp], C.c_int),
             "cliffs_adjoint_recorded_records": ([vp, vp, vp], C.c_int),
             "cliffs_adjoint_recorded_scenario": ([vp, C.c_int32, C.c_int32, vp, vp], C.c_int),
@@ -374,10 +372,6 @@ def cliffs_set_rows_per_warp(g, rows):
     _check(lib().cliffs_set_rows_per_warp(g, int(rows)))
 
 
-def cliffs_set_step_kernel(g, kind):
-    _check(lib().cliffs_set_step_kernel(g, int(kind)))
-
-
 def cliffs_inject_wait_expiry(g, cycles):
     _check(lib().cliffs_inject_wait_expiry(g, int(cycles)))
 
@@ -513,10 +507,6 @@ class CliffsGrid:
 
     def set_rows_per_warp(self, rows):
         cliffs_set_rows_per_warp(self.h, rows)
-
-    def set_step_kernel(self, kind):
-        """0: the wide step kernel where it applies (default); 1: the two-node kernel only."""
-        cliffs_set_step_kernel(self.h, kind)
 
     def autotune(self, trials=3):
         return cliffs_autotune(self.h, trials)

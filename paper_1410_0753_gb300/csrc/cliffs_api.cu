@@ -22,7 +22,6 @@
 #include "internal.h"
 #include "adjoint.h"
 #include "sweep.cuh"
-#include "sweep_wide.cuh"
 
 using namespace cliffs;
 
@@ -307,18 +306,6 @@ struct cliffs_grid {
     std::vector<unsigned char> hard;         // per strip: dry nodes in its window, or an edge
     std::vector<int4> items;                 // fused kernel work items (strip, r0, r1, 0)
     int4* items_dev = nullptr;
-    // the wide fused step (k_step_wide, 120 output columns per warp) takes the steps swept x
-    // first under eq. (solver2) with reflecting edges: its own strips, work items, sample
-    // lists and TMA descriptors (128-column boxes); the same rows per warp S
-    bool wide = false;                       // the wide kernel takes the steps it can
-    bool wide_off = false;                   // cliffs_set_step_kernel(g, 1): two-node kernel only
-    int nstrips_w = 0;
-    std::vector<unsigned char> hard_w;
-    std::vector<int4> items_w;
-    int4* items_w_dev = nullptr;
-    int* samp_ptr_w = nullptr;
-    int4* samp_w = nullptr;
-    StepMaps maps_w[2];
     // timing
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -340,7 +327,6 @@ struct cliffs_grid {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int pblocks = 0;
-    int pblocks_w = 0;                       // the same for the wide warps (k_batch_wide)
     // adjoint work space: K recomputed states and the checkpoints (row-major, 3 planes
     // each), the transposed x-swept state, adjoint and depth (7 planes of [nx][tpitch]),
     // the row-major intermediate adjoint (3 planes), gauge nodes and seeds
@@ -453,44 +439,6 @@ int build_samples(cliffs_grid* g) {
     return CLIFFS_OK;
 }
 
-// per-warp sample lists of the wide step (kind 0 grids): a warp owns output columns
-// [120 strip, 120 strip + 120) of its item's rows
-int build_samples_w(cliffs_grid* g) {
-    const long long nw = (long long)g->items_w.size();
-    std::vector<std::vector<int>> seg_start(g->nstrips_w), seg_item(g->nstrips_w);
-    for (size_t i = 0; i < g->items_w.size(); ++i) {
-        seg_start[g->items_w[i].x].push_back(g->items_w[i].y);
-        seg_item[g->items_w[i].x].push_back((int)i);
-    }
-    std::vector<std::vector<int4>> per(nw);
-    for (const int4& it : g->samples) {
-        const int st = it.y / WOUT;
-        const auto& v = seg_start[st];
-        const int k = (int)(std::upper_bound(v.begin(), v.end(), it.x) - v.begin()) - 1;
-        per[seg_item[st][k]].push_back(it);
-    }
-    std::vector<int> ptr(nw + 1, 0);
-    std::vector<int4> flat;
-    for (long long w = 0; w < nw; ++w) {
-        std::stable_sort(per[w].begin(), per[w].end(),
-                         [](const int4& a, const int4& b) { return a.x < b.x; });
-        ptr[w] = (int)flat.size();
-        flat.insert(flat.end(), per[w].begin(), per[w].end());
-    }
-    ptr[nw] = (int)flat.size();
-    if (g->samp_ptr_w) CK(cudaFree(g->samp_ptr_w));
-    if (g->samp_w) CK(cudaFree(g->samp_w));
-    g->samp_ptr_w = nullptr;
-    g->samp_w = nullptr;
-    CK(cudaMalloc(&g->samp_ptr_w, sizeof(int) * (nw + 1)));
-    CK(cudaMemcpy(g->samp_ptr_w, ptr.data(), sizeof(int) * (nw + 1), cudaMemcpyHostToDevice));
-    if (!flat.empty()) {
-        CK(cudaMalloc(&g->samp_w, sizeof(int4) * flat.size()));
-        CK(cudaMemcpy(g->samp_w, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice));
-    }
-    return CLIFFS_OK;
-}
-
 // Work items of the fused kernel: every strip is cut into segments of S rows, or S_hard
 // rows in strips whose window holds dry nodes or reaches past the domain edge (their warps
 // take the wet/dry correction paths on every row, so shorter segments even out the time
@@ -511,35 +459,18 @@ int set_rows_per_warp(cliffs_grid* g, int S, int S_hard) {
         g->items_dev = nullptr;
         CK(cudaMalloc(&g->items_dev, sizeof(int4) * g->items.size()));
         CK(cudaMemcpy(g->items_dev, g->items.data(), sizeof(int4) * g->items.size(), cudaMemcpyHostToDevice));
-        // the same cut for the wide kernel's strips
-        g->items_w.clear();
-        for (int st = 0; st < g->nstrips_w; ++st) {
-            const int h = g->hard_w.empty() ? 0 : g->hard_w[st];
-            const int seg = h ? S_hard : S;
-            for (int r0 = 0; r0 < g->ny; r0 += seg)
-                g->items_w.push_back(make_int4(st, r0, std::min(r0 + seg, g->ny), 0));
-        }
-        cudaFree(g->items_w_dev);
-        g->items_w_dev = nullptr;
-        CK(cudaMalloc(&g->items_w_dev, sizeof(int4) * g->items_w.size()));
-        CK(cudaMemcpy(g->items_w_dev, g->items_w.data(), sizeof(int4) * g->items_w.size(), cudaMemcpyHostToDevice));
-        const int rc = build_samples_w(g);
-        if (rc) return rc;
     }
     return build_samples(g);
 }
 
 int hard_rows(int S) { return std::max(8, (S * 3 / 4) & ~1); }
 
-// warps of one fused launch with S rows per warp, and the warps resident at once (of the
-// wide kernel when it takes the grid's steps)
+// warps of one fused launch with S rows per warp, and the warps resident at once
 long long fused_warps(const cliffs_grid* g, int S) {
-    const int ns = g->wide ? g->nstrips_w : g->nstrips;
-    const std::vector<unsigned char>& hard = g->wide ? g->hard_w : g->hard;
     int nhard = 0;
-    for (int st = 0; st < ns; ++st) nhard += hard.empty() ? 0 : hard[st];
+    for (int st = 0; st < g->nstrips; ++st) nhard += g->hard.empty() ? 0 : g->hard[st];
     const int Sh = hard_rows(S);
-    return ((long long)(ns - nhard) * ((g->ny + S - 1) / S) +
+    return ((long long)(g->nstrips - nhard) * ((g->ny + S - 1) / S) +
             (long long)nhard * ((g->ny + Sh - 1) / Sh)) * g->B;
 }
 
@@ -547,10 +478,8 @@ long long resident_warps(const cliffs_grid* g) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const bool sph = g->cfg.coords != 1;
-    const int per = g->wide ? wide_blocks_per_sm(sph) * wide_warps_per_block()
-                            : fused_blocks_per_sm(sph) * fused_warps_per_block();
-    return (long long)std::max(1, nsm) * std::max(1, per);
+    return (long long)std::max(1, nsm) * std::max(1, fused_blocks_per_sm(g->cfg.coords != 1)) *
+           fused_warps_per_block();
 }
 
 // the smallest even S whose launch fits in `waves` waves of resident warps (0 if none does)
@@ -575,8 +504,6 @@ int choose_geometry(cliffs_grid* g) {
     } else {
         g->kind = 0;
         g->nstrips = (g->nx + XOUT - 1) / XOUT;
-        g->nstrips_w = (g->nx + WOUT - 1) / WOUT;
-        g->wide = g->cfg.solver != 1 && g->cfg.open_edges == 0 && !g->wide_off;
         // rows per warp S: each warp walks S + 6 rows (3-row halo above and below), so the
         // cost of one wave of warps is ~ S + 6; pick the even S minimising waves * (S + 6)
         // with the resident warps the occupancy calculator reports (ties go to the larger S)
@@ -648,15 +575,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// a [batch][ny][pitch] FP32 tensor (batch 1 for the depth) read in box_cols x 2 x 1 boxes
-// (64 columns for k_step_fused, 128 for k_step_wide); out-of-range boxes fill with zeros
-int make_map(CUtensorMap* m, const float* base, int rank, int pitch, int ny, int batch,
-             int box_cols = TMA_BOX_COLS) {
+// a [batch][ny][pitch] FP32 tensor (batch 1 for the depth) read in 64 x 2 x 1 boxes;
+// out-of-range boxes fill with zeros
+int make_map(CUtensorMap* m, const float* base, int rank, int pitch, int ny, int batch) {
     auto fn = encode_fn();
     if (!fn) return set_err(CLIFFS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)ny, (cuuint64_t)batch};
     cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)TMA_BOX_ROWS, 1};
+    cuuint32_t box[3] = {(cuuint32_t)TMA_BOX_COLS, (cuuint32_t)TMA_BOX_ROWS, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -674,14 +600,6 @@ int make_maps(cliffs_grid* g) {
         if (!rc) rc = make_map(&M.d, g->d32, 3, g->pitch, g->ny, 1);
         if (!rc) rc = make_map(&M.em, g->emax, 3, g->pitch, g->ny, g->B);
         if (!rc) rc = make_map(&M.sm, g->smax, 3, g->pitch, g->ny, g->B);
-        if (rc) return rc;
-        StepMaps& W = g->maps_w[k];
-        rc = make_map(&W.e, g->eta[k], 3, g->pitch, g->ny, g->B, WWIN);
-        if (!rc) rc = make_map(&W.u, g->u[k], 3, g->pitch, g->ny, g->B, WWIN);
-        if (!rc) rc = make_map(&W.v, g->v[k], 3, g->pitch, g->ny, g->B, WWIN);
-        if (!rc) rc = make_map(&W.d, g->d32, 3, g->pitch, g->ny, 1, WWIN);
-        if (!rc) rc = make_map(&W.em, g->emax, 3, g->pitch, g->ny, g->B, WWIN);
-        if (!rc) rc = make_map(&W.sm, g->smax, 3, g->pitch, g->ny, g->B, WWIN);
         if (rc) return rc;
     }
     return CLIFFS_OK;
@@ -711,15 +629,6 @@ void fill_step_args(cliffs_grid* g, StepArgs& a, int in, int out) {
     a.yfirst = 0;
     a.inv_dt2_s1 = g->cfg.solver == 1 ? (float)(1.0 / (g->cfg.dt * g->cfg.dt)) : 0.f;
     a.open_edges = g->cfg.open_edges;
-}
-
-// the wide kernel's work items and sample lists in place of the two-node kernel's
-void wide_args(const cliffs_grid* g, StepArgs& a) {
-    a.items = g->items_w_dev;
-    a.nitems = (int)g->items_w.size();
-    a.samp_ptr = g->samp_ptr_w;
-    a.samp = g->samp_w;
-    a.nstrips = g->nstrips_w;
 }
 
 // dst[3][n] = (a, b, c): the three state planes into one checkpoint in one launch (n a
@@ -824,7 +733,6 @@ void free_grid(cliffs_grid* g) {
     cudaFree(g->xa); cudaFree(g->xb); cudaFree(g->xk); cudaFree(g->xrow); cudaFree(g->ymet);
     cudaFree(g->err); cudaFree(g->limit); cudaFree(g->items_d); cudaFree(g->items_dev);
     cudaFree(g->samp_ptr); cudaFree(g->samp); cudaFree(g->grec); cudaFree(g->nrec);
-    cudaFree(g->items_w_dev); cudaFree(g->samp_ptr_w); cudaFree(g->samp_w);
     cudaFree(g->pt_slot); cudaFree(g->pt_w); cudaFree(g->tmp); cudaFree(g->ured);
     cudaFree(g->order_d); cudaFree(g->nact_d); cudaFree(g->ctl_d);
     if (g->ctl_h) cudaFreeHost(g->ctl_h);
@@ -1102,15 +1010,6 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
                 for (int c = c0; c < c1; ++c)
                     if (hd[(size_t)j * nx + c] < g->cfg.h_min) { g->hard[st] = 1; break; }
         }
-        const int nstrips_w = (nx + WOUT - 1) / WOUT;        // the same for the wide windows
-        g->hard_w.assign(nstrips_w, 0);
-        for (int st = 0; st < nstrips_w; ++st) {
-            const int c0 = st * WOUT - 4, c1 = c0 + WWIN;
-            if (c0 < 0 || c1 > nx) { g->hard_w[st] = 1; continue; }
-            for (int j = 0; j < ny && !g->hard_w[st]; ++j)
-                for (int c = c0; c < c1; ++c)
-                    if (hd[(size_t)j * nx + c] < g->cfg.h_min) { g->hard_w[st] = 1; break; }
-        }
     }
     int rc = choose_geometry(g);
     if (rc) return rc;
@@ -1377,10 +1276,7 @@ int cliffs_step_n(cliffs_grid* g, int64_t n) {
             CK(cudaEventRecord(e0, s));
         }
         cudaError_t le;
-        if (g->kind == 0 && g->wide && !a.yfirst) {
-            wide_args(g, a);
-            le = launch_step_wide(a, g->maps_w[in], g->B, s);
-        } else if (g->kind == 0) le = launch_step_fused(a, g->maps[in], g->B, s);
+        if (g->kind == 0) le = launch_step_fused(a, g->maps[in], g->B, s);
         else if (g->kind == 1) le = launch_xsweep(a, g->B, s);
         else le = launch_ysweep(a, g->B, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(le));
@@ -1435,15 +1331,11 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         g->pblocks = sms * std::max(1, batch_blocks_per_sm(g->cfg.coords != 1));
-        g->pblocks_w = sms * std::max(1, batch_wide_blocks_per_sm(g->cfg.coords != 1));
     }
-    // the wide warps take a run swept x first under eq. (solver2) with reflecting edges
-    const bool wide = g->wide && !g->cfg.alternate;
     // launch arguments; all padding zeroed so that they compare byte for byte
     struct Key { StepArgs a; BatchArgs b; } k;
     std::memset(&k, 0, sizeof(k));
     fill_step_args(g, k.a, 0, 1);
-    if (wide) wide_args(g, k.a);
     k.a.eta_out = k.a.u_out = k.a.v_out = nullptr;
     k.a.eta_in = k.a.u_in = k.a.v_in = nullptr;
     k.a.limit = nullptr;
@@ -1500,13 +1392,12 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n) {
         // the graph: copy the control block in from its pinned host image, then the
         // cooperative launch
         StepMaps2 mm;
-        mm.m[0] = wide ? g->maps_w[0] : g->maps[0];
-        mm.m[1] = wide ? g->maps_w[1] : g->maps[1];
+        mm.m[0] = g->maps[0];
+        mm.m[1] = g->maps[1];
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t e1 = cudaMemcpyAsync(g->ctl_d, g->ctl_h, 4 * sizeof(long long), cudaMemcpyHostToDevice, g->cap);
-        cudaError_t e2 = e1 != cudaSuccess ? e1 : wide ? launch_batch_wide(k.a, mm, b, g->pblocks_w, g->cap)
-                                                      : launch_batch(k.a, mm, b, g->pblocks, g->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_batch(k.a, mm, b, g->pblocks, g->cap) : e1;
         cudaError_t e3 = cudaStreamEndCapture(g->cap, &graph);
         if (e2 != cudaSuccess || e3 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -1897,16 +1788,6 @@ int cliffs_set_rows_per_warp(cliffs_grid* g, int32_t rows) {
     return set_rows_per_warp(g, rows, hard_rows(rows));
 }
 
-int cliffs_set_step_kernel(cliffs_grid* g, int32_t kind) {
-    g_err[0] = 0;
-    if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
-    if (kind != 0 && kind != 1) return set_err(CLIFFS_ERR_ARG, "step kernel %d: 0 (automatic) or 1 (two-node)", kind);
-    g->wide_off = kind == 1;
-    if (!g->have_bathy || g->kind != 0) return CLIFFS_OK;
-    g->wide = g->cfg.solver != 1 && g->cfg.open_edges == 0 && !g->wide_off;
-    return CLIFFS_OK;
-}
-
 int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32_t* ncand) {
     g_err[0] = 0;
     if (!g) return set_err(CLIFFS_ERR_ARG, "null argument");
@@ -1955,13 +1836,11 @@ int cliffs_autotune(cliffs_grid* g, int trials, int32_t* cand, double* us, int32
         if (rc) break;
         a.S = g->S; a.nseg = g->nseg; a.samp_ptr = g->samp_ptr; a.samp = g->samp;
         a.items = g->items_dev; a.nitems = (int)g->items.size();
-        if (g->wide) wide_args(g, a);
         float tbest = 1e30f;
         for (int t = 0; t <= trials; ++t) {             // the first launch warms up
             cudaMemsetAsync(flush, t & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
-            cudaError_t le = g->wide ? launch_step_wide(a, g->maps_w[cur], g->B, s)
-                                     : launch_step_fused(a, g->maps[cur], g->B, s);
+            cudaError_t le = launch_step_fused(a, g->maps[cur], g->B, s);
             cudaEventRecord(e1, s);
             if (le != cudaSuccess) { rc = set_err(CLIFFS_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(le)); break; }
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_err(CLIFFS_ERR_CUDA, "autotune sync"); break; }

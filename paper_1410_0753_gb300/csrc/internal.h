@@ -153,13 +153,6 @@ __device__ __forceinline__ void bnd_apply(float* eta, float* u, float* v, int pi
 cudaError_t launch_batch(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(bool sph);
 cudaError_t launch_step_fused(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s);
-// the wide fused step (cliffs_step_wide.cu): x first, eq. (solver2), reflecting edges;
-// items of 120-column strips and maps of 128-column boxes
-cudaError_t launch_step_wide(const StepArgs& a, const StepMaps& m, int batch, cudaStream_t s);
-int wide_blocks_per_sm(bool sph);
-int wide_warps_per_block();
-cudaError_t launch_batch_wide(const StepArgs& a, const StepMaps2& mm, const BatchArgs& b, int blocks, cudaStream_t s);
-int batch_wide_blocks_per_sm(bool sph);
 int fused_blocks_per_sm(bool sph);
 int fused_warps_per_block();
 cudaError_t launch_xsweep(const StepArgs& a, int batch, cudaStream_t s);
