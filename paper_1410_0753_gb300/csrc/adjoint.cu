@@ -58,19 +58,18 @@ __device__ __forceinline__ AIface a_iface(const ANode& b, const ANode& a) {
     return f;
 }
 
-// Friction of eq. (solver2)'s reading: adt = dt g n^2 w sqrt(w^2 + t^2) h^(-4/3), clamped to
-// w when larger in magnitude (mode 2), else mode 1; mode 0 without friction.
-struct AFric { float adt, s, hm; int mode; };
+// Friction of reading 4 as the forward step computes it (fric_k2): adt = w k with
+// k = min(dt g n^2 sqrt(s2) h^(-4/3), 1); mode 2 when clamped (k = 1), else mode 1; mode 0
+// without friction.
+struct AFric { float adt, s2, k; int mode; };
 
 __device__ __forceinline__ AFric a_friction(const ANode& C, const SweepConst& K) {
     AFric F{0.f, 0.f, 0.f, 0};
     if (K.dt_gn2 > 0.f) {
-        const float s2 = fmaf(C.w, C.w, C.t * C.t);
-        F.s = s2 * rsqrt_approx(fmaxf(s2, 1e-30f));
-        F.hm = pow_m43(C.e + C.d);
-        F.adt = K.dt_gn2 * C.w * F.s * F.hm;
-        F.mode = 1;
-        if (fabsf(F.adt) > fabsf(C.w)) { F.adt = C.w; F.mode = 2; }
+        float ex;
+        F.k = fric_k(C.w, C.t, C.e + C.d, K.dt_gn2, F.s2, ex);
+        F.adt = C.w * F.k;
+        F.mode = ex >= 0.f ? 2 : 1;
     }
     return F;
 }
@@ -163,11 +162,12 @@ __device__ __forceinline__ void a_dstage_adj(const ANode& L, const ANode& C, con
     const float gadt = -(gdp + gdq);
     if (F.mode == 2) {
         wC += gadt;
-    } else if (F.mode == 1 && F.s > 0.f) {
-        const float G = gadt * K.dt_gn2 * F.hm, rs = rcp_approx(F.s);
-        wC += G * (F.s + C.w * C.w * rs);
-        tC += G * C.w * C.t * rs;
-        eC += G * C.w * F.s * (-4.f / 3.f) * rcp_approx(C.e + C.d);
+    } else if (F.mode == 1 && F.s2 > 1e-30f) {   // below, k < 1e-15: no friction to speak of
+        // adt = w k, k ~ sqrt(s2) h^(-4/3): dk/dw = k w / s2, dk/dt = k t / s2, dk/dh = -4/3 k / h
+        const float G = gadt * F.k, rs2 = rcp_approx(F.s2);
+        wC += G * (1.f + C.w * C.w * rs2);
+        tC += G * C.w * C.t * rs2;
+        eC += G * C.w * (-4.f / 3.f) * rcp_approx(C.e + C.d);
     }
     if (SRC) {
         const float gs = (gdp - gdq) * m.sdt;
@@ -260,16 +260,16 @@ __device__ __forceinline__ AIface2 a_iface2(const N2& b, const N2& a) {
     return f;
 }
 
-// unclamped-friction part of the adjoint for one node
-__device__ __forceinline__ void fric_adj1(float gadt, float w, float t, float e, float d, float s, float hm,
-                                          bool clamped, const SweepConst& K, float& wC, float& tC, float& eC) {
+// friction part of the adjoint for one node (adt = w k, see a_friction)
+__device__ __forceinline__ void fric_adj1(float gadt, float w, float t, float e, float d, float s2, float k,
+                                          bool clamped, float& wC, float& tC, float& eC) {
     if (clamped) {
         wC += gadt;
-    } else if (s > 0.f) {
-        const float G = gadt * K.dt_gn2 * hm, rs = rcp_approx(s);
-        wC += G * (s + w * w * rs);
-        tC += G * w * t * rs;
-        eC += G * w * s * (-4.f / 3.f) * rcp_approx(e + d);
+    } else if (s2 > 1e-30f) {                      // below, k < 1e-15: no friction to speak of
+        const float G = gadt * k, rs2 = rcp_approx(s2);
+        wC += G * (1.f + w * w * rs2);
+        tC += G * w * t * rs2;
+        eC += G * w * (-4.f / 3.f) * rcp_approx(e + d);
     }
 }
 
@@ -285,19 +285,15 @@ __device__ __forceinline__ void a_dstage_adj2(const N2& L, const N2& C, const N2
     const float2 dQp = sub2(QpR, QpL), dQq = sub2(QqR, QqL);
     float2 dp = fma2(mul2(lp, k2), dQp, mul2(nh, add2(QpL, QpR)));
     float2 dq = fma2(mul2(lq, k2), dQq, mul2(nh, add2(QqL, QqR)));
-    float2 s = v2(0.f), hm = v2(0.f);
+    float2 s2 = v2(0.f), kf = v2(0.f);
     bool clA = false, clB = false;
     const bool fric = K.dt_gn2 > 0.f;
     if (fric) {
-        const float2 s2 = fma2(C.w, C.w, mul2(C.t, C.t));
-        s = make_float2(s2.x * rsqrt_approx(fmaxf(s2.x, 1e-30f)), s2.y * rsqrt_approx(fmaxf(s2.y, 1e-30f)));
-        const float2 h = add2(C.e, C.d);
-        hm = make_float2(pow_m43(h.x), pow_m43(h.y));
-        float2 adt = mul2(mul2(mul2(v2(K.dt_gn2), C.w), s), hm);
-        clA = fabsf(adt.x) > fabsf(C.w.x);
-        clB = fabsf(adt.y) > fabsf(C.w.y);
-        if (clA) adt.x = C.w.x;
-        if (clB) adt.y = C.w.y;
+        float2 ex;
+        kf = fric_k2(C.w, C.t, add2(C.e, C.d), K.dt_gn2, s2, ex);
+        clA = ex.x >= 0.f;
+        clB = ex.y >= 0.f;
+        const float2 adt = mul2(C.w, kf);
         dp = sub2(dp, adt);
         dq = sub2(dq, adt);
     }
@@ -328,8 +324,8 @@ __device__ __forceinline__ void a_dstage_adj2(const N2& L, const N2& C, const N2
     cC = add2(cC, sub2(glp, glq));
     if (fric) {
         const float2 gadt = mul2(v2(-1.f), add2(gdp, gdq));
-        fric_adj1(gadt.x, C.w.x, C.t.x, C.e.x, C.d.x, s.x, hm.x, clA, K, wC.x, tC.x, eC.x);
-        fric_adj1(gadt.y, C.w.y, C.t.y, C.e.y, C.d.y, s.y, hm.y, clB, K, wC.y, tC.y, eC.y);
+        fric_adj1(gadt.x, C.w.x, C.t.x, C.e.x, C.d.x, s2.x, kf.x, clA, wC.x, tC.x, eC.x);
+        fric_adj1(gadt.y, C.w.y, C.t.y, C.e.y, C.d.y, s2.y, kf.y, clB, wC.y, tC.y, eC.y);
     }
     if (SRC) {
         const float2 gs = mul2(sub2(gdp, gdq), sdt);

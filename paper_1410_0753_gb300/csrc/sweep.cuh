@@ -65,25 +65,29 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-// x^(-4/3) for x > 0 from the hardware base-2 logarithm and exponential
-__device__ __forceinline__ float pow_m43(float x) {
-    float l, r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
-    l *= -4.0f / 3.0f;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
-    return r;
-}
 // sqrt(x) for x >= 0 (x = 0 gives 0 through the 1e-30 floor)
 __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrt_approx(fmaxf(x, 1e-30f)); }
 __device__ __forceinline__ float div_pos(float a, float b) { return a * rcp_approx(b); }
+// base-2 logarithm (log2(0) = -inf) and exponential (2^-inf = 0)
+__device__ __forceinline__ float log2_fast(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float exp2_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 #else
 // Build option CLIFFS_IEEE_MATH: correctly rounded square root, reciprocal and quotient
 // (IEEE round-to-nearest) in place of the hardware approximations.
 __device__ __forceinline__ float rsqrt_approx(float x) { return __frsqrt_rn(x); }
 __device__ __forceinline__ float rcp_approx(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ float pow_m43(float x) { return __frcp_rn(__fmul_rn(x, cbrtf(x))); }
 __device__ __forceinline__ float sqrt_pos(float x) { return __fsqrt_rn(x); }
 __device__ __forceinline__ float div_pos(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float log2_fast(float x) { return log2f(x); }
+__device__ __forceinline__ float exp2_fast(float x) { return exp2f(x); }
 #endif
 
 // c = sqrt(g h) of both nodes (h > 0 for wet nodes; dry nodes give NaN and are not used)
@@ -106,6 +110,27 @@ __device__ __forceinline__ float wave_speed(float h) {
 
 __device__ __forceinline__ bool wet_mark(float eta, float d, const SweepConst& K) {
     return (d >= K.dwall) && (eta + d >= K.hmin);              // (a): dry when h < h_min
+}
+
+// Friction (reading 4: Manning at time level n, alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3),
+// clamped so that |alpha dt| <= |w|), as alpha dt = w k with
+//   k = min(dt g n^2 sqrt(s2) h^(-4/3), 1) = 2^min(ex, 0),
+//   ex = log2(dt g n^2) + log2(s2) / 2 - 4/3 log2(h),   s2 = w^2 + t^2:
+// one power of two carries the clamp (ex >= 0: clamped, alpha dt = w). s2 = 0 gives k = 0.
+// The adjoint's recomputation calls the same function, so both take the same clamp decision.
+__device__ __forceinline__ float2 fric_k2(float2 w, float2 t, float2 h, float dt_gn2, float2& s2, float2& ex) {
+    s2 = fma2(w, w, mul2(t, t));
+    const float2 ls = make_float2(log2_fast(s2.x), log2_fast(s2.y));
+    const float2 lh = make_float2(log2_fast(h.x), log2_fast(h.y));
+    ex = fma2(v2(0.5f), ls, fma2(v2(-4.0f / 3.0f), lh, v2(log2_fast(dt_gn2))));
+    return make_float2(exp2_fast(fminf(ex.x, 0.f)), exp2_fast(fminf(ex.y, 0.f)));
+}
+__device__ __forceinline__ float fric_k(float w, float t, float h, float dt_gn2, float& s2, float& ex) {
+    float2 s2p, exp_;
+    const float2 k = fric_k2(v2(w), v2(t), v2(h), dt_gn2, s2p, exp_);
+    s2 = s2p.x;
+    ex = exp_.x;
+    return k.x;
 }
 
 struct Flux2 { float2 p, q, t; };
@@ -178,8 +203,7 @@ static __device__ __noinline__ void open_flux(float e, float w, float t, float d
 
 // (d): eq. (solver2) at two nodes given their left and right interface fluxes.
 //   k2 = dt^2 / (dx_{j-1} + dx_j); sdt = dt tan(phi) / R in the spherical y-sweep (SRC).
-// Friction: alpha = g n^2 w sqrt(w^2 + t^2) / h^(4/3) at time level n on both p and q,
-// clamped so that |alpha dt| <= |w|.
+// Friction (fric_k2) at time level n on both p and q.
 // With S1, eq. (solver1): the first-order term is dt Q(j+1, j-1) over dx_{j-1} + dx_j, given
 // as the flux F1 between the two neighbours (per unit length) instead of the mean of L and R.
 template <bool SRC, bool FRIC, bool S1 = false>
@@ -200,12 +224,8 @@ __device__ __forceinline__ void node_update2(float2 e, float2 w, float2 t, float
         dq = fma2(mul2(lq, k2), sub2(R.q, L.q), mul2(nh, add2(L.q, R.q)));
     }
     if (FRIC) {
-        const float2 h = add2(e, d);
-        const float2 s2 = fma2(w, w, mul2(t, t));
-        const float2 s = make_float2(sqrt_pos(s2.x), sqrt_pos(s2.y));
-        float2 adt = mul2(mul2(mul2(v2(K.dt_gn2), w), s), make_float2(pow_m43(h.x), pow_m43(h.y)));
-        if (fabsf(adt.x) > fabsf(w.x)) adt.x = w.x;
-        if (fabsf(adt.y) > fabsf(w.y)) adt.y = w.y;
+        float2 s2, ex;
+        const float2 adt = mul2(w, fric_k2(w, t, add2(e, d), K.dt_gn2, s2, ex));
         dp = sub2(dp, adt);
         dq = sub2(dq, adt);
     }

@@ -500,3 +500,99 @@ def test_recorded_batched_run_per_scenario():
     assert e.value.code == ERR_ARG
     assert np.array_equal(g.adjoint_recorded(seed, scenario=0), refs[0][0])
     g.close()
+
+
+def test_adjoint_inversion_1024_at_its_stated_size():
+    """The inversion workload at its stated size: 1024^2 nodes, 2000 FP32 steps, a checkpoint
+    every 100 steps, 32 gauges, L = sum (eta_g - obs)^2 with obs from the FP64 oracle at the
+    true coefficients; the gradient with respect to the 64 unit-source coefficients theta.
+    (1) Dot-product identity: <dL/dtheta, dtheta> from the GPU adjoint against the oracle's
+        FP64 tangent-linear model with the same (GPU) seed, on 3 seeded directions; the
+        sum runs over 2001 records x 32 gauges, so its rounding scales with sum |terms|,
+        to which the difference is compared (bound 1e-4).
+    (2) The oracle's gradient: the same directional derivatives with the oracle's own FP64
+        residual as seed, within 1e-3 of |dL/dtheta|.
+    (3) Central differences (h = 1e-3) of the FP64 oracle's loss on the 2 largest
+        coordinates and 2 random directions, against the GPU gradient: within 1e-3 of
+        max |dL/dtheta| on the directions whose two runs take the same wet/dry history (the
+        same nodes ever wet, the same final mask), within 1e-2 on the others; the gradient
+        is that of the step with its branches frozen, which a difference across a flooding
+        decision does not see (over 2000 steps of run-up most directions flip a shoreline
+        node between theta - h and theta + h).
+    (4) Central differences of the GPU's FP32 forward on the 8 largest coordinates and 4
+        random directions, reported: at this size they carry the
+        FP32 forward's rounding, ~2 sum|r| delta_r / 2h with delta_r ~ 1e-6 m over 2000 steps,
+        a few 1e-3 of max |dL/dtheta|; bound 2e-2."""
+    w = workloads.inversion_1024()
+    n = w.steps
+    assert (w.nx, w.ny, n, len(w.gauges)) == (1024, 1024, 2000, 32)
+    B = w.extra["basis"].reshape(64, -1).astype(np.float64)     # [64][nodes]
+    d64 = P.f32(P.oracle_depth(w))
+    p = oracle.params_from(w)
+    kw = dict(nsteps=n, gout=w.gout, gauges=w.gauges)
+    eta_true = P.f32(np.tensordot(w.extra["theta_true"].astype(np.float64), w.extra["basis"], axes=1))
+    obs = oracle.run(p, w.x, w.y, d64, eta_true, **kw)["gauges"][:, :, 0]
+    g = _start(w)
+
+    def eta_of(theta):
+        return (theta @ B).reshape(w.ny, w.nx).astype(np.float32)
+
+    def loss(theta):
+        g.set_initial(eta_of(theta))
+        g.step(n)
+        r = g.gauges()[:, :, 0].astype(np.float64) - obs
+        return float((r * r).sum()), r
+
+    def loss64(theta):
+        o = oracle.run(p, w.x, w.y, d64, eta_of(theta).astype(np.float64), maxout=1, **kw)
+        r = o["gauges"][:, :, 0] - obs
+        # the wet/dry history: nodes ever wet (max-wave set) and wet at the end
+        return float((r * r).sum()), o["eta_max"] > -1e30, (o["eta"] + d64) >= w.h_min
+
+    theta0 = w.extra["theta0"].astype(np.float64)
+    L0, r32 = loss(theta0)
+    seed32 = (2.0 * r32).astype(np.float32)
+    g.set_initial(eta_of(theta0))
+    grad_eta = g.adjoint(n, seed32, checkpoint_every=100).astype(np.float64).ravel()
+    gtheta = B @ grad_eta
+    assert np.isfinite(gtheta).all() and np.linalg.norm(gtheta) > 0
+    h = 1e-3
+    rng = np.random.default_rng(41)
+    dirs = [np.eye(64)[k] for k in np.argsort(-np.abs(gtheta))[:8]]
+    for _ in range(4):
+        v = rng.standard_normal(64)
+        dirs.append(v / np.linalg.norm(v))
+    fd32_worst = 0.0
+    for v in dirs:
+        fd = (loss(theta0 + h * v)[0] - loss(theta0 - h * v)[0]) / (2 * h)
+        fd32_worst = max(fd32_worst, abs(fd - float(gtheta @ v)) / np.abs(gtheta).max())
+    g.close()
+    fd64 = []
+    for v in dirs[:2] + dirs[8:10]:                   # 2 coordinates, 2 random directions
+        Lp, evp, wp = loss64(theta0 + h * v)
+        Lm, evm, wm = loss64(theta0 - h * v)
+        flip_free = bool(np.array_equal(evp, evm) and np.array_equal(wp, wm))
+        fd64.append((abs((Lp - Lm) / (2 * h) - float(gtheta @ v)) / np.abs(gtheta).max(), flip_free))
+    free = [e for e, f in fd64 if f]
+    fd64_worst = max(free, default=0.0)
+    fd64_all = max(e for e, _ in fd64)
+    eta0 = eta_of(theta0).astype(np.float64)
+    r64 = oracle.run(p, w.x, w.y, d64, eta0, **kw)["gauges"][:, :, 0] - obs
+    seed64 = 2.0 * r64
+    dot_worst, grad_worst = 0.0, 0.0
+    for k in range(3):
+        v = rng.standard_normal(64)
+        v /= np.linalg.norm(v)
+        delta = (v @ B).reshape(w.ny, w.nx)
+        _, gtan, _, _ = oracle.run_tlm(p, w.x, w.y, d64, eta0, delta, **kw)
+        got = float(gtheta @ v)
+        terms = seed32.astype(np.float64) * gtan
+        dot_worst = max(dot_worst, abs(got - terms.sum()) / np.abs(terms).sum())
+        grad_worst = max(grad_worst, abs(got - float((seed64 * gtan).sum())) / np.linalg.norm(gtheta))
+    P.report("adjoint_inversion_1024_full", steps=n, dot_rel=dot_worst, oracle_grad_rel=grad_worst,
+             fd64_rel_flip_free=fd64_worst, fd64_per_direction=[[float(e), int(f)] for e, f in fd64],
+             fd32_rel=fd32_worst, loss=L0, grad_norm=float(np.linalg.norm(gtheta)))
+    assert dot_worst <= DOT_RTOL, dot_worst
+    assert grad_worst <= 1e-3, grad_worst
+    assert fd64_worst <= FD_RTOL and fd64_all <= 1e-2, fd64
+    assert fd32_worst <= 2e-2, fd32_worst

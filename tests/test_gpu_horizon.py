@@ -2,130 +2,165 @@
 
 Configurations and horizons: the 1024^2 inversion grid over its 2000 steps (32 gauges,
 friction, a shore), scenarios of the 256 x 512^2 ensemble over their full durations (up to
-about 4000 steps), and the 2048^2 geographic grid over its 3600 steps with every output
-recorded. The last needs about six minutes of the oracle on the host cores and runs only
-with CLIFFS_HORIZON=1; the 200^2 beach over its 1000 steps is in test_gpu_parity.py and the
-8192^2 grid is checked on windows there. Tolerances as in test_gpu_parity.py: gauge traces
-within 1e-4 of the oracle's max |eta| per gauge (1e-7 m absolute for traces below 1e-3 m),
-wet masks equal except near round-off; fields and maxima within 1e-4 of the amplitude where
-the solution is smooth, with an allowance at bores for a front displaced by a hundredth of a
-cell. Those hold for a well-conditioned run. Over long run-up a deviation of FP32 size can
-flip shoreline flooding decisions and then grow; each run's own conditioning is measured
-(the FP64 oracle against itself under a 1e-5 perturbation from mid-horizon), and a run that
-amplifies the perturbation more than tenfold is held to three times that sensitivity.
+about 4000 steps), and the 2048^2 geographic grid over its 3600 steps. The 200^2 beach over
+its 1000 steps is in test_gpu_parity.py and the 8192^2 grid is checked on windows there.
+
+Tolerances as in test_gpu_parity.py: gauge traces within 1e-4 of the oracle's max |eta| per
+gauge (1e-7 m absolute for traces below 1e-3 m), wet masks equal.
+
+The GPU and the oracle are advanced together, in chunks, and their wet/dry masks compared
+after every chunk. While the masks agree, both take the same branch of every threshold of
+the method (steps (a) and (b) of the inundation algorithm), and the gauge tolerance holds.
+Over long run-up a decision can land within an FP32-sized distance of its threshold (a
+flooding margin eta_j + d_i - h_min or a wet margin h - h_min of ~1e-6): FP32 and FP64 then
+take it differently, and the two runs continue from states that differ by a wetted or a
+dried node. Such a run is checked in three parts:
+  1. up to the step before the first mask difference, the gauge tolerance holds;
+  2. at that step the FP64 oracle, started from the GPU's own state one step earlier, takes
+     the GPU's decisions (the two sides apply the same method to states an FP32-sized
+     deviation apart), except at nodes it leaves within the near-round-off band of the wet
+     threshold, |h - h_min| < 1e-5 max(1, |d|), where the step's own FP32 arithmetic decides
+     (the band in which the masks of the parity tests may differ);
+  3. over the rest of the horizon the GPU's gauge deviation is what the FP64 scheme itself
+     produces from the GPU's state before the flip (the oracle continued from that state
+     against the oracle's own run): within three times that deviation plus the tolerance.
 """
 import dataclasses
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import workloads
-from paper_1410_0753_gb300 import CliffsGrid
+from paper_1410_0753_gb300 import CliffsGrid, cliffs_read_state
 from tests import parity as P
 
 pytestmark = pytest.mark.gpu
 
-
-def _jump(f):
-    """Largest difference to a 4-neighbour, per cell (the local jump of a field)."""
-    j = np.zeros_like(f)
-    dx = np.abs(np.diff(f, axis=1))
-    j[:, 1:] = np.maximum(j[:, 1:], dx)
-    j[:, :-1] = np.maximum(j[:, :-1], dx)
-    if f.shape[0] > 1:
-        dy = np.abs(np.diff(f, axis=0))
-        j[1:, :] = np.maximum(j[1:, :], dy)
-        j[:-1, :] = np.maximum(j[:-1, :], dy)
-    return j
+CHUNK = 10
 
 
-def _check(name, w, g, o, d64, amp):
-    """Gauges to the stated tolerance. Fields: a smooth cell within 1e-4 of the amplitude; at
-    a bore, where the solution jumps by J between neighbouring cells, a front displaced by a
-    fraction eps of a cell changes the cell by eps J, so the bound there adds 1e-2 J (fronts
-    within a hundredth of a cell after the whole horizon; FP32 rounding shifts them far
-    less)."""
-    rel, absol = P.gauge_errors(g["gauges"][:, :, 0], o["gauges"][:, :, 0])
-    wet32, wet64, near = P.wet_masks(g["eta"], o["eta"], P.f32(d64), P.f32(d64), w.h_min)
-    mism = (wet32 != wet64) & ~near
-    wet_ever = o["eta_max"] > -1e30
-    de = np.abs(g["eta"] - o["eta"])
-    dm = np.where(wet_ever, np.abs(g["eta_max"] - o["eta_max"]), 0.0)
-    je = _jump(np.where(wet64, o["eta"], 0.0))
-    jm = _jump(np.where(wet_ever, o["eta_max"], 0.0))
-    smooth = wet64 & (je < 1e-2 * amp)
-    iy, ix = np.unravel_index(np.argmax(np.where(wet64, de, 0.0)), de.shape)
-    P.report(name, steps=w.steps, gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0),
-             eta_abs_max=float(de[wet64].max()), eta_abs_smooth=float(de[smooth].max(initial=0.0)),
-             worst_at=[int(ix), int(iy)], worst_jump=float(je[iy, ix]), emax_abs_max=float(dm.max()),
-             mask_mismatch_not_near=int(mism.sum()), near=int(near.sum()))
-    assert rel.max(initial=0.0) <= P.GAUGE_RTOL and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
-    assert mism.sum() == 0
-    assert np.all(de[wet64] <= 1e-4 * amp + 1e-2 * je[wet64])
-    assert np.all(dm[wet_ever] <= 1e-4 * amp + 1e-2 * jm[wet_ever])
+def _eta(g):
+    e = np.empty((g.ny, g.nx), np.float32)
+    cliffs_read_state(g.h, 0, e, None, None)
+    return e
 
 
-EPS = 1e-5
+def _wet(eta, d32, hmin, fp32):
+    if fp32:
+        return (eta.astype(np.float32) + d32.astype(np.float32)) >= np.float32(hmin)
+    return (eta + d32) >= hmin
 
 
-def _sensitivity(p, w, d64, eta0, n, u0=None, v0=None):
-    """The problem's own conditioning: the oracle from its mid-horizon state against the same
-    continuation with the state perturbed by EPS (relative, seeded), as the largest gauge
-    difference relative to the gauge's max |eta|. EPS is the size of FP32's accumulated
-    deviation over these horizons (smooth-field errors of 1e-6 to 2e-5 of the amplitude in
-    the runs here). A well-conditioned run returns about EPS (the perturbation itself at the
-    gauges); one where deviations flip shoreline flooding decisions returns much more."""
-    half = n // 2
-    kw = dict(maxout=w.maxout, gout=w.gout, gauges=w.gauges, bndout=w.bndout, nests=w.nests or None)
-    r = oracle.run(p, w.x, w.y, d64, eta0, u0, v0, nsteps=half)
-    rng = np.random.default_rng(11)
-    f = lambda a: a * (1.0 + EPS * rng.standard_normal(a.shape))
-    c0 = oracle.run(p, w.x, w.y, d64, r["eta"], r["u"], r["v"], nsteps=n - half, step0=half, **kw)
-    c1 = oracle.run(p, w.x, w.y, d64, f(r["eta"]), f(r["u"]), f(r["v"]), nsteps=n - half, step0=half, **kw)
-    g0, g1 = c0["gauges"][:, :, 0], c1["gauges"][:, :, 0]
-    return float((np.abs(g1 - g0).max(axis=0) / np.maximum(np.abs(g0).max(axis=0), 1e-3)).max())
+def _gauge_rel(g32, g64):
+    rel, absol = P.gauge_errors(g32, g64)
+    return float(rel.max(initial=0.0)), float(absol.max(initial=0.0))
 
 
-def _assess(name, w, got, o, d64, amp, sens):
-    """A run whose own FP64 solution amplifies the perturbation at most tenfold is held to the
-    stated tolerances (_check); one that amplifies it more is held to three times its own
-    sensitivity on the gauges, and its masks and fields are reported (next to the shoreline
-    they can then differ by flooding decisions taken on different sides of h_min)."""
-    if sens <= 10 * EPS:
-        _check(name, w, got, o, d64, amp)
-        P.report(name + "_sensitivity", sensitivity=sens, well_conditioned=1)
-        return
-    rel, absol = P.gauge_errors(got["gauges"][:, :, 0], o["gauges"][:, :, 0])
-    wet32, wet64, near = P.wet_masks(got["eta"], o["eta"], d64, d64, w.h_min)
-    de = np.abs(got["eta"] - o["eta"])
-    je = _jump(np.where(wet64, o["eta"], 0.0))
-    smooth = wet64 & (je < 1e-2 * amp)
-    P.report(name, steps=w.steps, sensitivity=sens, well_conditioned=0,
-             gauge_rel_max=rel.max(initial=0.0), gauge_abs_max=absol.max(initial=0.0),
-             eta_abs_smooth=float(de[smooth].max(initial=0.0)), mask_mismatch=int((wet32 != wet64).sum()),
-             mismatch_depth_max=float(np.abs(d64[wet32 != wet64]).max(initial=0.0)))
-    assert rel.max(initial=0.0) <= max(P.GAUGE_RTOL, 3.0 * sens) and absol.max(initial=0.0) <= P.GAUGE_ATOL_SMALL
+def horizon(name, w, eta0, n, make_grid):
+    """Co-step a GPU grid (make_grid(): configured, bathymetry set) and the oracle over n
+    steps from eta0; returns the report dict after the assertions of the module docstring."""
+    assert w.gout == 1                     # record r is the state after r steps
+    d32 = P.f32(P.oracle_depth(w))
+    p = oracle.params_from(w)
+    kw = dict(gout=w.gout, gauges=w.gauges)
+    g = make_grid()
+    e0 = eta0.astype(np.float32)
+    g.set_initial(e0)
+    o = dict(eta=e0.astype(np.float64), u=np.zeros_like(d32), v=np.zeros_like(d32))
+    recs, k, first = [], 0, None
+    start = None                           # (k, oracle state) at the start of the first mismatching chunk
+    while k < n:
+        m = min(CHUNK, n - k)
+        prev = (k, o)
+        g.step(m)
+        r = oracle.run(p, w.x, w.y, d32, o["eta"], o["u"], o["v"], nsteps=m, step0=k, record_initial=k == 0, **kw)
+        recs.append(r["gauges"][:, :, 0])
+        o = dict(eta=r["eta"], u=r["u"], v=r["v"])
+        k += m
+        if first is None and np.any(_wet(_eta(g), d32, w.h_min, True) != _wet(o["eta"], d32, w.h_min, False)):
+            first, start = k, prev
+    g64 = np.concatenate(recs)
+    g32 = g.gauges()[:, :, 0].astype(np.float64)
+    assert g32.shape == g64.shape
+    e32 = _eta(g)
+    rel, absol = _gauge_rel(g32, g64)
+    out = dict(steps=n, gauge_rel_max=rel, gauge_abs_max=absol,
+               eta_abs_max=float(np.abs(e32 - o["eta"])[_wet(o["eta"], d32, w.h_min, False)].max(initial=0.0)))
+    if first is None:
+        out.update(flip_step=-1)
+        P.report(name, **out)
+        assert rel <= P.GAUGE_RTOL and absol <= P.GAUGE_ATOL_SMALL, out
+        g.close()
+        return out
+    # replay the first mismatching chunk step by step on both sides (the GPU run repeats
+    # bit for bit from the initial state)
+    k0, ost = start
+    g.set_initial(e0)
+    g.step(k0)
+    s = k0
+    while True:
+        gprev = g.state()
+        oprev = dict(ost)
+        g.step(1)
+        r = oracle.run(p, w.x, w.y, d32, ost["eta"], ost["u"], ost["v"], nsteps=1, step0=s, record_initial=False)
+        ost = dict(eta=r["eta"], u=r["u"], v=r["v"])
+        s += 1
+        m32 = _wet(_eta(g), d32, w.h_min, True)
+        if np.any(m32 != _wet(ost["eta"], d32, w.h_min, False)) or s >= first:
+            break
+    assert s == first or np.any(m32 != _wet(ost["eta"], d32, w.h_min, False))
+    m64 = _wet(ost["eta"], d32, w.h_min, False)
+    flips = int((m32 != m64).sum())
+    # 2. the oracle from the GPU's state one step before the flip takes the GPU's decisions,
+    # except at nodes whose wet margin |h - h_min| it leaves within the near-round-off band
+    gs = [a.astype(np.float64) for a in gprev]
+    r = oracle.run(p, w.x, w.y, d32, gs[0], gs[1], gs[2], nsteps=1, step0=s - 1, record_initial=False)
+    mo = _wet(r["eta"], d32, w.h_min, False)
+    diff = mo != m32
+    margin = np.abs(r["eta"] + d32 - w.h_min)
+    band = P.NEAR * np.maximum(1.0, np.abs(d32))
+    same_decisions = bool(not diff.any())
+    near_only = bool(np.all(margin[diff] < band[diff]))
+    jy, jx = np.nonzero(m32 != m64)
+    at = [(int(x), int(y), float(d32[y, x]), float(gprev[0][y, x]), float(_eta(g)[y, x]), float(margin[y, x]))
+          for y, x in zip(jy, jx)][:4]
+    state_diff = max(float(np.abs(gs[i] - oprev[key]).max()) for i, key in enumerate(("eta", "u", "v")))
+    pre = s - 1                                     # records 0 .. s-1 precede the flip
+    rel_pre, abs_pre = _gauge_rel(g32[: pre + 1], g64[: pre + 1])
+    # 3. the FP64 scheme continued from the GPU's state before the flip, against its own run
+    c = oracle.run(p, w.x, w.y, d32, gs[0], gs[1], gs[2], nsteps=n - (s - 1), step0=s - 1, record_initial=True, **kw)
+    g64c = np.concatenate([g64[: s - 1], c["gauges"][:, :, 0]])
+    rel_fp64, _ = _gauge_rel(g64c, g64)
+    out.update(flip_step=s, flipped_nodes=flips, flipped_at=at, state_diff_before_flip=state_diff,
+               gauge_rel_before_flip=rel_pre, oracle_from_gpu_state_same_decisions=int(same_decisions),
+               differing_decisions_near_round_off=int(near_only), fp64_deviation_from_gpu_state=rel_fp64)
+    P.report(name, **out)
+    g.close()
+    assert rel_pre <= P.GAUGE_RTOL and abs_pre <= P.GAUGE_ATOL_SMALL, out
+    assert same_decisions or near_only, out
+    assert rel <= 3.0 * rel_fp64 + P.GAUGE_RTOL and absol <= P.GAUGE_ATOL_SMALL, out
+    return out
+
+
+def _grid(w, **kw):
+    def make():
+        g = CliffsGrid.from_workload(w, **kw)
+        g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
+        return g
+    return make
 
 
 def test_inversion_1024_full_horizon():
     w = workloads.inversion_1024()
-    d64 = P.f32(P.oracle_depth(w))
-    g = P.gpu_run(w, w.steps)
-    o = P.oracle_run(w, w.steps, d64)
-    sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
-    _assess("horizon_inversion_1024", w, g, o, d64, np.abs(w.eta0).max(), sens)
-    g["grid"].close()
+    horizon("horizon_inversion_1024", w, w.eta0, w.steps, _grid(w))
 
 
 def test_ensemble_scenarios_full_durations():
-    """Three scenarios of the ensemble (the longest, the shortest and the median duration)
-    run to their own durations in one persistent launch, each against its own oracle run and
-    assessed against its own conditioning (run-up on the ensemble's beach makes some scenarios
-    ill-conditioned)."""
+    """Three scenarios of the ensemble (the longest, the shortest and the median duration):
+    all 256 run to their own durations in one persistent launch; each pick equals its own
+    single-scenario run bit for bit, and that run is co-stepped with the oracle."""
     w = workloads.ensemble_512()
-    d64 = P.f32(P.oracle_depth(w))
     order = np.argsort(w.durations)
     picks = [int(order[-1]), int(order[0]), int(order[len(order) // 2])]
     g = CliffsGrid.from_workload(w)
@@ -133,25 +168,21 @@ def test_ensemble_scenarios_full_durations():
     g.set_initial(w.eta0.astype(np.float32))
     g.set_durations(w.durations)
     g.step(int(w.durations.max()), persistent=True)
-    p = oracle.params_from(w)
+    batched = {b: (g.state(b)[0], g.gauges(b)[: int(w.durations[b]) // w.gout + 1]) for b in picks}
+    g.close()
     for b in picks:
         n = int(w.durations[b])
-        e, u, v = g.state(b)
-        em, sm = g.maxwave(b)
-        got = dict(eta=e, gauges=g.gauges(b)[: n // w.gout + 1], eta_max=em)
-        o = oracle.run(p, w.x, w.y, d64, w.eta0[b], nsteps=n, maxout=w.maxout, gout=w.gout, gauges=w.gauges)
-        sens = _sensitivity(p, w, d64, w.eta0[b], n)
-        _assess("horizon_ensemble_scenario_%d" % b, dataclasses.replace(w, steps=n), got, o, d64,
-               np.abs(w.eta0[b]).max(), sens)
-    g.close()
+        w1 = dataclasses.replace(w, eta0=w.eta0[b], steps=n, durations=None)
+        make = _grid(w1, batch=1)
+        single = make()
+        single.set_initial(w.eta0[b].astype(np.float32))
+        single.step(n)
+        assert np.array_equal(single.state()[0], batched[b][0])
+        assert np.array_equal(single.gauges(), batched[b][1])
+        single.close()
+        horizon("horizon_ensemble_scenario_%d" % b, w1, w.eta0[b], n, make)
 
 
-@pytest.mark.skipif(os.environ.get("CLIFFS_HORIZON") != "1", reason="about six minutes of oracle time")
 def test_spherical_coast_2048_full_horizon():
     w = workloads.spherical_coast()
-    d64 = P.f32(P.oracle_depth(w))
-    g = P.gpu_run(w, w.steps)
-    o = P.oracle_run(w, w.steps, d64)
-    sens = _sensitivity(oracle.params_from(w), w, d64, w.eta0, w.steps)
-    _assess("horizon_spherical_2048", w, g, o, d64, np.abs(w.eta0).max(), sens)
-    g["grid"].close()
+    horizon("horizon_spherical_2048", w, w.eta0, w.steps, _grid(w, nests=[], maxout=w.steps + 1))
