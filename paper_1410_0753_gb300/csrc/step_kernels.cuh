@@ -90,6 +90,11 @@ __device__ __forceinline__ int open_end_y(const StepArgs& a, int row) {
 __device__ __forceinline__ int runaway(float e, float u, float v) {
     return !(fabsf(e) + fabsf(u) + fabsf(v) < 3e5f);
 }
+// The same test accumulated branch-free over the rows of a warp's work: the sum of
+// e^2 + u^2 + v^2 over its stored nodes reaches 9e10 when any node reaches 3e5 in a component
+// (no physical state sums that high over a warp's few thousand nodes), and a non-finite
+// value makes it non-finite.
+constexpr float RUNAWAY_SQ = 9e10f;
 
 // What changes from one step to the next: the input state's TMA descriptors, the output
 // planes, and the max-wave fields and record rows when they are due this step (else null).
@@ -112,6 +117,8 @@ __device__ __forceinline__ StepOut step_out(const StepMaps* M, const StepArgs& a
 // field maxout), (em, sm) hold the stored maxima of the pair (loaded beforehand); on wet
 // nodes they take the new eta and speed sqrt(u^2 + v^2) where these are larger and are
 // written back.
+// With CHECK the runaway test runs here (the fused kernels accumulate it instead, chk_out).
+template <bool CHECK = true>
 __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, size_t o, bool va, bool vb,
                                           float2 E, float2 U, float2 V, float2 D,
                                           float2 em, float2 sm, int& bad) {
@@ -120,10 +127,10 @@ __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, s
         *reinterpret_cast<float2*>(O.eta_out + o) = E;
         *reinterpret_cast<float2*>(O.u_out + o) = U;
         *reinterpret_cast<float2*>(O.v_out + o) = V;
-        bad |= runaway(E.x, U.x, V.x) | runaway(E.y, U.y, V.y);
+        if (CHECK) bad |= runaway(E.x, U.x, V.x) | runaway(E.y, U.y, V.y);
     } else {
         O.eta_out[o] = E.x; O.u_out[o] = U.x; O.v_out[o] = V.x;
-        bad |= runaway(E.x, U.x, V.x);
+        if (CHECK) bad |= runaway(E.x, U.x, V.x);
     }
     if (O.emax) {
         // max-wave of the pair (wet nodes only), the tests in packed form
@@ -154,13 +161,15 @@ __device__ __forceinline__ void emit_pair(const StepArgs& a, const StepOut& O, s
 // samples, every lane whose record belongs to that row fetches the node's values from the
 // lane that owns the node by shuffle and writes the record, so all samples of a row go out
 // together; `next` holds the row of the next sample so rows without samples cost a compare.
+// The writer is a separate (not inlined) function: it runs on the few rows with samples,
+// and kept out of the row loop it leaves the loop's code to the sweeps.
 struct Samples {
     int sp, se, base, next;
     int4 mine;
 
-    __device__ __forceinline__ void load(const StepArgs& a, int lane) {
+    __device__ __forceinline__ void load(const int4* samp, int lane) {
         base = sp;
-        mine = (sp + lane < se) ? __ldg(a.samp + sp + lane) : make_int4(0x7fffffff, 0, 0, 0);
+        mine = (sp + lane < se) ? __ldg(samp + sp + lane) : make_int4(0x7fffffff, 0, 0, 0);
     }
     __device__ __forceinline__ void init(const StepArgs& a, const StepOut& O, int gw, int lane) {
         sp = se = base = 0;
@@ -170,43 +179,52 @@ struct Samples {
             sp = a.samp_ptr[gw];
             se = a.samp_ptr[gw + 1];
             if (sp < se) {
-                load(a, lane);
+                load(a.samp, lane);
                 next = __shfl_sync(FULL, mine.x, 0);
             }
         }
     }
     __device__ __forceinline__ void emit(const StepArgs& a, const StepOut& O, int b, int r, int c0,
-                                         int lane, float2 E, float2 U, float2 V) {
-        if (r != next) return;
-        while (true) {
-            const bool mineRow = lane >= sp - base && mine.x == r;
-            const int rel = mine.y - c0;
-            const int src = mineRow ? (rel >> 1) & 31 : lane;
-            const float ex = __shfl_sync(FULL, E.x, src), ey = __shfl_sync(FULL, E.y, src);
-            const float ux = __shfl_sync(FULL, U.x, src), uy = __shfl_sync(FULL, U.y, src);
-            const float vx = __shfl_sync(FULL, V.x, src), vy = __shfl_sync(FULL, V.y, src);
-            if (mineRow) {
-                const bool isB = rel & 1;
-                float* out = (mine.z == 0) ? (O.rec_g ? O.rec_g + (long long)b * a.rec_g_bstride : nullptr)
-                                           : O.rec_n;
-                if (out) {
-                    out[3 * mine.w + 0] = isB ? ey : ex;
-                    out[3 * mine.w + 1] = isB ? uy : ux;
-                    out[3 * mine.w + 2] = isB ? vy : vx;
-                }
-            }
-            sp += __popc(__ballot_sync(FULL, mineRow));
-            if (sp >= se) { next = 0x7fffffff; return; }
-            if (sp - base < 32) {                  // the next record is cached: a later row
-                next = __shfl_sync(FULL, mine.x, sp - base);
-                return;
-            }
-            load(a, lane);                         // the row's records run past the cache
-            next = __shfl_sync(FULL, mine.x, 0);
-            if (next != r) return;
-        }
-    }
+                                         int lane, float2 E, float2 U, float2 V);
 };
+
+// the samples of row r (warp-collective); returns the updated sample cursor
+static __device__ __noinline__ Samples samples_write(Samples S, const int4* samp, float* rec_g, float* rec_n, int r,
+                                                     int c0, int lane, float2 E, float2 U, float2 V) {
+    while (true) {
+        const bool mineRow = lane >= S.sp - S.base && S.mine.x == r;
+        const int rel = S.mine.y - c0;
+        const int src = mineRow ? (rel >> 1) & 31 : lane;
+        const float ex = __shfl_sync(FULL, E.x, src), ey = __shfl_sync(FULL, E.y, src);
+        const float ux = __shfl_sync(FULL, U.x, src), uy = __shfl_sync(FULL, U.y, src);
+        const float vx = __shfl_sync(FULL, V.x, src), vy = __shfl_sync(FULL, V.y, src);
+        if (mineRow) {
+            const bool isB = rel & 1;
+            float* out = (S.mine.z == 0) ? rec_g : rec_n;
+            if (out) {
+                out[3 * S.mine.w + 0] = isB ? ey : ex;
+                out[3 * S.mine.w + 1] = isB ? uy : ux;
+                out[3 * S.mine.w + 2] = isB ? vy : vx;
+            }
+        }
+        S.sp += __popc(__ballot_sync(FULL, mineRow));
+        if (S.sp >= S.se) { S.next = 0x7fffffff; return S; }
+        if (S.sp - S.base < 32) {                  // the next record is cached: a later row
+            S.next = __shfl_sync(FULL, S.mine.x, S.sp - S.base);
+            return S;
+        }
+        S.load(samp, lane);                        // the row's records run past the cache
+        S.next = __shfl_sync(FULL, S.mine.x, 0);
+        if (S.next != r) return S;
+    }
+}
+
+__device__ __forceinline__ void Samples::emit(const StepArgs& a, const StepOut& O, int b, int r, int c0,
+                                              int lane, float2 E, float2 U, float2 V) {
+    if (r != next) return;
+    *this = samples_write(*this, a.samp, O.rec_g ? O.rec_g + (long long)b * a.rec_g_bstride : nullptr, O.rec_n,
+                          r, c0, lane, E, U, V);
+}
 
 // ------------------------------------------------------------------ fused step
 // One warp of the fused step. A work item is a strip and an output row range [r0, r1); the
@@ -231,6 +249,8 @@ struct FusedWarp {
     Samples smp;
     StepOut O;
     int bad;
+    float2 chk_x;              // sum of 0 * (x-swept eta): 0, or NaN once a value is not finite
+    float2 chk_out;            // sum of e^2 + u^2 + v^2 over the stored nodes (RUNAWAY_SQ)
 
     __device__ __forceinline__ FusedWarp(const StepArgs& a_) : a(a_) {}
 
@@ -241,6 +261,7 @@ struct FusedWarp {
         bar = reinterpret_cast<uint64_t*>(smem_raw + FUSED_WARPS * WARP_RING_BYTES) + wib * RING;
         used = 0;
         bad = 0;
+        chk_x = chk_out = v2(0.f);
         if (lane == 0) {
             for (int s = 0; s < RING; ++s) mbar_init(&bar[s], 1);
             fence_mbar_init();
@@ -287,9 +308,8 @@ struct FusedWarp {
         // y-sweep input of row k: eta, w = v, t = u
         const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
         // a non-finite x-sweep result reads as a dry node in the y-sweep and would be
-        // refilled by step (b) there: it is flagged here
-        if (vA && !oA) bad |= !(fabsf(E.x) < 1e5f);
-        if (vB && !oB) bad |= !(fabsf(E.y) < 1e5f);
+        // refilled by step (b) there: it is caught here (0 * NaN or 0 * inf is NaN)
+        chk_x = fma2(E, v2(0.f), chk_x);
         const int r = k - 3;
         // the y-sweep results a lane must get right: its own output columns, and with YF every
         // column of the window (the x-sweep on the way out reads three columns past the outputs)
@@ -310,7 +330,12 @@ struct FusedWarp {
                         em = reinterpret_cast<const float2*>(s + 4 * ARR_FLOATS)[lane];
                         sm = reinterpret_cast<const float2*>(s + 5 * ARR_FLOATS)[lane];
                     }
-                    emit_pair(a, O, orow + (size_t)(r - r0) * a.pitch, vA, vB, oe, ot, ow, od, em, sm, bad);
+                    emit_pair<false>(a, O, orow + (size_t)(r - r0) * a.pitch, vA, vB, oe, ot, ow, od, em, sm, bad);
+                    // the stored nodes only (an unstored column past the domain edge may hold
+                    // anything after an open-water y-sweep that did not need it)
+                    const float2 q2 = fma2(oe, oe, fma2(ot, ot, mul2(ow, ow)));
+                    if (vB) chk_out = add2(chk_out, q2);
+                    else if (vA) chk_out.x += q2.x;
                     smp.emit(a, O, b, r, c0, lane, oe, ot, ow);
                 }
             }, OPEN ? open_end_y(a, k - 2) : 0);
@@ -379,6 +404,7 @@ struct FusedWarp {
     }
 
     __device__ __forceinline__ void report() {
+        bad |= !(chk_x.x + chk_x.y == 0.f) | !(chk_out.x + chk_out.y < RUNAWAY_SQ);
         if (bad) atomicOr(a.err, (bad & 2) ? (ERRF_TIMEOUT | ERRF_NONFINITE) : ERRF_NONFINITE);
     }
 };
@@ -457,6 +483,7 @@ k_batch(const __grid_constant__ StepMaps2 MM, const StepArgs a, const BatchArgs 
     FusedWarp<SPH, FRIC, true, S1, OPEN> WY(a);
     if (ALT) {
         WY.lane = W.lane; WY.K = W.K; WY.ring = W.ring; WY.bar = W.bar; WY.used = W.used; WY.bad = 0;
+        WY.chk_x = WY.chk_out = v2(0.f);
     }
     for (long long st = step0 + 1; st <= step_end; ++st) {
         const bool yf = ALT && (((st - 1) & 1) != 0);
