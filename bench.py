@@ -213,7 +213,7 @@ def _event_ms(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_forms(torch, stream, only=None, adjoint_steps=None, ensemble=None):
+def measure_forms(torch, stream, only=None, adjoint_steps=None, ensemble=None, rows_per_warp=0):
     """The batched ensemble (256 scenarios of uneven duration on one 512 x 512 bathymetry, one
     persistent graph-captured launch) and the adjoint (1024 x 1024, 2000 steps, checkpoint
     every 100), each reported against the plain single-scenario forward on this GPU."""
@@ -222,7 +222,7 @@ def measure_forms(torch, stream, only=None, adjoint_steps=None, ensemble=None):
     out = {}
     s = stream.cuda_stream
     if only in (None, "spherical"):
-        out["spherical"] = _form_spherical(torch, stream, workloads, CliffsGrid)
+        out["spherical"] = _form_spherical(torch, stream, workloads, CliffsGrid, rows_per_warp=rows_per_warp)
     if only in (None, "batched"):
         out["batched"] = _form_batched(torch, stream, workloads, CliffsGrid, ensemble)
     if only in (None, "stress"):
@@ -298,7 +298,7 @@ def _form_stress(torch, stream, workloads, CliffsGrid):
     return out
 
 
-def _form_spherical(torch, stream, workloads, CliffsGrid, steps=20):
+def _form_spherical(torch, stream, workloads, CliffsGrid, steps=20, rows_per_warp=0):
     """The 2048 x 2048 geographic grid (1 arc-minute) with every output due every step:
     max-wave, 64 gauges and the boundary series of 4 enclosed grids; L2 (~150 MB working set)
     flushed by a 256 MiB device write before every timed step."""
@@ -307,8 +307,12 @@ def _form_spherical(torch, stream, workloads, CliffsGrid, steps=20):
     g = CliffsGrid.from_workload(w, stream=s)
     g.set_bathy(w.x, w.y, w.depth, True, w.filter_alpha, w.filter_min_depth)
     g.set_initial(w.eta0.astype(np.float32))
-    tune = g.autotune(3)
-    rows = min(tune, key=tune.get) if tune else None
+    if rows_per_warp:                     # a fixed tile (to profile the configuration a run chose)
+        g.set_rows_per_warp(rows_per_warp)
+        rows = rows_per_warp
+    else:
+        tune = g.autotune(3)
+        rows = min(tune, key=tune.get) if tune else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for i in range(5):
         flush.fill_(i & 0xFF)
@@ -699,7 +703,7 @@ def main():
     ap.add_argument("--ensemble", default=None, metavar="B,DMIN,DMAX",
                     help="batched form on B scenarios of DMIN..DMAX steps instead of 256 of 500..4000")
     ap.add_argument("--rows-per-warp", type=int, default=0,
-                    help="fix the fused step's tile instead of autotuning it")
+                    help="fix the fused step's tile instead of autotuning it (headline and geographic form)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.forms_only:
@@ -708,7 +712,7 @@ def main():
         _build.build()
         ens = tuple(int(t) for t in args.ensemble.split(",")) if args.ensemble else None
         print(json.dumps({"forms": measure_forms(torch, torch.cuda.current_stream(), args.forms_only,
-                                                 args.adjoint_steps, ens)}), flush=True)
+                                                 args.adjoint_steps, ens, args.rows_per_warp)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
