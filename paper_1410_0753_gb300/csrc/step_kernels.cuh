@@ -350,6 +350,27 @@ struct FusedWarp {
         push_row<PH>(k, s, E, U, V, D);
     }
 
+    // The two rows of a ring slot on Cartesian grids (x first, eq. (solver2), reflecting
+    // edges): when one vote finds every node of both rows wet, their x-sweeps run in one
+    // basic block as two independent chains (the same operations as row by row).
+    __device__ __forceinline__ void rows2(int k, const float* s) {
+        float2 E0, U0, V0, D0, E1, U1, V1, D1;
+        XMet2 m0r, m1r;
+        const bool in0 = load_row(k, s, E0, U0, V0, D0, m0r);
+        const bool in1 = load_row(k + 1, s + XWIN, E1, U1, V1, D1, m1r);
+        const bool wet = wet_mark(E0.x, D0.x, K) && wet_mark(E0.y, D0.y, K) &&
+                         wet_mark(E1.x, D1.x, K) && wet_mark(E1.y, D1.y, K);
+        if (in0 && in1 && __all_sync(FULL, wet)) {
+            xsweep2_open<FRIC>(E0, U0, V0, D0, m0r, K);
+            xsweep2_open<FRIC>(E1, U1, V1, D1, m1r, K);
+        } else {
+            if (in0) xsweep2<FRIC, S1, OPEN>(E0, U0, V0, D0, m0r, K, lane, ends);
+            if (in1) xsweep2<FRIC, S1, OPEN>(E1, U1, V1, D1, m1r, K, lane, ends);
+        }
+        push_row<0>(k, s, E0, U0, V0, D0);
+        push_row<1>(k + 1, s + XWIN, E1, U1, V1, D1);
+    }
+
     // Process work item `idx` (strip, rows) of scenario b_ for the step described by O_.
     // Returns false when a wait expired (the warp's copies have landed when it returns).
     __device__ __forceinline__ bool run_item(int idx, int b_, const StepOut& O_) {
@@ -386,8 +407,12 @@ struct FusedWarp {
             if (!__all_sync(FULL, ok)) break;
             const float* s = ring + slot * SLOT_FLOATS;
             const int k = k0 + SLOT_ROWS * j;
-            row<0>(k, s);
-            row<1>(k + 1, s + XWIN);
+            if (!SPH && !YF && !S1 && !OPEN) {
+                rows2(k, s);
+            } else {
+                row<0>(k, s);
+                row<1>(k + 1, s + XWIN);
+            }
             __syncwarp();
             if (j + RING < npairs) issue(j + RING);
         }

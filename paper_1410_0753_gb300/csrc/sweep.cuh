@@ -379,6 +379,28 @@ __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 
     E = E2; W = W2; T = T2;
 }
 
+// xsweep2 when every node of the warp is wet at the start of the sweep (eq. (solver2),
+// reflecting edges): steps (a), (b), (c) and (e) change nothing then, and this is the
+// sequence of operations xsweep2 takes in that case, without its warp-uniform branches, so
+// that the x-sweeps of two rows can share one basic block.
+template <bool FRIC>
+__device__ __forceinline__ void xsweep2_open(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
+                                             const SweepConst& K) {
+    const float2 C = wave_speed2(add2(E, D));
+    const float eR = __shfl_down_sync(FULL, E.x, 1), wR = __shfl_down_sync(FULL, W.x, 1);
+    const float tR = __shfl_down_sync(FULL, T.x, 1), dR = __shfl_down_sync(FULL, D.x, 1);
+    const float cR = __shfl_down_sync(FULL, C.x, 1);
+    const Flux2 FR = iface2(E, W, T, D, C, make_float2(E.y, eR), make_float2(W.y, wR),
+                            make_float2(T.y, tR), make_float2(D.y, dR), make_float2(C.y, cR), m.inv_r);
+    Flux2 FL;
+    FL.p = make_float2(__shfl_up_sync(FULL, FR.p.y, 1), FR.p.x);
+    FL.q = make_float2(__shfl_up_sync(FULL, FR.q.y, 1), FR.q.x);
+    FL.t = make_float2(__shfl_up_sync(FULL, FR.t.y, 1), FR.t.x);
+    float2 E2, W2, T2;
+    node_update2<false, FRIC, false>(E, W, T, D, C, FL, FR, m.k2, v2(0.f), K, E2, W2, T2);
+    E = E2; W = W2; T = T2;
+}
+
 // One row of a pair of columns in the y-sweep pipeline.
 struct YRow {
     float2 e, w, t, d, c;     // w: velocity along the column (v), t: across it (u)
