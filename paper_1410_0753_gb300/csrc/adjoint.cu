@@ -568,8 +568,11 @@ __device__ __forceinline__ void load2(const float* p, long long o, int pos, int 
 // Adjoint of the sweeps along one direction. DIR 0: lines are rows of row-major data and
 // the output is written transposed; DIR 1: lines are rows of transposed data (columns of
 // the grid) and the output is written row-major.
+#ifndef CLIFFS_ADJ_LINE_BLOCKS
+#define CLIFFS_ADJ_LINE_BLOCKS 3
+#endif
 template <int DIR, bool SPH, bool S1>
-__global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const AdjLineArgs A) {
+__global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : CLIFFS_ADJ_LINE_BLOCKS) k_adj_line(const AdjLineArgs A) {
     __shared__ float tile[3][AOUT][TP];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int strip = blockIdx.x, l0 = blockIdx.y * ALINES;
@@ -637,11 +640,14 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : 3) k_adj_line(const Adj
         }
         __syncthreads();
     }
-    float* out[3] = {A.oe, A.ow, A.ot};
-    for (int idx = threadIdx.x; idx < 3 * AOUT * ALINES; idx += blockDim.x) {
-        const int f = idx / (AOUT * ALINES), q = (idx / ALINES) % AOUT, ln = idx % ALINES;
-        const int p = strip * AOUT + q, line = l0 + ln;
-        if (p < A.npos && line < A.nlines) out[f][(long long)p * A.opitch + line] = tile[f][q][ln];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        float* out = f == 0 ? A.oe : f == 1 ? A.ow : A.ot;
+        for (int k = threadIdx.x; k < AOUT * ALINES; k += AWARPS * 32) {
+            const int q = k / ALINES, ln = k % ALINES;
+            const int p = strip * AOUT + q, line = l0 + ln;
+            if (p < A.npos && line < A.nlines) out[(long long)p * A.opitch + line] = tile[f][q][ln];
+        }
     }
 }
 
@@ -694,11 +700,14 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
         }
     }
     __syncthreads();
-    float* out[3] = {te, tu, tv};
-    for (int idx = threadIdx.x; idx < 3 * XOUT * ALINES; idx += blockDim.x) {
-        const int f = idx / (XOUT * ALINES), q = (idx / ALINES) % XOUT, ln = idx % ALINES;
-        const int c = strip * XOUT + q, r = r0 + ln;
-        if (c < a.nx && r < a.ny) out[f][(long long)c * tpitch + r] = tile[f][q][ln];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        float* out = f == 0 ? te : f == 1 ? tu : tv;
+        for (int k = threadIdx.x; k < XOUT * ALINES; k += AWARPS * 32) {
+            const int q = k / ALINES, ln = k % ALINES;
+            const int c = strip * XOUT + q, r = r0 + ln;
+            if (c < a.nx && r < a.ny) out[(long long)c * tpitch + r] = tile[f][q][ln];
+        }
     }
 }
 

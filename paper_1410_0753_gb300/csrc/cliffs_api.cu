@@ -48,6 +48,18 @@ int set_err(int code, const char* fmt, ...) {
 const double R_SPHERE = 6371000.0;
 const double DEGR = 3.14159265358979323846 / 180.0;
 
+// The adjoint recomputes its segments of K steps several at a time, as one batched launch
+// per step: as many segments as fit in this many bytes of recomputed states, tiled to fill
+// about this many waves of resident warps.
+#ifndef CLIFFS_ADJ_GROUP_GIB
+#define CLIFFS_ADJ_GROUP_GIB 8
+#endif
+#ifndef CLIFFS_ADJ_GROUP_WAVES
+#define CLIFFS_ADJ_GROUP_WAVES 2
+#endif
+const double ADJ_GROUP_BYTES = (double)CLIFFS_ADJ_GROUP_GIB * (1 << 30);
+const int ADJ_GROUP_WAVES = CLIFFS_ADJ_GROUP_WAVES;
+
 // ----------------------------------------------------------------------------- kernels
 
 // depth-jump filter, section "Numerical stability": eqs. (dstab), (newdw), (newdc)
@@ -327,10 +339,16 @@ struct cliffs_grid {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int pblocks = 0;
-    // adjoint work space: K recomputed states and the checkpoints (row-major, 3 planes
-    // each), the transposed x-swept state, adjoint and depth (7 planes of [nx][tpitch]),
-    // the row-major intermediate adjoint (3 planes), gauge nodes and seeds
+    // adjoint work space: K recomputed states of up to adj_G segments ([3][adj_G][plane]
+    // per state) and the checkpoints (row-major, 3 planes each), the transposed x-swept
+    // state, adjoint and depth (7 planes of [nx][tpitch]), the row-major intermediate
+    // adjoint (3 planes), gauge nodes and seeds; the work items of the batched segment
+    // recomputation (adj_S rows per warp)
     int adj_K = 0;
+    int adj_G = 0;
+    int adj_S = 0;
+    std::vector<int4> adj_items;
+    int4* adj_items_dev = nullptr;
     long long adj_ncap = 0;
     float* adj_slots = nullptr;
     float* adj_ckpt = nullptr;
@@ -738,7 +756,7 @@ void free_grid(cliffs_grid* g) {
     if (g->ctl_h) cudaFreeHost(g->ctl_h);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
-    cudaFree(g->adj_gxy); cudaFree(g->adj_seed);
+    cudaFree(g->adj_gxy); cudaFree(g->adj_seed); cudaFree(g->adj_items_dev);
     for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
     cudaFree(g->bnd_rows);
     cudaFree(g->rec_ckpt);
@@ -1507,7 +1525,7 @@ int cliffs_adjoint_recorded_scenario(cliffs_grid* g, int32_t scenario, int32_t c
 // the y-sweep of X_j is recomputed row-major, the x-sweep adjoint runs over it, then the
 // y-sweep adjoint over X_j transposed, with transposes where the layouts differ.
 static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineArgs& X, const AdjLineArgs& Y,
-                               const float* st, long long j, bool seeded) {
+                               const float* st, long long fst, long long j, bool seeded) {
     const int nx = g->nx, ny = g->ny, tp = (ny + 31) / 32 * 32;
     const long long P = g->plane, TPL = (long long)tp * nx;
     cudaStream_t s = g->stream;
@@ -1521,7 +1539,7 @@ static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineA
     for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // lambda_{j+1} row-major
         le = launch_transpose(LT + f * TPL, tp, LB + f * P, g->pitch, nx, ny, s);
     StepArgs ay = a;                                             // y-sweep of X_j
-    ay.eta_in = st; ay.u_in = st + P; ay.v_in = st + 2 * P;
+    ay.eta_in = st; ay.u_in = st + fst; ay.v_in = st + 2 * fst;
     ay.eta_out = XR; ay.u_out = XR + P; ay.v_out = XR + 2 * P;
     ay.emax = ay.smax = nullptr; ay.rec_g = ay.rec_n = nullptr; ay.samp_ptr = nullptr; ay.limit = nullptr;
     ay.nstrips = (nx + XWIN - 1) / XWIN; ay.S = 64; ay.nseg = (ny + 63) / 64;
@@ -1532,7 +1550,7 @@ static int adjoint_yfirst_step(cliffs_grid* g, const StepArgs& a, const AdjLineA
     X2.seed = nullptr;
     if (le == cudaSuccess) le = launch_adj_line(X2, 0, a.sph, s);
     for (int f = 0; f < 3 && le == cudaSuccess; ++f)            // X_j transposed
-        le = launch_transpose(st + f * P, g->pitch, XT + f * TPL, tp, ny, nx, s);
+        le = launch_transpose(st + f * fst, g->pitch, XT + f * TPL, tp, ny, nx, s);
     AdjLineArgs Y2 = Y;                                          // y-sweep adjoint -> row-major
     Y2.ge = LT2; Y2.gw = LT2 + 2 * TPL; Y2.gt = LT2 + TPL;
     if (le == cudaSuccess) le = launch_adj_line(Y2, 1, a.sph, s);
@@ -1570,22 +1588,68 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     const long long nseg = (n + K - 1) / K;
     const long long nrec = n / g->cfg.gout + 1;
     const int G = g->G;
-    // work space (kept for later calls)
-    if (g->adj_K < K || !g->adj_slots) {
+    // Segments are recomputed NG at a time: one launch per step advances NG segments (the
+    // fused kernel's batch dimension), which fills the GPU where one grid's launch does not.
+    // NG is the number of segments whose K states fit in ADJ_GROUP_BYTES (1 with boundary
+    // input or the alternating order, whose steps differ between segments).
+    int NG = 1;
+    if (K > 1 && !g->bnd_any && !g->cfg.alternate) {
+        const double seg_bytes = 12.0 * (double)P * K;
+        NG = (int)std::max(1.0, std::min((double)nseg, std::floor((double)ADJ_GROUP_BYTES / seg_bytes)));
+    }
+    // work space (kept for later calls); a smaller group if the larger one does not fit
+    if (g->adj_K < K || g->adj_G < NG || !g->adj_slots) {
         cudaFree(g->adj_slots);
         g->adj_slots = nullptr;
         g->adj_maps.clear();
-        CK(cudaMalloc(&g->adj_slots, sizeof(float) * 3 * P * (size_t)std::max(K, 2)));
-        g->adj_K = std::max(K, 2);
-        g->adj_maps.resize(g->adj_K);
-        for (int j = 0; j < g->adj_K; ++j) {
+        const int KA = std::max(K, 2);
+        for (;;) {
+            const cudaError_t me = cudaMalloc(&g->adj_slots, sizeof(float) * 3 * P * (size_t)NG * KA);
+            if (me == cudaSuccess) break;
+            cudaGetLastError();
+            if (NG == 1) return set_err(CLIFFS_ERR_CUDA, "adjoint work space: %s", cudaGetErrorString(me));
+            NG = (NG + 1) / 2;
+        }
+        g->adj_K = KA;
+        g->adj_G = NG;
+        g->adj_maps.resize(KA);
+        for (int j = 0; j < KA; ++j) {
             StepMaps& M = g->adj_maps[j];
             M = g->maps[0];
-            float* b = g->adj_slots + 3 * P * j;
-            int rc = make_map(&M.e, b, 3, g->pitch, ny, 1);
-            if (!rc) rc = make_map(&M.u, b + P, 3, g->pitch, ny, 1);
-            if (!rc) rc = make_map(&M.v, b + 2 * P, 3, g->pitch, ny, 1);
+            float* b = g->adj_slots + 3 * P * (size_t)NG * j;
+            int rc = make_map(&M.e, b, 3, g->pitch, ny, NG);
+            if (!rc) rc = make_map(&M.u, b + (size_t)NG * P, 3, g->pitch, ny, NG);
+            if (!rc) rc = make_map(&M.v, b + (size_t)2 * NG * P, 3, g->pitch, ny, NG);
             if (rc) return rc;
+        }
+    }
+    NG = std::min(NG, g->adj_G);
+    const long long FS = (long long)g->adj_G * P;          // floats between the fields of a state
+    // work items of the batched launches: rows per warp such that NG grids fill about
+    // ADJ_GROUP_WAVES waves of resident warps (strips with dry nodes take shorter segments)
+    if (NG > 1) {
+        const long long cap = resident_warps(g) * ADJ_GROUP_WAVES;
+        int Sr = 16;
+        for (; Sr < ny; Sr += 2) {
+            long long nw = 0;
+            for (int st = 0; st < g->nstrips; ++st) {
+                const int seg = (!g->hard.empty() && g->hard[st]) ? hard_rows(Sr) : Sr;
+                nw += (ny + seg - 1) / seg;
+            }
+            if (nw * NG <= cap) break;
+        }
+        if (Sr != g->adj_S || g->adj_items.empty()) {
+            g->adj_items.clear();
+            for (int st = 0; st < g->nstrips; ++st) {
+                const int seg = (!g->hard.empty() && g->hard[st]) ? hard_rows(Sr) : Sr;
+                for (int r0 = 0; r0 < ny; r0 += seg) g->adj_items.push_back(make_int4(st, r0, std::min(r0 + seg, ny), 0));
+            }
+            cudaFree(g->adj_items_dev);
+            g->adj_items_dev = nullptr;
+            CK(cudaMalloc(&g->adj_items_dev, sizeof(int4) * g->adj_items.size()));
+            CK(cudaMemcpy(g->adj_items_dev, g->adj_items.data(), sizeof(int4) * g->adj_items.size(),
+                          cudaMemcpyHostToDevice));
+            g->adj_S = Sr;
         }
     }
     if (!recorded && (g->adj_ncap < nseg || !g->adj_ckpt)) {
@@ -1624,23 +1688,27 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     float* LT = g->adj_t + 3 * TPL;                         // adjoint (eta, u, v) transposed
     float* DT = g->adj_t + 6 * TPL;                         // depth transposed
     float* LB = g->adj_lb;                                  // adjoint (eta, u, v) row-major
-    auto slot = [&](int j) { return g->adj_slots + 3 * P * j; };
+    auto slot = [&](int j) { return g->adj_slots + 3 * FS * j; };
     StepArgs a;
     fill_step_args(g, a, 0, 1);
     a.limit = nullptr;
     a.step = 1;
-    // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating order)
+    // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating
+    // order), for nb segments at once (their steps then have the same parity and no boundary
+    // input: NG is 1 otherwise)
     const long long s0 = recorded ? 0 : steps_of(g, scenario);   // steps done before X_0
-    auto fwd = [&](int from, int to, long long j) -> int {
-        a.eta_in = slot(from); a.u_in = slot(from) + P; a.v_in = slot(from) + 2 * P;
-        a.eta_out = slot(to); a.u_out = slot(to) + P; a.v_out = slot(to) + 2 * P;
+    auto fwd = [&](int from, int to, long long j, int nb) -> int {
+        a.eta_in = slot(from); a.u_in = slot(from) + FS; a.v_in = slot(from) + 2 * FS;
+        a.eta_out = slot(to); a.u_out = slot(to) + FS; a.v_out = slot(to) + 2 * FS;
         a.yfirst = g->cfg.alternate && ((s0 + j) & 1);     // the forward's parity: steps since set_initial
+        a.items = nb > 1 ? g->adj_items_dev : g->items_dev;
+        a.nitems = nb > 1 ? (int)g->adj_items.size() : (int)g->items.size();
         if (g->bnd_any) {                                  // boundary input, as in cliffs_step_n
-            const int rci = impose_boundary(g, slot(from), slot(from) + P, slot(from) + 2 * P,
+            const int rci = impose_boundary(g, slot(from), slot(from) + FS, slot(from) + 2 * FS,
                                             g->t_start + (double)(s0 + j) * g->cfg.dt);
             if (rci) return rci;
         }
-        const cudaError_t le = launch_step_fused(a, g->adj_maps[from], 1, s);
+        const cudaError_t le = launch_step_fused(a, g->adj_maps[from], nb, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
     };
@@ -1653,17 +1721,18 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     const size_t so = (size_t)scenario * P;                 // the scenario's plane
     if (!recorded) {
         CK(cudaMemcpyAsync(slot(0), g->eta[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(slot(0) + P, g->u[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(slot(0) + 2 * P, g->v[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + FS, g->u[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(slot(0) + 2 * FS, g->v[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
     }
     // checkpoint pass: X_{sK} for every segment s (a recorded run has them already)
     for (long long j = 0; !recorded && j <= (nseg - 1) * K; ++j) {
         const int cur = (int)(j & 1);
         if (j % K == 0)
-            CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K), slot(cur), sizeof(float) * 3 * P,
-                               cudaMemcpyDeviceToDevice, s));
+            for (int f = 0; f < 3; ++f)
+                CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K) + f * P, slot(cur) + f * FS, sizeof(float) * P,
+                                   cudaMemcpyDeviceToDevice, s));
         if (j < (nseg - 1) * K) {
-            int rc = fwd(cur, 1 - cur, j);
+            int rc = fwd(cur, 1 - cur, j, 1);
             if (rc) return rc;
         }
     }
@@ -1695,48 +1764,59 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     }
     X.open_lo = g->cfg.open_edges & 1; X.open_hi = (g->cfg.open_edges >> 1) & 1;     // W, E
     Y.open_lo = (g->cfg.open_edges >> 2) & 1; Y.open_hi = (g->cfg.open_edges >> 3) & 1;   // S, N
-    for (long long sg = nseg - 1; sg >= 0; --sg) {
-        const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
+    // groups of segments [sb, se), from the last: a shorter last segment alone, then NG at a time
+    for (long long se = nseg; se > 0;) {
+        const long long sb = (n % K != 0 && se == nseg) ? se - 1 : std::max<long long>(0, se - NG);
+        const int nb = (int)(se - sb);
         // a one-step segment (every state kept: K = 1) is read where it is stored, with no
         // copy and no recomputation
         // a checkpoint holds [3][batch][plane] (recorded) or [3][plane]: this scenario's fields
-        const float* c0 = ckpt + cstride * sg + coff;
-        const float* kept = (j1 - j0 == 1 && cfield == P) ? c0 : nullptr;
+        const bool kept = nb == 1 && std::min<long long>(sb * K + K, n) - sb * K == 1 && cfield == P;
         if (!kept)
-            for (int f = 0; f < 3; ++f)
-                CK(cudaMemcpyAsync(slot(0) + f * P, c0 + f * cfield, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
-        for (long long j = j0; j + 1 < j1; ++j) {
-            int rc = fwd((int)(j - j0), (int)(j - j0 + 1), j);
+            for (int b = 0; b < nb; ++b)
+                for (int f = 0; f < 3; ++f)
+                    CK(cudaMemcpyAsync(slot(0) + f * FS + b * P, ckpt + cstride * (sb + b) + coff + f * cfield,
+                                       sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        const long long len = std::min<long long>(sb * K + K, n) - sb * K;   // steps of each segment
+        for (long long i = 0; i + 1 < len; ++i) {
+            int rc = fwd((int)i, (int)(i + 1), sb * K + i, nb);
             if (rc) return rc;
         }
-        for (long long j = j1 - 1; j >= j0; --j) {
-            const float* st = kept ? kept : slot((int)(j - j0));
-            // with boundary input the stored state is imposed again first (the step ran on the
-            // imposed state), and the seed goes in after the input edges of lambda_j are zeroed
-            if (g->bnd_any) {
-                const int rci = impose_boundary(g, const_cast<float*>(st), const_cast<float*>(st) + P,
-                                                const_cast<float*>(st) + 2 * P,
-                                                g->t_start + (double)(s0 + j) * g->cfg.dt);
-                if (rci) return rci;
-            }
-            const float* seed_j = (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * 3 * G : nullptr;
-            if (g->cfg.alternate && ((s0 + j) & 1)) {
-                int rc2 = adjoint_yfirst_step(g, a, X, Y, st, j, g->bnd_any ? false : seeded);
-                if (rc2) return rc2;
-            } else {
-                le = launch_adj_xfwd(a, st, st + P, st + 2 * P, XT, XT + TPL, XT + 2 * TPL, tp, s);
-                if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
-                X.pe = st; X.pw = st + P; X.pt = st + 2 * P;
-                X.seed = g->bnd_any ? nullptr : seed_j;
-                if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
-                if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
-            }
-            if (g->bnd_any) {
-                le = launch_adj_zero_edges(LT, tp, nx, ny, input_edges(g), s);
-                if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, G, seed_j, s);
-                if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+        for (long long sg = se - 1; sg >= sb; --sg) {
+            const long long j0 = sg * K, j1 = std::min<long long>(j0 + K, n);
+            for (long long j = j1 - 1; j >= j0; --j) {
+                const float* st = kept ? ckpt + cstride * sg + coff : slot((int)(j - j0)) + (sg - sb) * P;
+                const long long fst = kept ? cfield : FS;     // floats between the fields of st
+                // with boundary input the stored state is imposed again first (the step ran on
+                // the imposed state), and the seed goes in after the input edges of lambda_j are
+                // zeroed
+                if (g->bnd_any) {
+                    const int rci = impose_boundary(g, const_cast<float*>(st), const_cast<float*>(st) + fst,
+                                                    const_cast<float*>(st) + 2 * fst,
+                                                    g->t_start + (double)(s0 + j) * g->cfg.dt);
+                    if (rci) return rci;
+                }
+                const float* seed_j =
+                    (seeded && j % g->cfg.gout == 0) ? g->adj_seed + (j / g->cfg.gout) * 3 * G : nullptr;
+                if (g->cfg.alternate && ((s0 + j) & 1)) {
+                    int rc2 = adjoint_yfirst_step(g, a, X, Y, st, fst, j, g->bnd_any ? false : seeded);
+                    if (rc2) return rc2;
+                } else {
+                    le = launch_adj_xfwd(a, st, st + fst, st + 2 * fst, XT, XT + TPL, XT + 2 * TPL, tp, s);
+                    if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
+                    X.pe = st; X.pw = st + fst; X.pt = st + 2 * fst;
+                    X.seed = g->bnd_any ? nullptr : seed_j;
+                    if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
+                    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+                }
+                if (g->bnd_any) {
+                    le = launch_adj_zero_edges(LT, tp, nx, ny, input_edges(g), s);
+                    if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, G, seed_j, s);
+                    if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
+                }
             }
         }
+        se = sb;
     }
     // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]; the u and v parts stay for
     // cliffs_adjoint_velocity
