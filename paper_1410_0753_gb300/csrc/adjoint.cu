@@ -554,6 +554,14 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
 }
 
 // ------------------------------------------------------------------ kernels
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start before its predecessor in the stream has finished. grid_dep_wait() returns once
+// the predecessor has completed and its writes are visible (at once without the attribute);
+// grid_dep_release() lets the successor start (its blocks then fill the SMs this grid's last
+// wave leaves idle).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void load2(const float* p, long long o, int pos, int n, float& a, float& b, float fill) {
     a = b = fill;
     if (pos >= 0 && pos + 1 < n) {
@@ -591,6 +599,9 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : CLIFFS_ADJ_LINE_BLOCKS)
             mb[i] = AMet{q.x, q.y, q.z, q.w};
         }
     }
+    // the inputs below come from the previous kernels of the adjoint step
+    grid_dep_wait();
+    grid_dep_release();
     for (int j = 0; j < ALINES / AWARPS; ++j) {
         const int ln = wi * (ALINES / AWARPS) + j;
         const int line = l0 + ln;
@@ -659,6 +670,12 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
                                                           const float* __restrict__ pv, float* te, float* tu,
                                                           float* tv, int tpitch) {
     __shared__ float tile[3][XOUT][TP];
+    // Launched right behind the x-sweep adjoint of the next step (programmatic launch), this
+    // kernel reads a stored state nothing writes any more and overwrites the x-swept buffer
+    // whose last reader finished before that kernel got going; it runs in that kernel's last
+    // wave and holds its own completion until that kernel has completed, so that the y-sweep
+    // adjoint after it sees both.
+    grid_dep_release();
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int strip = blockIdx.x, r0 = blockIdx.y * ALINES;
     const int c0 = strip * XOUT - 4, cA = c0 + 2 * lane;
@@ -709,6 +726,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
             if (c < a.nx && r < a.ny) out[(long long)c * tpitch + r] = tile[f][q][ln];
         }
     }
+    grid_dep_wait();
 }
 
 // out[c][r] = in[r][c] for r < rows, c < cols (32 x 32 tiles through shared memory)
@@ -759,7 +777,23 @@ cudaError_t launch_adj_zero_edges(float* t, int tpitch, int nx, int ny, int mask
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s) {
+// a launch that may start before its predecessor in the stream has finished
+static cudaError_t launch_pdl(const void* k, dim3 grid, dim3 block, void** args, cudaStream_t s, bool pdl) {
+    if (!pdl) return cudaLaunchKernel(k, grid, block, args, 0, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s, bool pdl) {
     const dim3 grid((A.npos + AOUT - 1) / AOUT, (A.nlines + ALINES - 1) / ALINES);
     static const void* const t[8] = {(const void*)k_adj_line<0, false, false>, (const void*)k_adj_line<0, true, false>,
                                      (const void*)k_adj_line<1, false, false>, (const void*)k_adj_line<1, true, false>,
@@ -767,12 +801,12 @@ cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_
                                      (const void*)k_adj_line<1, false, true>, (const void*)k_adj_line<1, true, true>};
     AdjLineArgs aa = A;
     void* args[] = {&aa};
-    return cudaLaunchKernel(t[(sph ? 1 : 0) + (dir ? 2 : 0) + (A.inv_dt2_s1 > 0.f ? 4 : 0)], grid,
-                            dim3(AWARPS * 32), args, 0, s);
+    return launch_pdl(t[(sph ? 1 : 0) + (dir ? 2 : 0) + (A.inv_dt2_s1 > 0.f ? 4 : 0)], grid, dim3(AWARPS * 32),
+                      args, s, pdl);
 }
 
 cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
-                            float* tu, float* tv, int tpitch, cudaStream_t s) {
+                            float* tu, float* tv, int tpitch, cudaStream_t s, bool pdl) {
     const dim3 grid((a.nx + XOUT - 1) / XOUT, (a.ny + ALINES - 1) / ALINES);
     static const void* const t[16] = {
         (const void*)k_adj_xfwd<false, false, false, false>, (const void*)k_adj_xfwd<true, false, false, false>,
@@ -785,9 +819,9 @@ cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, c
         (const void*)k_adj_xfwd<false, true, true, true>, (const void*)k_adj_xfwd<true, true, true, true>};
     StepArgs aa = a;
     void* args[] = {&aa, (void*)&e, (void*)&u, (void*)&v, &te, &tu, &tv, &tpitch};
-    return cudaLaunchKernel(t[(a.sph ? 1 : 0) + (a.dt_gn2 > 0.f ? 2 : 0) + (a.inv_dt2_s1 > 0.f ? 4 : 0) +
-                              (a.open_edges ? 8 : 0)],
-                            grid, dim3(AWARPS * 32), args, 0, s);
+    return launch_pdl(t[(a.sph ? 1 : 0) + (a.dt_gn2 > 0.f ? 2 : 0) + (a.inv_dt2_s1 > 0.f ? 4 : 0) +
+                        (a.open_edges ? 8 : 0)],
+                      grid, dim3(AWARPS * 32), args, s, pdl);
 }
 
 cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,

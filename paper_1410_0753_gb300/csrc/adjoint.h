@@ -23,9 +23,12 @@ struct AdjLineArgs {
     int open_lo, open_hi;            // the line's first / last node is at an open outer edge
 };
 
-cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s);
+// pdl: launched with programmatic stream serialization. For k_adj_line the kernel then
+// starts early and waits for its predecessor before reading anything it wrote; for
+// k_adj_xfwd only right behind the x-sweep adjoint of the next step (see adjoint.cu).
+cudaError_t launch_adj_line(const AdjLineArgs& A, int dir, bool sph, cudaStream_t s, bool pdl = false);
 cudaError_t launch_adj_xfwd(const StepArgs& a, const float* e, const float* u, const float* v, float* te,
-                            float* tu, float* tv, int tpitch, cudaStream_t s);
+                            float* tu, float* tv, int tpitch, cudaStream_t s, bool pdl = false);
 cudaError_t launch_transpose(const float* in, int ipitch, float* out, int opitch, int rows, int cols,
                              cudaStream_t s);
 cudaError_t launch_adj_seed(float* te, int tpitch, long long tplane, const int* gxy, int G, const float* seed,

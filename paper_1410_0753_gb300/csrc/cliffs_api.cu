@@ -52,13 +52,17 @@ const double DEGR = 3.14159265358979323846 / 180.0;
 // per step: as many segments as fit in this many bytes of recomputed states, tiled to fill
 // about this many waves of resident warps.
 #ifndef CLIFFS_ADJ_GROUP_GIB
-#define CLIFFS_ADJ_GROUP_GIB 8
+#define CLIFFS_ADJ_GROUP_GIB 16
 #endif
 #ifndef CLIFFS_ADJ_GROUP_WAVES
-#define CLIFFS_ADJ_GROUP_WAVES 2
+#define CLIFFS_ADJ_GROUP_WAVES 3
 #endif
 const double ADJ_GROUP_BYTES = (double)CLIFFS_ADJ_GROUP_GIB * (1 << 30);
 const int ADJ_GROUP_WAVES = CLIFFS_ADJ_GROUP_WAVES;
+#ifndef CLIFFS_ADJ_PDL
+#define CLIFFS_ADJ_PDL 1
+#endif
+const bool ADJ_PDL = CLIFFS_ADJ_PDL != 0;     // programmatic launches between the adjoint's kernels
 
 // ----------------------------------------------------------------------------- kernels
 
@@ -1802,11 +1806,18 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
                     int rc2 = adjoint_yfirst_step(g, a, X, Y, st, fst, j, g->bnd_any ? false : seeded);
                     if (rc2) return rc2;
                 } else {
-                    le = launch_adj_xfwd(a, st, st + fst, st + 2 * fst, XT, XT + TPL, XT + 2 * TPL, tp, s);
-                    if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s);
+                    // Without boundary input or the alternating order the three launches of a
+                    // step follow one another as programmatic launches: each may start in the
+                    // last wave of the one before; the x-sweep recomputation only right behind
+                    // the previous step's x-sweep adjoint (not behind the recomputation that
+                    // writes its state).
+                    const bool pdl = ADJ_PDL && !g->bnd_any && !g->cfg.alternate;
+                    le = launch_adj_xfwd(a, st, st + fst, st + 2 * fst, XT, XT + TPL, XT + 2 * TPL, tp, s,
+                                         pdl && j + 1 < j1);
+                    if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s, pdl);
                     X.pe = st; X.pw = st + fst; X.pt = st + 2 * fst;
                     X.seed = g->bnd_any ? nullptr : seed_j;
-                    if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s);
+                    if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s, pdl);
                     if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
                 }
                 if (g->bnd_any) {
