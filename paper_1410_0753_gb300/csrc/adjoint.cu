@@ -562,9 +562,12 @@ __device__ __forceinline__ void line_adjoint(const float (&e)[2], const float (&
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-__device__ __forceinline__ void load2(const float* p, long long o, int pos, int n, float& a, float& b, float fill) {
+// the pair of nodes pos, pos + 1 of a line (fill outside 0 .. n-1); inner: the caller knows
+// both are inside
+__device__ __forceinline__ void load2(const float* p, long long o, int pos, int n, float& a, float& b, float fill,
+                                      bool inner = false) {
     a = b = fill;
-    if (pos >= 0 && pos + 1 < n) {
+    if (inner || (pos >= 0 && pos + 1 < n)) {
         const float2 v = *reinterpret_cast<const float2*>(p + o + pos);
         a = v.x; b = v.y;
     } else {
@@ -599,22 +602,32 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : CLIFFS_ADJ_LINE_BLOCKS)
             mb[i] = AMet{q.x, q.y, q.z, q.w};
         }
     }
-    // the inputs below come from the previous kernels of the adjoint step
+    static_assert(ALINES == AWARPS, "one line per warp");
+    const int ln = wi, line = l0 + ln;
+    const long long o = (long long)line * A.ipitch;
+    float e[2], w[2], t[2], d[2], ge[2], gw[2], gt[2];
+    const bool has = line < A.nlines;               // warp-uniform
+    const bool inner = p0 >= 0 && p0 + XWIN <= A.npos;   // the window lies inside the line
+    // The x-sweep adjoint's primal input (a stored state) and the depth were written before
+    // the adjoint steps began: they load while the previous kernel finishes. Everything else
+    // comes from the previous kernels of the adjoint step.
+    if (DIR == 0 && has) {
+        load2(A.pe, o, pA, A.npos, e[0], e[1], 0.f, inner);
+        load2(A.pw, o, pA, A.npos, w[0], w[1], 0.f, inner);
+        load2(A.pt, o, pA, A.npos, t[0], t[1], 0.f, inner);
+    }
+    if (has) load2(A.pd, o, pA, A.npos, d[0], d[1], OUTSIDE_D, inner);
     grid_dep_wait();
     grid_dep_release();
-    for (int j = 0; j < ALINES / AWARPS; ++j) {
-        const int ln = wi * (ALINES / AWARPS) + j;
-        const int line = l0 + ln;
-        if (line >= A.nlines) break;                 // warp-uniform
-        const long long o = (long long)line * A.ipitch;
-        float e[2], w[2], t[2], d[2], ge[2], gw[2], gt[2];
-        load2(A.pe, o, pA, A.npos, e[0], e[1], 0.f);
-        load2(A.pw, o, pA, A.npos, w[0], w[1], 0.f);
-        load2(A.pt, o, pA, A.npos, t[0], t[1], 0.f);
-        load2(A.pd, o, pA, A.npos, d[0], d[1], OUTSIDE_D);
-        load2(A.ge, o, pA, A.npos, ge[0], ge[1], 0.f);
-        load2(A.gw, o, pA, A.npos, gw[0], gw[1], 0.f);
-        load2(A.gt, o, pA, A.npos, gt[0], gt[1], 0.f);
+    if (has) {
+        if (DIR == 1) {
+            load2(A.pe, o, pA, A.npos, e[0], e[1], 0.f, inner);
+            load2(A.pw, o, pA, A.npos, w[0], w[1], 0.f, inner);
+            load2(A.pt, o, pA, A.npos, t[0], t[1], 0.f, inner);
+        }
+        load2(A.ge, o, pA, A.npos, ge[0], ge[1], 0.f, inner);
+        load2(A.gw, o, pA, A.npos, gw[0], gw[1], 0.f, inner);
+        load2(A.gt, o, pA, A.npos, gt[0], gt[1], 0.f, inner);
         AMet m[2] = {mb[0], mb[1]};
         if (DIR == 0 && SPH) {
             const float f = A.xrow[line];
@@ -651,13 +664,29 @@ __global__ void __launch_bounds__(AWARPS * 32, SPH ? 2 : CLIFFS_ADJ_LINE_BLOCKS)
         }
         __syncthreads();
     }
+    // each position's 8 lines are 32 contiguous bytes of the output: two 16-byte stores (the
+    // output pitch and planes are multiples of 32 floats, l0 a multiple of 8)
+    static_assert(ALINES == 8, "two float4 per output position");
+    const bool full = l0 + ALINES <= A.nlines;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         float* out = f == 0 ? A.oe : f == 1 ? A.ow : A.ot;
-        for (int k = threadIdx.x; k < AOUT * ALINES; k += AWARPS * 32) {
-            const int q = k / ALINES, ln = k % ALINES;
-            const int p = strip * AOUT + q, line = l0 + ln;
-            if (p < A.npos && line < A.nlines) out[(long long)p * A.opitch + line] = tile[f][q][ln];
+        const int k = threadIdx.x;
+        if (k < 2 * AOUT) {
+            const int q = k >> 1, h = (k & 1) * 4;
+            const int p = strip * AOUT + q;
+            if (p < A.npos) {
+                float* dst = out + (long long)p * A.opitch + l0 + h;
+                const float4 v = make_float4(tile[f][q][h], tile[f][q][h + 1], tile[f][q][h + 2], tile[f][q][h + 3]);
+                if (full) {
+                    *reinterpret_cast<float4*>(dst) = v;
+                } else {
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (l0 + h + i < A.nlines) dst[i] = vv[i];
+                }
+            }
         }
     }
 }
@@ -689,11 +718,12 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
         const int r = r0 + ln;
         if (r >= a.ny) break;                       // warp-uniform
         const long long o = (long long)r * a.pitch;
+        const bool inner = c0 >= 0 && c0 + XWIN <= a.nx;
         float2 E, U, V, D;
-        load2(pe, o, cA, a.nx, E.x, E.y, 0.f);
-        load2(pu, o, cA, a.nx, U.x, U.y, 0.f);
-        load2(pv, o, cA, a.nx, V.x, V.y, 0.f);
-        load2(a.d, o, cA, a.nx, D.x, D.y, OUTSIDE_D);
+        load2(pe, o, cA, a.nx, E.x, E.y, 0.f, inner);
+        load2(pu, o, cA, a.nx, U.x, U.y, 0.f, inner);
+        load2(pv, o, cA, a.nx, V.x, V.y, 0.f, inner);
+        load2(a.d, o, cA, a.nx, D.x, D.y, OUTSIDE_D, inner);
         XMet2 m{il, ir, k2};
         if (SPH) {
             const float2 f = v2(a.xrow[r]);
@@ -717,13 +747,26 @@ __global__ void __launch_bounds__(AWARPS * 32) k_adj_xfwd(const StepArgs a, cons
         }
     }
     __syncthreads();
+    const bool full = r0 + ALINES <= a.ny;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         float* out = f == 0 ? te : f == 1 ? tu : tv;
-        for (int k = threadIdx.x; k < XOUT * ALINES; k += AWARPS * 32) {
-            const int q = k / ALINES, ln = k % ALINES;
-            const int c = strip * XOUT + q, r = r0 + ln;
-            if (c < a.nx && r < a.ny) out[(long long)c * tpitch + r] = tile[f][q][ln];
+        const int k = threadIdx.x;
+        if (k < 2 * XOUT) {
+            const int q = k >> 1, h = (k & 1) * 4;
+            const int c = strip * XOUT + q;
+            if (c < a.nx) {
+                float* dst = out + (long long)c * tpitch + r0 + h;
+                const float4 v = make_float4(tile[f][q][h], tile[f][q][h + 1], tile[f][q][h + 2], tile[f][q][h + 3]);
+                if (full) {
+                    *reinterpret_cast<float4*>(dst) = v;
+                } else {
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (r0 + h + i < a.ny) dst[i] = vv[i];
+                }
+            }
         }
     }
     grid_dep_wait();

@@ -1769,6 +1769,7 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     X.open_lo = g->cfg.open_edges & 1; X.open_hi = (g->cfg.open_edges >> 1) & 1;     // W, E
     Y.open_lo = (g->cfg.open_edges >> 2) & 1; Y.open_hi = (g->cfg.open_edges >> 3) & 1;   // S, N
     // groups of segments [sb, se), from the last: a shorter last segment alone, then NG at a time
+    bool after_xadj = false;                   // the last launch was an x-sweep adjoint
     for (long long se = nseg; se > 0;) {
         const long long sb = (n % K != 0 && se == nseg) ? se - 1 : std::max<long long>(0, se - NG);
         const int nb = (int)(se - sb);
@@ -1781,6 +1782,7 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
                 for (int f = 0; f < 3; ++f)
                     CK(cudaMemcpyAsync(slot(0) + f * FS + b * P, ckpt + cstride * (sb + b) + coff + f * cfield,
                                        sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        if (!kept) after_xadj = false;                     // the checkpoint copies and the recomputation
         const long long len = std::min<long long>(sb * K + K, n) - sb * K;   // steps of each segment
         for (long long i = 0; i + 1 < len; ++i) {
             int rc = fwd((int)i, (int)(i + 1), sb * K + i, nb);
@@ -1805,22 +1807,25 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
                 if (g->cfg.alternate && ((s0 + j) & 1)) {
                     int rc2 = adjoint_yfirst_step(g, a, X, Y, st, fst, j, g->bnd_any ? false : seeded);
                     if (rc2) return rc2;
+                    after_xadj = false;
                 } else {
                     // Without boundary input or the alternating order the three launches of a
                     // step follow one another as programmatic launches: each may start in the
                     // last wave of the one before; the x-sweep recomputation only right behind
-                    // the previous step's x-sweep adjoint (not behind the recomputation that
-                    // writes its state).
+                    // the previous step's x-sweep adjoint (not behind the copies and the
+                    // recomputation that write its state).
                     const bool pdl = ADJ_PDL && !g->bnd_any && !g->cfg.alternate;
                     le = launch_adj_xfwd(a, st, st + fst, st + 2 * fst, XT, XT + TPL, XT + 2 * TPL, tp, s,
-                                         pdl && j + 1 < j1);
+                                         pdl && after_xadj);
                     if (le == cudaSuccess) le = launch_adj_line(Y, 1, a.sph, s, pdl);
                     X.pe = st; X.pw = st + fst; X.pt = st + 2 * fst;
                     X.seed = g->bnd_any ? nullptr : seed_j;
                     if (le == cudaSuccess) le = launch_adj_line(X, 0, a.sph, s, pdl);
+                    after_xadj = true;
                     if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
                 }
                 if (g->bnd_any) {
+                    after_xadj = false;
                     le = launch_adj_zero_edges(LT, tp, nx, ny, input_edges(g), s);
                     if (le == cudaSuccess && seed_j) le = launch_adj_seed(LT, tp, TPL, g->adj_gxy, G, seed_j, s);
                     if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(le));
