@@ -210,8 +210,11 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
  * steps keep the forward's parity (steps counted from set_initial).
  * With checkpoint_every == 1 every state is kept and read in place: no recomputation, at
  * n states of 12 bytes per node (25 GB for 2000 steps of a 1024^2 grid).
- * Memory: (checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per node,
- * kept for later calls.
+ * Segments are recomputed several at a time, as one batched launch per step, when neither
+ * boundary input nor the alternating order is set: as many segments NG as fit in 16 GiB of
+ * recomputed states (at least one).
+ * Memory: (NG checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per
+ * node, kept for later calls; if the NG segments do not fit, fewer are tried.
  * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 1, checkpoint_every < 1,
  * NULL output); ERR_UNSTABLE, ERR_TIMEOUT from the forward
  * recomputation; ERR_CUDA. */
