@@ -58,6 +58,7 @@ const double DEGR = 3.14159265358979323846 / 180.0;
 #define CLIFFS_ADJ_GROUP_WAVES 3
 #endif
 const double ADJ_GROUP_BYTES = (double)CLIFFS_ADJ_GROUP_GIB * (1 << 30);
+const int ADJ_GROUP_MAX = 16;                  // and at most this many segments per launch
 const int ADJ_GROUP_WAVES = CLIFFS_ADJ_GROUP_WAVES;
 #ifndef CLIFFS_ADJ_PDL
 #define CLIFFS_ADJ_PDL 1
@@ -1594,12 +1595,14 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     const int G = g->G;
     // Segments are recomputed NG at a time: one launch per step advances NG segments (the
     // fused kernel's batch dimension), which fills the GPU where one grid's launch does not.
-    // NG is the number of segments whose K states fit in ADJ_GROUP_BYTES (1 with boundary
-    // input or the alternating order, whose steps differ between segments).
+    // NG is the number of segments whose K states fit in ADJ_GROUP_BYTES, at most
+    // ADJ_GROUP_MAX (1 with boundary input or the alternating order, whose steps differ
+    // between segments).
     int NG = 1;
     if (K > 1 && !g->bnd_any && !g->cfg.alternate) {
         const double seg_bytes = 12.0 * (double)P * K;
-        NG = (int)std::max(1.0, std::min((double)nseg, std::floor((double)ADJ_GROUP_BYTES / seg_bytes)));
+        NG = (int)std::max(1.0, std::min({(double)nseg, (double)ADJ_GROUP_MAX,
+                                          std::floor((double)ADJ_GROUP_BYTES / seg_bytes)}));
     }
     // work space (kept for later calls); a smaller group if the larger one does not fit
     if (g->adj_K < K || g->adj_G < NG || !g->adj_slots) {
