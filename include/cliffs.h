@@ -212,7 +212,9 @@ int cliffs_run_persistent(cliffs_grid* g, int64_t n);
  * n states of 12 bytes per node (25 GB for 2000 steps of a 1024^2 grid).
  * Segments are recomputed several at a time, as one batched launch per step, when neither
  * boundary input nor the alternating order is set: as many segments NG as fit in 16 GiB of
- * recomputed states, at least one and at most 16.
+ * recomputed states, at least one and at most 16. The checkpoint pass keeps every state of
+ * the last NG segments (1 with boundary input or the alternating order) in that space, so
+ * those are not recomputed.
  * Memory: (NG checkpoint_every + ceil(n / checkpoint_every) + 6) states of 12 bytes per
  * node, kept for later calls; if the NG segments do not fit, fewer are tried.
  * Errors: ERR_STATE before set_initial; ERR_ARG (1D grid, n < 1, checkpoint_every < 1,

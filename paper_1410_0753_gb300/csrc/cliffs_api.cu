@@ -351,6 +351,13 @@ struct cliffs_grid {
     // recomputation (adj_S rows per warp)
     int adj_K = 0;
     int adj_G = 0;
+    // the checkpoint pass: two states to step between (3 planes each) and their TMA
+    // descriptors; descriptors of single planes of the state slots (batch extent 1), made
+    // when first needed: [slot * adj_G + plane]
+    float* adj_pp = nullptr;
+    StepMaps adj_ppmaps[2];
+    std::vector<StepMaps> adj_pmaps;
+    std::vector<unsigned char> adj_pmaps_ok;
     int adj_S = 0;
     std::vector<int4> adj_items;
     int4* adj_items_dev = nullptr;
@@ -761,7 +768,7 @@ void free_grid(cliffs_grid* g) {
     if (g->ctl_h) cudaFreeHost(g->ctl_h);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     cudaFree(g->adj_slots); cudaFree(g->adj_ckpt); cudaFree(g->adj_t); cudaFree(g->adj_lb);
-    cudaFree(g->adj_gxy); cudaFree(g->adj_seed); cudaFree(g->adj_items_dev);
+    cudaFree(g->adj_gxy); cudaFree(g->adj_seed); cudaFree(g->adj_items_dev); cudaFree(g->adj_pp);
     for (int e = 0; e < 4; ++e) cudaFree(g->bnd_v[e]);
     cudaFree(g->bnd_rows);
     cudaFree(g->rec_ckpt);
@@ -1619,6 +1626,8 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
         }
         g->adj_K = KA;
         g->adj_G = NG;
+        g->adj_pmaps.assign((size_t)KA * NG, StepMaps{});
+        g->adj_pmaps_ok.assign((size_t)KA * NG, 0);
         g->adj_maps.resize(KA);
         for (int j = 0; j < KA; ++j) {
             StepMaps& M = g->adj_maps[j];
@@ -1704,17 +1713,29 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     // order), for nb segments at once (their steps then have the same parity and no boundary
     // input: NG is 1 otherwise)
     const long long s0 = recorded ? 0 : steps_of(g, scenario);   // steps done before X_0
-    auto fwd = [&](int from, int to, long long j, int nb) -> int {
-        a.eta_in = slot(from); a.u_in = slot(from) + FS; a.v_in = slot(from) + 2 * FS;
-        a.eta_out = slot(to); a.u_out = slot(to) + FS; a.v_out = slot(to) + 2 * FS;
+    // the same from state `in` (fields fin floats apart, read through the descriptors M) to
+    // state `out` (fields fout apart), one grid
+    auto step1 = [&](float* in, long long fin, const StepMaps& M, float* out, long long fout, long long j) -> int {
+        a.eta_in = in; a.u_in = in + fin; a.v_in = in + 2 * fin;
+        a.eta_out = out; a.u_out = out + fout; a.v_out = out + 2 * fout;
         a.yfirst = g->cfg.alternate && ((s0 + j) & 1);     // the forward's parity: steps since set_initial
-        a.items = nb > 1 ? g->adj_items_dev : g->items_dev;
-        a.nitems = nb > 1 ? (int)g->adj_items.size() : (int)g->items.size();
+        a.items = g->items_dev;
+        a.nitems = (int)g->items.size();
         if (g->bnd_any) {                                  // boundary input, as in cliffs_step_n
-            const int rci = impose_boundary(g, slot(from), slot(from) + FS, slot(from) + 2 * FS,
-                                            g->t_start + (double)(s0 + j) * g->cfg.dt);
+            const int rci = impose_boundary(g, in, in + fin, in + 2 * fin, g->t_start + (double)(s0 + j) * g->cfg.dt);
             if (rci) return rci;
         }
+        const cudaError_t le = launch_step_fused(a, M, 1, s);
+        if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
+        return CLIFFS_OK;
+    };
+    auto fwd = [&](int from, int to, long long j, int nb) -> int {
+        if (nb == 1) return step1(slot(from), FS, g->adj_maps[from], slot(to), FS, j);
+        a.eta_in = slot(from); a.u_in = slot(from) + FS; a.v_in = slot(from) + 2 * FS;
+        a.eta_out = slot(to); a.u_out = slot(to) + FS; a.v_out = slot(to) + 2 * FS;
+        a.yfirst = 0;
+        a.items = g->adj_items_dev;
+        a.nitems = (int)g->adj_items.size();
         const cudaError_t le = launch_step_fused(a, g->adj_maps[from], nb, s);
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
@@ -1723,23 +1744,90 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     const long long cfield = recorded ? (long long)g->B * P : P;      // floats between fields
     const long long cstride = 3 * cfield;                             // floats between checkpoints
     const long long coff = recorded ? (long long)scenario * P : 0;    // the scenario's plane
+    // Groups of segments [sb, se), from the last, each recomputed in one batched run. Without
+    // a recorded run and with K > 1 the checkpoint pass itself keeps every state of the first
+    // group (the last segments: NG of them, the shorter last one included), which then needs
+    // no recomputation. Otherwise a shorter last segment is recomputed alone, then NG at a
+    // time.
+    const bool keep_first = !recorded && K > 1;
+    std::vector<std::pair<long long, long long>> groups;
+    for (long long se = nseg; se > 0;) {
+        const long long sb = (keep_first && se == nseg) ? std::max<long long>(0, se - NG)
+                             : (n % K != 0 && se == nseg) ? se - 1 : std::max<long long>(0, se - NG);
+        groups.push_back({sb, se});
+        se = sb;
+    }
     // X_0: the grid's current state (or the recorded run's first checkpoint)
     const int cb = (int)cur_buf(g, scenario);
     const size_t so = (size_t)scenario * P;                 // the scenario's plane
-    if (!recorded) {
+    if (!recorded && !keep_first) {
         CK(cudaMemcpyAsync(slot(0), g->eta[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(slot(0) + FS, g->u[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(slot(0) + 2 * FS, g->v[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        // checkpoint pass with every state kept (K = 1): X_j for every step j
+        for (long long j = 0; j <= (nseg - 1) * K; ++j) {
+            const int cur = (int)(j & 1);
+            if (j % K == 0)
+                for (int f = 0; f < 3; ++f)
+                    CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K) + f * P, slot(cur) + f * FS, sizeof(float) * P,
+                                       cudaMemcpyDeviceToDevice, s));
+            if (j < (nseg - 1) * K) {
+                int rc = fwd(cur, 1 - cur, j, 1);
+                if (rc) return rc;
+            }
+        }
     }
-    // checkpoint pass: X_{sK} for every segment s (a recorded run has them already)
-    for (long long j = 0; !recorded && j <= (nseg - 1) * K; ++j) {
-        const int cur = (int)(j & 1);
-        if (j % K == 0)
-            for (int f = 0; f < 3; ++f)
-                CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K) + f * P, slot(cur) + f * FS, sizeof(float) * P,
-                                   cudaMemcpyDeviceToDevice, s));
-        if (j < (nseg - 1) * K) {
-            int rc = fwd(cur, 1 - cur, j, 1);
+    if (keep_first) {
+        // checkpoint pass X_0 .. X_{n-1}: up to the first group's first step jk between two
+        // states of its own (a checkpoint every K steps), from there in the first group's
+        // slots (segment sb0 + p in plane p)
+        const long long sb0 = groups[0].first, jk = sb0 * K;
+        if (!g->adj_pp) {
+            CK(cudaMalloc(&g->adj_pp, sizeof(float) * 6 * P));
+            for (int k = 0; k < 2; ++k) {
+                StepMaps& M = g->adj_ppmaps[k];
+                M = g->maps[0];
+                float* b = g->adj_pp + 3 * P * k;
+                int rc = make_map(&M.e, b, 3, g->pitch, ny, 1);
+                if (!rc) rc = make_map(&M.u, b + P, 3, g->pitch, ny, 1);
+                if (!rc) rc = make_map(&M.v, b + 2 * P, 3, g->pitch, ny, 1);
+                if (rc) return rc;
+            }
+        }
+        // where X_j is kept during the pass, its field stride and its descriptors
+        auto at = [&](long long j) -> float* {
+            if (j < jk) return g->adj_pp + 3 * P * (j & 1);
+            return slot((int)(j % K)) + (j / K - sb0) * P;
+        };
+        auto maps_of = [&](long long j, const StepMaps*& M) -> int {
+            if (j < jk) { M = &g->adj_ppmaps[j & 1]; return CLIFFS_OK; }
+            const size_t q = (size_t)(j % K) * g->adj_G + (size_t)(j / K - sb0);
+            if (!g->adj_pmaps_ok[q]) {
+                StepMaps& Mq = g->adj_pmaps[q];
+                Mq = g->maps[0];
+                float* b = at(j);
+                int rc = make_map(&Mq.e, b, 3, g->pitch, ny, 1);
+                if (!rc) rc = make_map(&Mq.u, b + FS, 3, g->pitch, ny, 1);
+                if (!rc) rc = make_map(&Mq.v, b + 2 * FS, 3, g->pitch, ny, 1);
+                if (rc) return rc;
+                g->adj_pmaps_ok[q] = 1;
+            }
+            M = &g->adj_pmaps[q];
+            return CLIFFS_OK;
+        };
+        auto fs_of = [&](long long j) -> long long { return j < jk ? P : FS; };
+        float* x0 = at(0);
+        CK(cudaMemcpyAsync(x0, g->eta[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(x0 + fs_of(0), g->u[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(x0 + 2 * fs_of(0), g->v[cb] + so, sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
+        for (long long j = 0; j + 1 < n; ++j) {
+            if (j % K == 0 && j < jk)                         // checkpoints of the later groups
+                for (int f = 0; f < 3; ++f)
+                    CK(cudaMemcpyAsync(g->adj_ckpt + 3 * P * (j / K) + f * P, at(j) + f * P, sizeof(float) * P,
+                                       cudaMemcpyDeviceToDevice, s));
+            const StepMaps* M = nullptr;
+            int rc = maps_of(j, M);
+            if (!rc) rc = step1(at(j), fs_of(j), *M, at(j + 1), fs_of(j + 1), j);
             if (rc) return rc;
         }
     }
@@ -1771,23 +1859,23 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     }
     X.open_lo = g->cfg.open_edges & 1; X.open_hi = (g->cfg.open_edges >> 1) & 1;     // W, E
     Y.open_lo = (g->cfg.open_edges >> 2) & 1; Y.open_hi = (g->cfg.open_edges >> 3) & 1;   // S, N
-    // groups of segments [sb, se), from the last: a shorter last segment alone, then NG at a time
     bool after_xadj = false;                   // the last launch was an x-sweep adjoint
-    for (long long se = nseg; se > 0;) {
-        const long long sb = (n % K != 0 && se == nseg) ? se - 1 : std::max<long long>(0, se - NG);
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const long long sb = groups[gi].first, se = groups[gi].second;
         const int nb = (int)(se - sb);
+        const bool pass_kept = keep_first && gi == 0;        // states from the checkpoint pass
         // a one-step segment (every state kept: K = 1) is read where it is stored, with no
         // copy and no recomputation
         // a checkpoint holds [3][batch][plane] (recorded) or [3][plane]: this scenario's fields
-        const bool kept = nb == 1 && std::min<long long>(sb * K + K, n) - sb * K == 1 && cfield == P;
-        if (!kept)
+        const bool kept = !pass_kept && nb == 1 && std::min<long long>(sb * K + K, n) - sb * K == 1 && cfield == P;
+        if (!kept && !pass_kept)
             for (int b = 0; b < nb; ++b)
                 for (int f = 0; f < 3; ++f)
                     CK(cudaMemcpyAsync(slot(0) + f * FS + b * P, ckpt + cstride * (sb + b) + coff + f * cfield,
                                        sizeof(float) * P, cudaMemcpyDeviceToDevice, s));
         if (!kept) after_xadj = false;                     // the checkpoint copies and the recomputation
         const long long len = std::min<long long>(sb * K + K, n) - sb * K;   // steps of each segment
-        for (long long i = 0; i + 1 < len; ++i) {
+        for (long long i = 0; i + 1 < len && !pass_kept; ++i) {
             int rc = fwd((int)i, (int)(i + 1), sb * K + i, nb);
             if (rc) return rc;
         }
@@ -1835,7 +1923,6 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
                 }
             }
         }
-        se = sb;
     }
     // dL/d eta_0 = the eta part of lambda_0, back to [ny][nx]; the u and v parts stay for
     // cliffs_adjoint_velocity
