@@ -195,8 +195,9 @@ def test_adjoint_checkpoint_spacing_and_state_untouched():
     n = 40
     seed = np.random.default_rng(3).standard_normal((n // w.gout + 1, len(w.gauges))).astype(np.float32)
     ref = g.adjoint(n, seed, checkpoint_every=n)
-    # K = 2: 20 segments, recomputed as one batched group of 16 and one of 4; K = 7 and 16:
-    # a shorter last segment alone, then the rest in one group
+    # K = 2: 20 segments; the checkpoint pass keeps the states of the last 16, the first 4
+    # are recomputed in one batched launch per step. K = 7 and 16: every segment (a shorter
+    # last one included) kept by the checkpoint pass. K = 1: every state kept.
     for K in (1, 2, 7, 16):
         assert np.array_equal(g.adjoint(n, seed, checkpoint_every=K), ref)
     for x, y in zip(before, g.state()):
