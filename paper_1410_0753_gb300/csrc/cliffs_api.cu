@@ -414,10 +414,16 @@ long long steps_of(const cliffs_grid* g, int b) {
     return s;
 }
 
+// Strips of the fused kernels (2D grids): window s holds columns 56 s .. 56 s + 63 and
+// finishes columns 56 s + 4 .. 56 s + 59, the first from column 0 and the last to column
+// nx - 1 (there the domain's edge is the window's, or past it lie dry ghost columns).
+int fused_strips(int nx) { return nx <= XWIN ? 1 : (nx - XWIN + XOUT - 1) / XOUT + 1; }
+int fused_strip_of(int c, int nstrips) { return c < XOUT + 4 ? 0 : std::min((c - 4) / XOUT, nstrips - 1); }
+
 // per-warp sample lists for the current launch geometry
 int build_samples(cliffs_grid* g) {
-    // a warp owns output columns [W * strip, W * strip + W): 56 for the x-sweeping kernels,
-    // 64 for the y-sweep alone
+    // a warp owns output columns [W * strip, W * strip + W): 56 for the x-sweep alone, 64 for
+    // the y-sweep alone; the fused kernels' strips are those of fused_strips
     const int W = (g->kind == 2) ? XWIN : XOUT;
     const int S = g->kind == 1 ? 1 : g->S;
     const int nseg = g->kind == 1 ? g->ny : g->nseg;
@@ -438,7 +444,7 @@ int build_samples(cliffs_grid* g) {
     for (const int4& it : g->samples) {
         long long w;
         if (g->kind == 0) {
-            const int st = it.y / W;
+            const int st = fused_strip_of(it.y, g->nstrips);
             const auto& v = seg_start[st];
             const int k = (int)(std::upper_bound(v.begin(), v.end(), it.x) - v.begin()) - 1;
             w = seg_item[st][k];
@@ -533,7 +539,7 @@ int choose_geometry(cliffs_grid* g) {
         g->nseg = (g->ny + g->S - 1) / g->S;
     } else {
         g->kind = 0;
-        g->nstrips = (g->nx + XOUT - 1) / XOUT;
+        g->nstrips = fused_strips(g->nx);
         // rows per warp S: each warp walks S + 6 rows (3-row halo above and below), so the
         // cost of one wave of warps is ~ S + 6; pick the even S minimising waves * (S + 6)
         // with the resident warps the occupancy calculator reports (ties go to the larger S)
@@ -1028,14 +1034,14 @@ int cliffs_set_bathy(cliffs_grid* g, const double* x, const double* y, const dou
     }
     if (nx >= 3 && ny >= 3) {
         // strips whose 64-column window holds a node that is dry at rest (d < h_min), or
-        // reaches past the domain edge
+        // reaches the domain edge
         std::vector<double> hd((size_t)nx * ny);
         CK(cudaMemcpy(hd.data(), g->d64, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost));
-        const int nstrips = (nx + XOUT - 1) / XOUT;
+        const int nstrips = fused_strips(nx);
         g->hard.assign(nstrips, 0);
         for (int st = 0; st < nstrips; ++st) {
-            const int c0 = st * XOUT - 4, c1 = c0 + XWIN;
-            if (c0 < 0 || c1 > nx) { g->hard[st] = 1; continue; }
+            const int c0 = st * XOUT, c1 = c0 + XWIN;
+            if (c0 == 0 || c1 >= nx) { g->hard[st] = 1; continue; }
             for (int j = 0; j < ny && !g->hard[st]; ++j)
                 for (int c = c0; c < c1; ++c)
                     if (hd[(size_t)j * nx + c] < g->cfg.h_min) { g->hard[st] = 1; break; }

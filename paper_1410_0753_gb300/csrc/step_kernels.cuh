@@ -242,6 +242,7 @@ struct FusedWarp {
     int lane, b, c0, cA, r0, r1, k0, npairs;
     size_t orow;               // output offset of row r0 (scenario plane + column)
     bool colA, colB, vA, vB, edge;
+    bool bounded;              // the window starts or ends at the domain's edge (xsweep2)
     unsigned tx, nbox;
     unsigned ends;             // open outer edges among this lane's columns (open_ends_x)
     XMet2 m0;
@@ -323,7 +324,7 @@ struct FusedWarp {
                             const float2 f = v2(__ldg(a.xrow + r));
                             mr.inv_l = mul2(mr.inv_l, f); mr.inv_r = mul2(mr.inv_r, f); mr.k2 = mul2(mr.k2, f);
                         }
-                        xsweep2<FRIC, S1, OPEN>(oe, ot, ow, od, mr, K, lane, ends);
+                        xsweep2<FRIC, S1, OPEN>(oe, ot, ow, od, mr, K, lane, ends, bounded);
                     }
                     float2 em = make_float2(0.f, 0.f), sm = em;
                     if (O.emax) {
@@ -346,7 +347,7 @@ struct FusedWarp {
     __device__ __forceinline__ void row(int k, const float* s) {
         float2 E, U, V, D;
         XMet2 m;
-        if (load_row(k, s, E, U, V, D, m) && !YF) xsweep2<FRIC, S1, OPEN>(E, U, V, D, m, K, lane, ends);
+        if (load_row(k, s, E, U, V, D, m) && !YF) xsweep2<FRIC, S1, OPEN>(E, U, V, D, m, K, lane, ends, bounded);
         push_row<PH>(k, s, E, U, V, D);
     }
 
@@ -360,12 +361,12 @@ struct FusedWarp {
         const bool in1 = load_row(k + 1, s + XWIN, E1, U1, V1, D1, m1r);
         const bool wet = wet_mark(E0.x, D0.x, K) && wet_mark(E0.y, D0.y, K) &&
                          wet_mark(E1.x, D1.x, K) && wet_mark(E1.y, D1.y, K);
-        if (in0 && in1 && __all_sync(FULL, wet)) {
+        if (in0 && in1 && !bounded && __all_sync(FULL, wet)) {
             xsweep2_open<FRIC>(E0, U0, V0, D0, m0r, K);
             xsweep2_open<FRIC>(E1, U1, V1, D1, m1r, K);
         } else {
-            if (in0) xsweep2<FRIC, S1, OPEN>(E0, U0, V0, D0, m0r, K, lane, ends);
-            if (in1) xsweep2<FRIC, S1, OPEN>(E1, U1, V1, D1, m1r, K, lane, ends);
+            if (in0) xsweep2<FRIC, S1, OPEN>(E0, U0, V0, D0, m0r, K, lane, ends, bounded);
+            if (in1) xsweep2<FRIC, S1, OPEN>(E1, U1, V1, D1, m1r, K, lane, ends, bounded);
         }
         push_row<0>(k, s, E0, U0, V0, D0);
         push_row<1>(k + 1, s + XWIN, E1, U1, V1, D1);
@@ -377,7 +378,7 @@ struct FusedWarp {
         O = O_;
         b = b_;
         const int4 item = __ldg(a.items + idx);          // (strip, first row, end row)
-        c0 = item.x * XOUT - 4;
+        c0 = item.x * XOUT;                          // window columns c0 .. c0 + 63 (fused_strips)
         cA = c0 + 2 * lane;
         r0 = item.y;
         r1 = item.z;
@@ -389,10 +390,14 @@ struct FusedWarp {
         colA = cA >= 0 && cA < a.nx;
         ends = OPEN ? open_ends_x(a, cA) : 0u;
         colB = cA + 1 >= 0 && cA + 1 < a.nx;
-        const bool own = lane >= 2 && lane < 30;
+        // the output columns: c0 + 4 .. c0 + 59, and from the domain's first column in the
+        // first window, to its last column in the window that reaches it (past it the
+        // window holds dry ghost columns, or its edge is the domain's)
+        const bool own = (lane >= 2 || c0 == 0) && (lane < 30 || c0 + XWIN >= a.nx);
         vA = own && colA;
         vB = own && colB;
-        edge = c0 < 0 || c0 + XWIN > a.nx;
+        edge = c0 + XWIN > a.nx;
+        bounded = c0 == 0 || c0 + XWIN == a.nx;
         for (int j = 0; j < min(RING, npairs); ++j) issue(j);
         float2 il = v2(0.f), ir = v2(0.f), k2 = v2(0.f);
         if (colA) { il.x = __ldg(a.xa + cA); ir.x = __ldg(a.xb + cA); k2.x = __ldg(a.xk + cA); }

@@ -271,14 +271,17 @@ struct XMet2 { float2 inv_l, inv_r, k2; };   // per pair: 1/dx_{j-1}, 1/dx_j, dt
 // x-sweep of one row segment held by a warp: lane l has nodes A = window column 2l (.x)
 // and B = 2l + 1 (.y). Neighbours across lanes come by shuffles. On return (E, W, T) hold
 // the sweep result; it is valid for window columns 4..59 (the outer 4 columns on each side
-// lack their 3-node dependency radius). W is the velocity along the row, T across it.
+// lack their 3-node dependency radius), and up to the window's edge on a side where that
+// edge is the domain's (bounded). W is the velocity along the row, T across it.
 // ends: this lane's nodes at open outer edges, bits 1 A left, 2 A right, 4 B left, 8 B right.
 template <bool FRIC, bool S1 = false, bool OPEN = false>
 __device__ __forceinline__ void xsweep2(float2& E, float2& W, float2& T, float2 D, const XMet2& m,
-                                        const SweepConst& K, int lane, unsigned ends = 0u) {
+                                        const SweepConst& K, int lane, unsigned ends = 0u, bool bounded = false) {
     const bool oA = wet_mark(E.x, D.x, K), oB = wet_mark(E.y, D.y, K);
     const unsigned bA = __ballot_sync(FULL, oA), bB = __ballot_sync(FULL, oB);
-    const bool allwet = (bA & bB) == FULL;
+    // bounded: the window starts or ends at the domain's edge, where the first (last) lane's
+    // outer neighbour is the wall's mirror ghost: the general path, which takes it so
+    const bool allwet = (bA & bB) == FULL && !bounded;
     bool wA = oA, wB = oB;                 // wet after (b)
     int dirA = 0, dirB = 0;
     if (!allwet) {
