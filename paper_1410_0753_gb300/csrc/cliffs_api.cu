@@ -1715,12 +1715,10 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
     fill_step_args(g, a, 0, 1);
     a.limit = nullptr;
     a.step = 1;
-    // step j of the run, from slot `from` to slot `to` (y first on odd j with the alternating
-    // order), for nb segments at once (their steps then have the same parity and no boundary
-    // input: NG is 1 otherwise)
     const long long s0 = recorded ? 0 : steps_of(g, scenario);   // steps done before X_0
-    // the same from state `in` (fields fin floats apart, read through the descriptors M) to
-    // state `out` (fields fout apart), one grid
+    // step j of the run (y first on odd j with the alternating order) for one grid, from
+    // state `in` (fields fin floats apart, read through the descriptors M) to state `out`
+    // (fields fout apart)
     auto step1 = [&](float* in, long long fin, const StepMaps& M, float* out, long long fout, long long j) -> int {
         a.eta_in = in; a.u_in = in + fin; a.v_in = in + 2 * fin;
         a.eta_out = out; a.u_out = out + fout; a.v_out = out + 2 * fout;
@@ -1735,6 +1733,8 @@ static int adjoint_core(cliffs_grid* g, int scenario, int64_t n, int32_t checkpo
         if (le != cudaSuccess) return set_err(CLIFFS_ERR_CUDA, "adjoint forward launch: %s", cudaGetErrorString(le));
         return CLIFFS_OK;
     };
+    // step j from slot `from` to slot `to`, for nb segments at once (their steps then have the
+    // same parity and no boundary input: NG is 1 otherwise)
     auto fwd = [&](int from, int to, long long j, int nb) -> int {
         if (nb == 1) return step1(slot(from), FS, g->adj_maps[from], slot(to), FS, j);
         a.eta_in = slot(from); a.u_in = slot(from) + FS; a.v_in = slot(from) + 2 * FS;
