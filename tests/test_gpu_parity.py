@@ -163,6 +163,41 @@ def test_1d_equals_2d_bit_exact():
         g.close()
 
 
+# ---------------------------------------------------------------------------- window edges
+
+@pytest.mark.parametrize("shape", [(64, 40), (120, 33), (176, 21), (61, 45)])
+def test_windows_ending_at_the_domain_edge_against_oracle(shape):
+    """All-wet grids whose x-sweep windows end exactly at the domain's edges (64: one window,
+    both edges; 120 and 176: the last window's edge is the domain's) or one window past it
+    (61): a wave reflected by the walls inside those windows against the oracle."""
+    nx, ny = shape
+    x = np.arange(nx) * 60.0
+    y = np.arange(ny) * 75.0
+    X, Y = np.meshgrid(x, y)
+    d = 20.0 + 5.0 * np.sin(X / 700.0) * np.cos(Y / 900.0)
+    eta = 0.5 * np.exp(-((X - 0.1 * x[-1]) ** 2 + (Y - 0.6 * y[-1]) ** 2) / (2 * 300.0 ** 2)) \
+        - 0.3 * np.exp(-((X - 0.95 * x[-1]) ** 2 + (Y - 0.3 * y[-1]) ** 2) / (2 * 250.0 ** 2))
+    gauges = [(0, ny // 2), (nx - 1, ny // 3), (min(nx - 1, 59), 1), (min(nx - 1, 60), ny - 2), (nx // 2, 0)]
+    dt = 0.8 * 60.0 / math.sqrt(9.81 * 26.0)
+    kw = dict(h_min=0.01, manning_n2=6.25e-4, maxout=1, gout=1)
+    steps = 200
+    g = CliffsGrid(nx, ny, dt, gauges=gauges, **kw)
+    g.set_bathy(x, y, d)
+    d64, _ = oracle.depth_filter(d)
+    g.set_initial(eta.astype(np.float32))
+    g.step(steps)
+    e32, u32, v32 = g.state()
+    p = oracle.params(nx, ny, dt, **{k: v for k, v in kw.items() if k not in ("maxout", "gout")})
+    o = oracle.run(p, x, y, P.f32(d64), P.f32(eta), nsteps=steps, maxout=1, gout=1, gauges=gauges)
+    err = np.abs(e32 - o["eta"]).max()
+    uerr = np.abs(u32 - o["u"]).max()
+    P.report("window_edges_%dx%d" % shape, eta_abs=err, u_abs=uerr)
+    assert err <= 1e-4 * 0.5
+    assert uerr <= 1e-4 * 0.5
+    assert_gauges("window_edges_%dx%d" % shape, g.gauges(), o["gauges"])
+    g.close()
+
+
 # ---------------------------------------------------------------------------- ragged sizes
 
 @pytest.mark.parametrize("shape", [(131, 97), (57, 203), (3, 3), (200, 1), (1, 150), (345, 17)])
